@@ -1,0 +1,319 @@
+"""Benchmark of the CSPH-TVD time step on one GB300 (or N replicas).
+
+Default workload: the 16384^2 fractal floodplain at dx = 2 m (268M cells,
+FP32, every physics term of Eqs. 1-4 on, 100-cell inflow strip), flooded to
+the median terrain height so about half of the cells are wet (the paper's
+emergency-discharge run had 35-60% water, Sec. 5).  A step is one pass of
+the whole hot path: forces, CFL time step, Lagrangian predictor-corrector,
+Eulerian fluxes and final update, all in the fused kernel (one launch).
+
+Prints one JSON line:
+  value        cell-updates/s (Gcell/s) of K device-resident steps (one CUDA
+               graph of K launches), max over ranks, all ranks' cells counted
+  e2e          the same metric through the C ABI with host buffers: each
+               step uploads the state from pinned host memory
+               (swe_set_state), advances one step (swe_step) and reads the
+               state back (swe_get_state), copies inside the timed region
+  roofline     the fused kernel against measured HBM copy bandwidth:
+               32 algorithmic bytes per cell (read H, Qx, Qy, b, n; write
+               H, Qx, Qy in FP32) over its CUDA-event time per launch
+  cpu_baseline the FP64 CPU oracle on a bounded crop of the same workload
+``--impl reference`` times the oracle alone on the host cores.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+from paper_1705_00614_gb300 import inputs as I  # noqa: E402
+
+METRIC = "Gcell-updates/s and HBM-roofline %; CNN-closure vs fine solve at ≤1% L2"
+UNIT = "Gcell-updates/s"
+BYTES_PER_CELL = {"f32": 32, "f64": 64}
+KERNEL_SOURCES = ["paper_1705_00614_gb300/csrc/swe_kernels.cuh", "paper_1705_00614_gb300/csrc/swe_math.cuh",
+                  "paper_1705_00614_gb300/csrc/swe_launch.h"]
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def flooded_workload(name):
+    """The benchmark problem: a named floodplain, filled to its median
+    terrain height (still water), keeping the inflow strip and physics."""
+    base = name.replace("-flooded", "")
+    p = I.workload(base)
+    eta0 = float(np.median(p.b))
+    H = np.maximum(0.0, eta0 - p.b)
+    z = np.zeros_like(H)
+    return I.Problem(name, p.params, p.b, p.n_manning, H, z, z.copy(), p.sources).to_f32_values(), eta0
+
+
+def crop(prob, y0, x0, n):
+    s = prob.sources
+    keep = (s.ix >= x0) & (s.ix < x0 + n) & (s.iy >= y0) & (s.iy < y0 + n)
+    src = I.Sources(s.ix[keep] - x0, s.iy[keep] - y0, s.weight[keep], s.vx[keep], s.vy[keep], s.hydro[keep],
+                    s.hydrographs)
+    par = I.Params(**{**prob.params.__dict__, "nx": n, "ny": n})
+    sl = (slice(y0, y0 + n), slice(x0, x0 + n))
+    return I.Problem("crop", par, prob.b[sl].copy(), prob.n_manning[sl].copy(), prob.H[sl].copy(),
+                     prob.Qx[sl].copy(), prob.Qy[sl].copy(), src)
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+            time.sleep(0.3)
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 8:
+                self.samples.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.2)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4) if s[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def traffic_from_profile(workload):
+    """DRAM bytes per launch of the fused kernel from the committed ncu
+    summary, if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "k_fused_f32_dram.txt")
+    if not os.path.exists(path):
+        return None
+    kv = {}
+    for line in open(path):
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv[k.strip()] = v.strip()
+    if kv.get("kernel_sources_sha256_16") != kernel_hash():
+        return None
+    try:
+        per_cell = float(kv["dram_bytes_per_cell"])
+    except (KeyError, ValueError):
+        return None
+    return per_cell
+
+
+def oracle_rate(prob, steps, cells_hint=None):
+    import oracle
+    oracle.build()
+    bd = oracle._Bound(prob)
+    H, Qx, Qy, t = prob.H, prob.Qx, prob.Qy, 0.0
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        H, Qx, Qy, info, _ = oracle.step(prob, H, Qx, Qy, t, bound=bd)
+        t = info["t_new"]
+    dt = time.perf_counter() - t0
+    cells = prob.params.nx * prob.params.ny * steps
+    return cells / dt / 1e9, dt
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, on crops of the workload."""
+    if rank != 0:
+        return
+    prob, eta0 = flooded_workload(args.workload)
+    n = args.ref_crop
+    y0 = int(prob.sources.iy.min()) - n // 2
+    c = crop(prob, max(0, y0), 0, n)
+    oracle_rate(c, args.warmup)
+    val, dt = oracle_rate(c, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "sample": f"{n}x{n} crop at the inflow strip",
+                       "parallelism": "single core"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps of a {n}x{n} crop of {args.workload}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="floodplain-16384sq-dx2m-flooded")
+    ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-crop", type=int, default=768)
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    from paper_1705_00614_gb300 import build as B
+    from paper_1705_00614_gb300 import swe
+    B.build()
+
+    prob, eta0 = flooded_workload(args.workload)
+    cells = prob.params.nx * prob.params.ny
+    stream = torch.cuda.current_stream()
+    solver = swe.Solver.from_problem(prob, args.precision, stream=stream.cuda_stream)
+
+    # instantiate the CUDA graph of K steps once, restart, then W untimed
+    # single-launch warm-up steps (they leave the cached K-step graph alone)
+    solver.step(args.steps, report=False)
+    solver.set_state(prob.H, prob.Qx, prob.Qy, 0.0)
+    for _ in range(args.warmup):
+        solver.step(1, report=False)
+    torch.cuda.synchronize()
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        solver.step(args.steps, report=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = e0.elapsed_time(e1)
+    info = solver.step(0)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = world * cells * args.steps / (ms * 1e-3) / 1e9
+
+    # end to end through the C ABI with pinned host buffers
+    shape = (prob.params.ny, prob.params.nx)
+    hb = [torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(6)]
+    hb[0][...] = prob.H
+    hb[1][...] = prob.Qx
+    hb[2][...] = prob.Qy
+    solver.set_state(hb[0], hb[1], hb[2], 0.0)
+    solver.step(1)
+    solver.get_state_into(hb[3], hb[4], hb[5])
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        solver.set_state(hb[0], hb[1], hb[2], 0.0)
+        solver.step(1, report=False)
+        solver.get_state_into(hb[3], hb[4], hb[5])
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = world * cells * args.e2e_steps / e2e_s / 1e9
+    io_bytes = 3 * cells * 8
+
+    bpc = BYTES_PER_CELL[args.precision]
+    achieved = bpc * cells / (ms_per_step * 1e-3) / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks_path):
+        peak = json.load(open(peaks_path))["hbm_gbs"]
+        peak_src = "measured"
+    else:
+        peak, peak_src = 6800.0, "fallback"
+    tr = traffic_from_profile(args.workload)
+    solver.close()
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu:
+            n = args.ref_crop
+            y0 = int(prob.sources.iy.min()) - n // 2
+            c = crop(prob, max(0, y0), 0, n)
+            val, dt = oracle_rate(c, args.cpu_steps)
+            cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{args.cpu_steps} FP64 oracle steps of a {n}x{n} crop at the inflow strip ({dt:.1f} s)"}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": args.workload, "cells": cells, "dx_m": prob.params.dx,
+                           "initial_eta_m": round(eta0, 4), "wet_fraction": float((prob.H > prob.params.eps).mean()),
+                           "l2": "inputs larger than L2 (state + statics 5.4 GB per step)",
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "final_t_s": info["t"], "wet_cells_end": info["wet_cells"]},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "peak_source": peak_src,
+                             "traffic": None if tr is None else tr * cells,
+                             "kernel": "k_fused<float>", "algorithmic_bytes_per_cell": bpc},
+                "cpu_baseline": cpu,
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+                "gpu_launches": args.steps,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,176 @@
+/*
+ * libswe — one time step of the combined Lagrangian-Euler (CSPH-TVD)
+ * shallow-water scheme on a regular grid, on one NVIDIA GB300 (sm_103a).
+ *
+ * The method: Dyakonova, Khoperskov & Khrapov, "Numerical Model of Shallow
+ * Water: the Use of NVIDIA CUDA Graphics Processors" (arXiv 1705.00614).
+ * The state solves the Saint-Venant equations, Eqs. 1-3, with the force
+ * terms of Eq. 4; a step is the four-stage scheme of Sec. 2.3 (Fig. 2),
+ * computed by the paper's kernels K2-K8 (Sec. 3): forces, CFL time step,
+ * Lagrangian predictor and corrector, Eulerian TVD face fluxes, final update.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns a swe_status (0 = SWE_OK, negative = error) except
+ *    swe_destroy and the string functions.  No C++ exception crosses the ABI.
+ *    On error, swe_last_error() returns a message for the calling thread.
+ *  - Host arrays are row-major [ny][nx] (x fastest), FP64, owned by the
+ *    caller and only read or written during the call (they are copied).
+ *    Cell (i, j) has centre ((i + 1/2) dx, (j + 1/2) dx).
+ *  - A context owns all device memory it uses (allocated in swe_create and,
+ *    for the staging buffer of host copies, at the first host copy) and
+ *    frees it in swe_destroy.  Device pointers returned by
+ *    swe_get_device_ptrs stay owned by the context.
+ *  - A context is bound to one CUDA stream (swe_params.cuda_stream, or the
+ *    legacy default stream when NULL) and is not thread safe.  Calls that
+ *    return data to the host synchronise that stream; the others only
+ *    enqueue work.
+ *  - Depth H (m), momentum Q = H U (m^2/s, the paper's HV of K8), bed b (m).
+ */
+#ifndef SWE_H
+#define SWE_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define SWE_API __attribute__((visibility("default")))
+#else
+#define SWE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct swe_ctx swe_ctx; /* opaque, owned by the library */
+
+typedef enum {
+    SWE_OK = 0,
+    SWE_ERR_ARG = -1,            /* invalid argument; nothing was changed */
+    SWE_ERR_CUDA = -2,           /* a CUDA call failed; see swe_last_error() */
+    SWE_ERR_OOM = -3,            /* device or host allocation failed */
+    SWE_ERR_NONFINITE = -4,      /* a NaN/Inf entered the state or the speeds */
+    SWE_ERR_DT = -5,             /* time step not positive (t_end already reached) */
+    SWE_ERR_DEVICE_TIMEOUT = -6, /* a bounded device wait ran out; the step is invalid */
+    SWE_ERR_STATE = -7           /* call out of order (e.g. no state set yet) */
+} swe_status;
+
+enum { SWE_F32 = 0, SWE_F64 = 1 };           /* arithmetic and storage type */
+enum { SWE_FUSED = 0, SWE_STAGED = 1 };      /* kernel organisation */
+
+/* Parameters of one grid: the physical constants of Eqs. 1-4 and the
+ * numerical ones of Sec. 2.3.  Zero-initialise and set what you need;
+ * swe_params_default fills the usual values. */
+typedef struct {
+    int32_t nx, ny;        /* cells along x and y, each >= 1 */
+    int32_t precision;     /* SWE_F32 or SWE_F64 */
+    int32_t mode;          /* SWE_FUSED (one tiled kernel per step) or
+                              SWE_STAGED (one kernel per stage, keeps every
+                              intermediate in device memory) */
+    double dx;             /* h = dx = dy (m), Sec. 2.2 */
+    double g;              /* gravitational acceleration (m/s^2) */
+    double cfl;            /* Courant number K, 0 < K < 1 (Fig. 2) */
+    double eps_dry;        /* a cell is wet when H > eps_dry (the Eps of K8) */
+    double dt_max;         /* upper bound of the time step (s) */
+    double dt_fixed;       /* > 0: every step uses this tau instead of the CFL */
+    double nu;             /* kinematic turbulent viscosity (m^2/s), Eq. 4 */
+    double coriolis_f;     /* 2 Omega sin(latitude) (1/s), Eq. 4 */
+    double wind_x, wind_y; /* wind velocity W (m/s), Eq. 4 */
+    double c_a;            /* wind drag coefficient C_a, Eq. 4 */
+    double rho_air_over_rho; /* rho_a / rho, Eq. 4 */
+    void* cuda_stream;     /* cudaStream_t to run on; borrowed, may be NULL */
+    int32_t tile_w;        /* fused mode: output columns per CTA (0 = auto) */
+    int32_t seg_h;         /* fused mode: output rows per CTA (0 = auto) */
+} swe_params;
+
+/* What one call of swe_step reports (all reductions in FP64). */
+typedef struct {
+    double t;          /* simulation time after the last step (s) */
+    double dt_last;    /* tau of the last step (s) */
+    double mass;       /* h^2 * sum of H after the last step (m^3) */
+    double src_vol;    /* volume added by sources in the last step (m^3) */
+    double clip_vol;   /* volume added by clipping negative depths, last step (m^3) */
+    double max_speed;  /* max over wet cells of max(U_s, U_p) at the new state (m/s) */
+    int64_t wet_cells; /* cells with H > eps_dry after the last step */
+    int64_t step;      /* steps taken since swe_set_state */
+    int32_t err_word;  /* device error bits (0 = none) */
+    int32_t pad;
+} swe_step_info;
+
+/* Fill p with defaults: g 9.81, K 0.3, eps 1e-4, dt_max 1, FP32, fused,
+ * rho_a/rho 1.225e-3, everything else 0.  nx, ny, dx must still be set. */
+SWE_API void swe_params_default(swe_params* p);
+
+/* Create a context for one grid (Sec. 2.2: uniform Cartesian grid).
+ * Allocates the padded state, statics and control block on the current
+ * CUDA device; bed = 0, Manning n = 0, no sources, no state yet.
+ * Errors: SWE_ERR_ARG (bad sizes/parameters), SWE_ERR_OOM, SWE_ERR_CUDA. */
+SWE_API int swe_create(const swe_params* p, swe_ctx** out_ctx);
+
+/* Terrain b(x, y) and Manning roughness n_M (Sec. 2.2, Eq. 4), each nx*ny
+ * host FP64.  manning_n may be NULL (0 everywhere).  Finite values only
+ * (SWE_ERR_NONFINITE otherwise); |b| < 1e20. */
+SWE_API int swe_set_terrain(swe_ctx* ctx, const double* b, const double* manning_n);
+
+/* State at time t: depth H >= 0 and momentum Qx = H Ux, Qy = H Uy (the
+ * paper's H and HV), nx*ny host FP64 each.  Resets the step counter, the
+ * time to t, and computes the first time step's signal speed (K3).
+ * Errors: SWE_ERR_ARG (negative depth), SWE_ERR_NONFINITE. */
+SWE_API int swe_set_state(swe_ctx* ctx, const double* H, const double* Qx, const double* Qy, double t);
+
+/* Sources and drains sigma with source velocity V (Eqs. 1-3).  Cell m at
+ * (ix[m], iy[m]) gets sigma = weight[m] * q_{hydro[m]}(t) [m/s], evaluated
+ * at t_n + tau/2, where hydrograph r has the row
+ * hydro_tab[4r..4r+3] = (kind, peak, t_p, s): kind 0 is
+ * peak * exp(-(t - t_p)^2 / (2 s^2)), kind 1 is the constant peak.
+ * Cells must be distinct and inside the grid; vx, vy may be NULL (V = 0).
+ * n = 0 removes all sources.  Copied. */
+SWE_API int swe_set_sources(swe_ctx* ctx, int32_t n, const int32_t* ix, const int32_t* iy,
+                    const double* weight, const double* vx, const double* vy,
+                    const int32_t* hydro, int32_t n_hydro, const double* hydro_tab);
+
+/* Open (closed[m] = 0) or close (closed[m] = 1) gate cells (hydraulic
+ * structures, Sec. 1/Eq. 1 text): a closed cell is a wall, keeps its water
+ * and carries no flux.  Takes effect from the next step. */
+SWE_API int swe_set_solid(swe_ctx* ctx, int32_t n, const int32_t* ix, const int32_t* iy,
+                  const uint8_t* closed);
+
+/* Advance nsteps time steps (Sec. 2.3 stages I-IV, kernels K2-K8).  tau of
+ * each step comes from the state at its start (K3) unless dt_fixed is set;
+ * if t_end > 0 the last step is shortened to land on t_end and later steps
+ * do nothing.  With info != NULL the stream is synchronised and the step
+ * report copied out; device error bits turn into SWE_ERR_NONFINITE or
+ * SWE_ERR_DEVICE_TIMEOUT.  With info == NULL the steps are only enqueued
+ * (nsteps >= 2 run as one CUDA graph). */
+SWE_API int swe_step(swe_ctx* ctx, int32_t nsteps, double t_end, swe_step_info* info);
+
+/* Copy the current state to host FP64 arrays (any of H, Qx, Qy may be
+ * NULL) and the current time to *t (may be NULL).  Synchronises. */
+SWE_API int swe_get_state(swe_ctx* ctx, double* H, double* Qx, double* Qy, double* t);
+
+/* Device pointers of the current state (first interior cell of H, Qx, Qy),
+ * the row pitch in elements and the element size in bytes.  Valid until
+ * the next swe_step or swe_set_state (the state is double buffered). */
+SWE_API int swe_get_device_ptrs(swe_ctx* ctx, void** H, void** Qx, void** Qy, int64_t* pitch_elems,
+                        int32_t* elem_bytes);
+
+/* SWE_STAGED contexts only: copy the intermediates of the last step to
+ * host FP64 arrays, in the order ux, uy, ax, ay, phi, usx, usy, hs, ax2,
+ * ay2, phi2, utx, uty, uhx, uhy, ht, qtx, qty, upx, upy (each nx*ny), then
+ * fx [3][ny][nx+1] and fy [3][ny+1][nx] (face fluxes F_H, F_Qx, F_Qy, the
+ * paper's Fh, Fv).  out[k] may be NULL to skip field k.  Synchronises. */
+SWE_API int swe_get_stages(swe_ctx* ctx, double* const* out);
+
+/* Wait for all work of the context's stream. */
+SWE_API int swe_sync(swe_ctx* ctx);
+
+/* Release every resource of the context (NULL is ignored). */
+SWE_API void swe_destroy(swe_ctx* ctx);
+
+SWE_API const char* swe_status_str(int status);
+SWE_API const char* swe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SWE_H */

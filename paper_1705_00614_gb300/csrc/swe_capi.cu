@@ -1,0 +1,789 @@
+// Host side of libswe: contexts, device memory, host copies, tensor maps,
+// tiling, CUDA graphs and the C ABI declared in include/swe.h.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/swe.h"
+#include "swe_launch.h"
+
+using namespace swe;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(SWE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool finite_all(const double* a, size_t n) {
+    for (size_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+enum StageField {
+    SF_UX, SF_UY, SF_AX, SF_AY, SF_PHI, SF_USX, SF_USY, SF_HS, SF_AX2, SF_AY2, SF_PHI2, SF_UTX, SF_UTY,
+    SF_UHX, SF_UHY, SF_HT, SF_QTX, SF_QTY, SF_UPX, SF_UPY, SF_SIG, SF_SVX, SF_SVY,
+    SF_FX0, SF_FX1, SF_FX2, SF_FY0, SF_FY1, SF_FY2, SF_COUNT
+};
+
+}  // namespace
+
+struct swe_ctx {
+    swe_params p;
+    int dev = 0;
+    int esz = 4;
+    int pitch = 0, rows = 0;
+    size_t plane = 0;
+    void* f[8] = {};  // H0 Qx0 Qy0 H1 Qx1 Qy1 b n
+    Ctl* ctl = nullptr;
+    Ctl* ctl_host = nullptr;
+    Part* parts = nullptr;
+    Part* parts2 = nullptr;
+    int parts_cap = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    // fused tiling
+    int seg_h = 0, ntx = 0, nty = 0, nitems = 0;
+    int sm_count = 0, occ = 0;
+    // sources
+    int nsrc = 0, nh = 0;
+    int* d_scell = nullptr;
+    int* d_shydro = nullptr;
+    double* d_sw = nullptr;
+    double* d_svx = nullptr;
+    double* d_svy = nullptr;
+    double* d_hydro = nullptr;
+    SrcEntry* d_entries = nullptr;
+    int* d_src_off = nullptr;
+    // terrain copy (to reopen gates) and gate state
+    std::vector<double> h_b;
+    std::vector<uint8_t> h_solid;
+    // staged intermediates
+    void* scr[SF_COUNT] = {};
+    // FP64 staging for host copies
+    double* staging = nullptr;
+    size_t staging_bytes = 0;
+    int* d_tmp_i = nullptr;
+    double* d_tmp_d = nullptr;
+    size_t tmp_cap = 0;
+    CUtensorMap tmH[2], tmQx[2], tmQy[2], tmB, tmN;
+    cudaGraphExec_t gexec = nullptr;
+    int gsteps = 0;
+    bool has_state = false;
+};
+
+namespace {
+
+template <class T>
+Grid<T> grid_of(const swe_ctx* c) {
+    Grid<T> g;
+    g.nx = c->p.nx;
+    g.ny = c->p.ny;
+    g.pitch = c->pitch;
+    for (int b = 0; b < 2; ++b) {
+        g.H[b] = (T*)c->f[3 * b + 0];
+        g.Qx[b] = (T*)c->f[3 * b + 1];
+        g.Qy[b] = (T*)c->f[3 * b + 2];
+    }
+    g.b = (T*)c->f[6];
+    g.n = (T*)c->f[7];
+    return g;
+}
+
+template <class T>
+Phys<T> phys_of(const swe_params& p) {
+    Phys<T> P;
+    P.g = (T)p.g;
+    P.h = (T)p.dx;
+    P.eps = (T)p.eps_dry;
+    P.nu = (T)p.nu;
+    P.f = (T)p.coriolis_f;
+    P.wx = (T)p.wind_x;
+    P.wy = (T)p.wind_y;
+    P.ca = (T)p.c_a;
+    P.ra = (T)p.rho_air_over_rho;
+    return P;
+}
+
+StepP stepp_of(const swe_params& p) {
+    StepP s;
+    s.dx = p.dx;
+    s.cfl = p.cfl;
+    s.dt_max = p.dt_max;
+    s.dt_fixed = p.dt_fixed;
+    return s;
+}
+
+template <class T>
+StagedArgs<T> staged_args(const swe_ctx* c) {
+    StagedArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    a.g = grid_of<T>(c);
+    a.P = phys_of<T>(c->p);
+    a.sp = stepp_of(c->p);
+    a.ctl = c->ctl;
+    a.parts = c->parts;
+    a.parts2 = c->parts2;
+    T** fields[] = {&a.ux, &a.uy, &a.ax, &a.ay, &a.phi, &a.usx, &a.usy, &a.hs, &a.ax2, &a.ay2, &a.phi2,
+                    &a.utx, &a.uty, &a.uhx, &a.uhy, &a.ht, &a.qtx, &a.qty, &a.upx, &a.upy, &a.sig,
+                    &a.svx, &a.svy, &a.fx[0], &a.fx[1], &a.fx[2], &a.fy[0], &a.fy[1], &a.fy[2]};
+    for (int k = 0; k < SF_COUNT; ++k) *fields[k] = (T*)c->scr[k];
+    a.s_cell = c->d_scell;
+    a.s_hydro = c->d_shydro;
+    a.s_w = c->d_sw;
+    a.s_vx = c->d_svx;
+    a.s_vy = c->d_svy;
+    a.nsrc = c->nsrc;
+    a.hydro = c->d_hydro;
+    a.nh = c->nh;
+    return a;
+}
+
+template <class T>
+FusedArgs<T> fused_args(const swe_ctx* c) {
+    FusedArgs<T> a;
+    std::memset(&a, 0, sizeof(a));
+    for (int b = 0; b < 2; ++b) {
+        a.tmH[b] = c->tmH[b];
+        a.tmQx[b] = c->tmQx[b];
+        a.tmQy[b] = c->tmQy[b];
+    }
+    a.tmB = c->tmB;
+    a.tmN = c->tmN;
+    a.g = grid_of<T>(c);
+    a.P = phys_of<T>(c->p);
+    a.sp = stepp_of(c->p);
+    a.ctl = c->ctl;
+    a.parts = c->parts;
+    a.src = c->d_entries;
+    a.src_off = c->d_src_off;
+    a.hydro = c->d_hydro;
+    a.nh = c->nh;
+    a.ntx = c->ntx;
+    a.seg_h = c->seg_h;
+    a.nitems = c->nitems;
+    return a;
+}
+
+bool is64(const swe_ctx* c) { return c->p.precision == SWE_F64; }
+
+// Launch-cost model of the fused kernel: waves of CTAs times rows per CTA.
+void choose_tiling(swe_ctx* c) {
+    const int nx = c->p.nx, ny = c->p.ny;
+    c->ntx = (nx + TW - 1) / TW;
+    int best = 0;
+    double best_cost = 1e300;
+    const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
+    const int slots = std::max(1, c->sm_count * std::max(1, c->occ));
+    for (int sh : cand) {
+        if (sh > ny && best != 0) break;
+        const long long items = (long long)c->ntx * ((ny + sh - 1) / sh);
+        const double waves = std::ceil((double)items / slots);
+        const double cost = waves * (std::min(sh, ny) + 2 * HALO);
+        if (cost < best_cost - 1e-9) {
+            best_cost = cost;
+            best = sh;
+        }
+    }
+    c->seg_h = c->p.seg_h > 0 ? c->p.seg_h : best;
+    c->nty = (ny + c->seg_h - 1) / c->seg_h;
+    c->nitems = c->ntx * c->nty;
+}
+
+int encode_map(swe_ctx* c, CUtensorMap* m, void* base) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return fail(SWE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[2] = {(cuuint64_t)(c->p.nx + 2 * PAD), (cuuint64_t)(c->p.ny + 2 * PAD)};
+    cuuint64_t strides[1] = {(cuuint64_t)c->pitch * (cuuint64_t)c->esz};
+    cuuint32_t box[2] = {(cuuint32_t)WIN, (cuuint32_t)RB};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, is64(c) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(SWE_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return SWE_OK;
+}
+
+int ensure_staging(swe_ctx* c, size_t bytes) {
+    if (c->staging_bytes >= bytes) return SWE_OK;
+    if (c->staging) {
+        CK(cudaStreamSynchronize(c->st));
+        cudaFree(c->staging);
+        c->staging = nullptr;
+        c->staging_bytes = 0;
+    }
+    if (cudaMalloc(&c->staging, bytes) != cudaSuccess) return fail(SWE_ERR_OOM, "staging allocation failed");
+    c->staging_bytes = bytes;
+    return SWE_OK;
+}
+
+int ensure_tmp(swe_ctx* c, size_t n) {
+    if (c->tmp_cap >= n) return SWE_OK;
+    CK(cudaStreamSynchronize(c->st));
+    cudaFree(c->d_tmp_i);
+    cudaFree(c->d_tmp_d);
+    c->d_tmp_i = nullptr;
+    c->d_tmp_d = nullptr;
+    c->tmp_cap = 0;
+    if (cudaMalloc(&c->d_tmp_i, n * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_tmp_d, n * sizeof(double)) != cudaSuccess)
+        return fail(SWE_ERR_OOM, "temporary allocation failed");
+    c->tmp_cap = n;
+    return SWE_OK;
+}
+
+// Host FP64 [ny][nx] -> padded device field (through the FP64 staging);
+// with flag, non-finite (and, with check_neg, negative) values are flagged.
+int upload_field(swe_ctx* c, const double* host, void* dev, unsigned* flag = nullptr, int check_neg = 0) {
+    const size_t n = (size_t)c->p.nx * c->p.ny;
+    int rc = ensure_staging(c, n * sizeof(double));
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(c->staging, host, n * sizeof(double), cudaMemcpyHostToDevice, c->st));
+    CK(is64(c) ? launch_pack<double>(c->staging, (double*)dev, c->p.nx, c->p.ny, c->pitch, c->st, flag, check_neg)
+               : launch_pack<float>(c->staging, (float*)dev, c->p.nx, c->p.ny, c->pitch, c->st, flag, check_neg));
+    return SWE_OK;
+}
+
+// Padded device field (base of the interior shifted by (ox, oy)) -> host
+// FP64 [ny][nx], both sizes given.
+int download_field(swe_ctx* c, const void* dev, double* host, int nx, int ny, long long shift_elems) {
+    const size_t n = (size_t)nx * ny;
+    int rc = ensure_staging(c, n * sizeof(double));
+    if (rc) return rc;
+    if (is64(c))
+        CK(launch_unpack<double>((const double*)dev + shift_elems, c->staging, nx, ny, c->pitch, c->st));
+    else
+        CK(launch_unpack<float>((const float*)dev + shift_elems, c->staging, nx, ny, c->pitch, c->st));
+    CK(cudaMemcpyAsync(host, c->staging, n * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    return SWE_OK;
+}
+
+int read_ctl(swe_ctx* c) {
+    CK(cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SWE_OK;
+}
+
+int state_speed(swe_ctx* c) {
+    if (is64(c)) CK(launch_state_speed<double>(staged_args<double>(c), c->st));
+    else CK(launch_state_speed<float>(staged_args<float>(c), c->st));
+    return SWE_OK;
+}
+
+void drop_graph(swe_ctx* c) {
+    if (c->gexec) {
+        cudaGraphExecDestroy(c->gexec);
+        c->gexec = nullptr;
+        c->gsteps = 0;
+    }
+}
+
+int launch_one_step(swe_ctx* c) {
+    if (c->p.mode == SWE_STAGED) {
+        if (is64(c)) CK(launch_staged<double>(staged_args<double>(c), c->st));
+        else CK(launch_staged<float>(staged_args<float>(c), c->st));
+    } else {
+        if (is64(c)) CK(launch_fused<double>(fused_args<double>(c), c->st));
+        else CK(launch_fused<float>(fused_args<float>(c), c->st));
+    }
+    return SWE_OK;
+}
+
+size_t cells_padded(const swe_ctx* c) { return (size_t)c->pitch * (size_t)c->rows; }
+
+// Per-work-item source lists of the fused kernel, in window coordinates and
+// sorted by (row, column).
+int build_source_tables(swe_ctx* c, const int32_t* ix, const int32_t* iy, const double* w, const double* vx,
+                        const double* vy, const int32_t* hy) {
+    std::vector<std::vector<SrcEntry>> per(c->nitems);
+    for (int m = 0; m < c->nsrc; ++m) {
+        const int sx_lo = std::max(0, (ix[m] + HALO - (WIN - 1) + TW - 1) / TW - 1);
+        const int sx_hi = std::min(c->ntx - 1, (ix[m] + HALO) / TW);
+        const int gy_lo = std::max(0, (iy[m] - c->seg_h - HALO) / c->seg_h - 1);
+        const int gy_hi = std::min(c->nty - 1, (iy[m] + HALO) / c->seg_h);
+        for (int sy = gy_lo; sy <= gy_hi; ++sy)
+            for (int sx = sx_lo; sx <= sx_hi; ++sx) {
+                const int x0 = sx * TW, y0 = sy * c->seg_h;
+                const int sh = std::min(c->seg_h, c->p.ny - y0);
+                const int r = iy[m] - y0 + HALO, col = ix[m] - x0 + HALO;
+                if (r < 0 || r >= sh + 2 * HALO || col < 0 || col >= WIN) continue;
+                SrcEntry e;
+                e.r = (short)r;
+                e.c = (short)col;
+                e.hydro = hy[m];
+                e.w = w[m];
+                e.vx = vx ? vx[m] : 0.0;
+                e.vy = vy ? vy[m] : 0.0;
+                per[sy * c->ntx + sx].push_back(e);
+            }
+    }
+    std::vector<int> off(c->nitems + 1, 0);
+    std::vector<SrcEntry> all;
+    for (int i = 0; i < c->nitems; ++i) {
+        std::sort(per[i].begin(), per[i].end(), [](const SrcEntry& a, const SrcEntry& b) {
+            return a.r != b.r ? a.r < b.r : a.c < b.c;
+        });
+        off[i] = (int)all.size();
+        all.insert(all.end(), per[i].begin(), per[i].end());
+    }
+    off[c->nitems] = (int)all.size();
+    cudaFree(c->d_entries);
+    cudaFree(c->d_src_off);
+    c->d_entries = nullptr;
+    c->d_src_off = nullptr;
+    if (cudaMalloc(&c->d_src_off, off.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_entries, std::max<size_t>(1, all.size()) * sizeof(SrcEntry)) != cudaSuccess)
+        return fail(SWE_ERR_OOM, "source table allocation failed");
+    CK(cudaMemcpy(c->d_src_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    if (!all.empty())
+        CK(cudaMemcpy(c->d_entries, all.data(), all.size() * sizeof(SrcEntry), cudaMemcpyHostToDevice));
+    return SWE_OK;
+}
+
+// Bed values of the given cells (walls where closed) -> device.
+int apply_beds(swe_ctx* c, const std::vector<int>& cells) {
+    if (cells.empty()) return SWE_OK;
+    int rc = ensure_tmp(c, cells.size());
+    if (rc) return rc;
+    std::vector<int> idx(cells.size());
+    std::vector<double> val(cells.size());
+    for (size_t m = 0; m < cells.size(); ++m) {
+        const int i = cells[m] % c->p.nx, j = cells[m] / c->p.nx;
+        idx[m] = (j + PAD) * c->pitch + (i + PAD);
+        val[m] = c->h_solid[cells[m]] ? WALL_BED : c->h_b[cells[m]];
+    }
+    CK(cudaStreamSynchronize(c->st));
+    CK(cudaMemcpy(c->d_tmp_i, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_tmp_d, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (is64(c)) CK(launch_scatter<double>((double*)c->f[6], c->d_tmp_i, c->d_tmp_d, (int)idx.size(), c->st));
+    else CK(launch_scatter<float>((float*)c->f[6], c->d_tmp_i, c->d_tmp_d, (int)idx.size(), c->st));
+    return SWE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void swe_params_default(swe_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->precision = SWE_F32;
+    p->mode = SWE_FUSED;
+    p->g = 9.81;
+    p->cfl = 0.3;
+    p->eps_dry = 1e-4;
+    p->dt_max = 1.0;
+    p->rho_air_over_rho = 1.225e-3;
+}
+
+const char* swe_status_str(int s) {
+    switch (s) {
+        case SWE_OK: return "ok";
+        case SWE_ERR_ARG: return "invalid argument";
+        case SWE_ERR_CUDA: return "CUDA error";
+        case SWE_ERR_OOM: return "out of memory";
+        case SWE_ERR_NONFINITE: return "non-finite value";
+        case SWE_ERR_DT: return "time step not positive";
+        case SWE_ERR_DEVICE_TIMEOUT: return "device wait timed out";
+        case SWE_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* swe_last_error(void) { return g_err.c_str(); }
+
+int swe_create(const swe_params* p, swe_ctx** out) {
+    if (!p || !out) return fail(SWE_ERR_ARG, "null argument");
+    *out = nullptr;
+    if (p->nx < 1 || p->ny < 1 || p->nx > (1 << 20) || p->ny > (1 << 20) ||
+        (double)p->nx * p->ny > 4.0e9)
+        return fail(SWE_ERR_ARG, "grid size out of range");
+    if (!(p->dx > 0.0) || !(p->g > 0.0) || !(p->cfl > 0.0 && p->cfl <= 1.0) || !(p->eps_dry >= 0.0) ||
+        !(p->dt_max > 0.0) || !(p->dt_fixed >= 0.0) || !(p->nu >= 0.0) || !(p->c_a >= 0.0) ||
+        !(p->rho_air_over_rho >= 0.0) || !std::isfinite(p->coriolis_f) || !std::isfinite(p->wind_x) ||
+        !std::isfinite(p->wind_y))
+        return fail(SWE_ERR_ARG, "physical or numerical parameter out of range");
+    if (p->precision != SWE_F32 && p->precision != SWE_F64) return fail(SWE_ERR_ARG, "precision");
+    if (p->mode != SWE_FUSED && p->mode != SWE_STAGED) return fail(SWE_ERR_ARG, "mode");
+    if (p->seg_h < 0 || p->seg_h > 32768 || p->tile_w < 0) return fail(SWE_ERR_ARG, "tiling");
+    if (p->tile_w != 0 && p->tile_w != TW) return fail(SWE_ERR_ARG, "tile_w must be 0 or 116");
+    swe_ctx* c = new (std::nothrow) swe_ctx();
+    if (!c) return fail(SWE_ERR_OOM, "context");
+    c->p = *p;
+    c->esz = p->precision == SWE_F64 ? 8 : 4;
+    c->pitch = ((p->nx + 2 * PAD + 31) / 32) * 32;
+    c->rows = p->ny + 2 * PAD;
+    c->plane = (size_t)c->pitch * c->rows * c->esz;
+    auto bail = [&](int code, const std::string& m) {
+        swe_destroy(c);
+        return fail(code, m);
+    };
+    if (cudaGetDevice(&c->dev) != cudaSuccess) return bail(SWE_ERR_CUDA, "no CUDA device");
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->dev) != cudaSuccess) return bail(SWE_ERR_CUDA, "device properties");
+    c->sm_count = prop.multiProcessorCount;
+    if (p->cuda_stream) {
+        c->st = (cudaStream_t)p->cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess)
+            return bail(SWE_ERR_CUDA, "stream creation");
+        c->own_stream = true;
+    }
+    for (int k = 0; k < 8; ++k) {
+        if (cudaMalloc(&c->f[k], c->plane) != cudaSuccess) return bail(SWE_ERR_OOM, "state allocation");
+        if (cudaMemsetAsync(c->f[k], 0, c->plane, c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "memset");
+    }
+    cudaError_t e = is64(c) ? launch_fill_bed<double>((double*)c->f[6], p->nx, p->ny, c->pitch, c->st)
+                            : launch_fill_bed<float>((float*)c->f[6], p->nx, p->ny, c->pitch, c->st);
+    if (e != cudaSuccess) return bail(SWE_ERR_CUDA, "fill bed");
+    if (cudaMalloc(&c->ctl, sizeof(Ctl)) != cudaSuccess) return bail(SWE_ERR_OOM, "control block");
+    if (cudaMemsetAsync(c->ctl, 0, sizeof(Ctl), c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "memset");
+    if (cudaMallocHost(&c->ctl_host, sizeof(Ctl)) != cudaSuccess) return bail(SWE_ERR_OOM, "pinned control block");
+    // occupancy of the fused kernel decides the tiling
+    c->occ = 1;
+    if (p->mode == SWE_FUSED) {
+        e = is64(c) ? prepare_fused<double>(&c->occ) : prepare_fused<float>(&c->occ);
+        if (e != cudaSuccess) return bail(SWE_ERR_CUDA, std::string("fused kernel setup: ") + cudaGetErrorString(e));
+        if (c->occ < 1) return bail(SWE_ERR_CUDA, "fused kernel does not fit on an SM");
+    }
+    choose_tiling(c);
+    const int staged_blocks = ((p->nx + 31) / 32) * ((p->ny + 7) / 8);
+    c->parts_cap = std::max(c->nitems, staged_blocks);
+    if (cudaMalloc(&c->parts, c->parts_cap * sizeof(Part)) != cudaSuccess ||
+        cudaMalloc(&c->parts2, c->parts_cap * sizeof(Part)) != cudaSuccess)
+        return bail(SWE_ERR_OOM, "partials");
+    cudaMemsetAsync(c->parts, 0, c->parts_cap * sizeof(Part), c->st);
+    cudaMemsetAsync(c->parts2, 0, c->parts_cap * sizeof(Part), c->st);
+    if (p->mode == SWE_STAGED) {
+        for (int k = 0; k < SF_COUNT; ++k) {
+            if (cudaMalloc(&c->scr[k], c->plane) != cudaSuccess) return bail(SWE_ERR_OOM, "staged intermediates");
+            if (cudaMemsetAsync(c->scr[k], 0, c->plane, c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "memset");
+        }
+    } else {
+        int rc = SWE_OK;
+        for (int b = 0; b < 2 && !rc; ++b) {
+            rc = encode_map(c, &c->tmH[b], c->f[3 * b]);
+            if (!rc) rc = encode_map(c, &c->tmQx[b], c->f[3 * b + 1]);
+            if (!rc) rc = encode_map(c, &c->tmQy[b], c->f[3 * b + 2]);
+        }
+        if (!rc) rc = encode_map(c, &c->tmB, c->f[6]);
+        if (!rc) rc = encode_map(c, &c->tmN, c->f[7]);
+        if (rc) {
+            std::string m = g_err;
+            return bail(rc, m);
+        }
+    }
+    c->h_b.assign((size_t)p->nx * p->ny, 0.0);
+    c->h_solid.assign((size_t)p->nx * p->ny, 0);
+    // empty source tables
+    c->nsrc = 0;
+    int rc = build_source_tables(c, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (rc) {
+        std::string m = g_err;
+        return bail(rc, m);
+    }
+    if (cudaStreamSynchronize(c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "initialisation");
+    *out = c;
+    return SWE_OK;
+}
+
+int swe_set_terrain(swe_ctx* c, const double* b, const double* n) {
+    if (!c || !b) return fail(SWE_ERR_ARG, "null argument");
+    const size_t N = (size_t)c->p.nx * c->p.ny;
+    if (!finite_all(b, N) || (n && !finite_all(n, N))) return fail(SWE_ERR_NONFINITE, "terrain not finite");
+    for (size_t k = 0; k < N; ++k)
+        if (std::fabs(b[k]) >= 1e20) return fail(SWE_ERR_ARG, "|b| must stay below 1e20");
+    CK(cudaSetDevice(c->dev));
+    int rc = upload_field(c, b, c->f[6]);
+    if (!rc && n) rc = upload_field(c, n, c->f[7]);
+    if (!rc && !n) CK(cudaMemsetAsync(c->f[7], 0, c->plane, c->st));
+    if (rc) return rc;
+    // keep the host copy before re-closing gates over it
+    CK(cudaStreamSynchronize(c->st));
+    std::memcpy(c->h_b.data(), b, N * sizeof(double));
+    std::vector<int> closed;
+    for (size_t k = 0; k < N; ++k)
+        if (c->h_solid[k]) closed.push_back((int)k);
+    rc = apply_beds(c, closed);
+    if (rc) return rc;
+    if (c->has_state) return state_speed(c);
+    return SWE_OK;
+}
+
+int swe_set_state(swe_ctx* c, const double* H, const double* Qx, const double* Qy, double t) {
+    if (!c || !H || !Qx || !Qy) return fail(SWE_ERR_ARG, "null argument");
+    const size_t N = (size_t)c->p.nx * c->p.ny;
+    (void)N;
+    if (!std::isfinite(t)) return fail(SWE_ERR_NONFINITE, "t not finite");
+    CK(cudaSetDevice(c->dev));
+    // the values are checked on the device while they are converted
+    Ctl h;
+    std::memset(&h, 0, sizeof(h));
+    h.t = t;
+    *c->ctl_host = h;
+    CK(cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
+    int rc = upload_field(c, H, c->f[0], &c->ctl->err, 1);
+    if (!rc) rc = upload_field(c, Qx, c->f[1], &c->ctl->err, 0);
+    if (!rc) rc = upload_field(c, Qy, c->f[2], &c->ctl->err, 0);
+    if (rc) return rc;
+    rc = read_ctl(c);
+    if (rc) return rc;
+    if (c->ctl_host->err) {
+        const unsigned e = c->ctl_host->err;
+        c->has_state = false;
+        if (e & 1u) return fail(SWE_ERR_NONFINITE, "state not finite (in FP64 or after conversion)");
+        return fail(SWE_ERR_ARG, "negative depth");
+    }
+    rc = state_speed(c);
+    if (rc) return rc;
+    c->has_state = true;
+    return SWE_OK;
+}
+
+int swe_set_sources(swe_ctx* c, int32_t n, const int32_t* ix, const int32_t* iy, const double* w,
+                    const double* vx, const double* vy, const int32_t* hy, int32_t nh, const double* tab) {
+    if (!c) return fail(SWE_ERR_ARG, "null context");
+    if (n < 0 || nh < 0 || nh > MAX_HYDRO) return fail(SWE_ERR_ARG, "source counts out of range");
+    if (n > 0 && (!ix || !iy || !w || !hy || !tab || nh < 1)) return fail(SWE_ERR_ARG, "null source array");
+    std::vector<int> cells;
+    for (int m = 0; m < n; ++m) {
+        if (ix[m] < 0 || ix[m] >= c->p.nx || iy[m] < 0 || iy[m] >= c->p.ny) return fail(SWE_ERR_ARG, "source outside grid");
+        if (hy[m] < 0 || hy[m] >= nh) return fail(SWE_ERR_ARG, "hydrograph index");
+        if (!std::isfinite(w[m]) || (vx && !std::isfinite(vx[m])) || (vy && !std::isfinite(vy[m])))
+            return fail(SWE_ERR_NONFINITE, "source values");
+        cells.push_back(iy[m] * c->p.nx + ix[m]);
+    }
+    std::sort(cells.begin(), cells.end());
+    if (std::adjacent_find(cells.begin(), cells.end()) != cells.end()) return fail(SWE_ERR_ARG, "duplicate source cell");
+    for (int r = 0; r < nh; ++r) {
+        const double* row = tab + 4 * r;
+        if (!(row[0] == 0.0 || row[0] == 1.0) || !std::isfinite(row[1]) || !std::isfinite(row[2]) ||
+            !std::isfinite(row[3]) || (row[0] == 0.0 && !(row[3] > 0.0)))
+            return fail(SWE_ERR_ARG, "hydrograph row");
+    }
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->st));
+    drop_graph(c);
+    cudaFree(c->d_scell); cudaFree(c->d_shydro); cudaFree(c->d_sw); cudaFree(c->d_svx); cudaFree(c->d_svy);
+    cudaFree(c->d_hydro);
+    c->d_scell = nullptr; c->d_shydro = nullptr; c->d_sw = nullptr; c->d_svx = nullptr; c->d_svy = nullptr;
+    c->d_hydro = nullptr;
+    c->nsrc = n;
+    c->nh = nh;
+    const size_t nn = std::max(1, n);
+    if (cudaMalloc(&c->d_scell, nn * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_shydro, nn * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&c->d_sw, nn * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_svx, nn * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_svy, nn * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_hydro, std::max(1, nh) * 4 * sizeof(double)) != cudaSuccess)
+        return fail(SWE_ERR_OOM, "source allocation");
+    if (n > 0) {
+        std::vector<int> pc(n);
+        std::vector<double> zx(n, 0.0);
+        for (int m = 0; m < n; ++m) pc[m] = (iy[m] + PAD) * c->pitch + (ix[m] + PAD);
+        CK(cudaMemcpy(c->d_scell, pc.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_shydro, hy, n * sizeof(int), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_sw, w, n * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_svx, vx ? vx : zx.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_svy, vy ? vy : zx.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(c->d_hydro, tab, nh * 4 * sizeof(double), cudaMemcpyHostToDevice));
+    }
+    return build_source_tables(c, ix, iy, w, vx, vy, hy);
+}
+
+int swe_set_solid(swe_ctx* c, int32_t n, const int32_t* ix, const int32_t* iy, const uint8_t* closed) {
+    if (!c) return fail(SWE_ERR_ARG, "null context");
+    if (n < 0 || (n > 0 && (!ix || !iy || !closed))) return fail(SWE_ERR_ARG, "gate arrays");
+    std::vector<int> cells;
+    for (int m = 0; m < n; ++m) {
+        if (ix[m] < 0 || ix[m] >= c->p.nx || iy[m] < 0 || iy[m] >= c->p.ny) return fail(SWE_ERR_ARG, "gate outside grid");
+        if (closed[m] > 1) return fail(SWE_ERR_ARG, "closed must be 0 or 1");
+    }
+    CK(cudaSetDevice(c->dev));
+    for (int m = 0; m < n; ++m) {
+        const int k = iy[m] * c->p.nx + ix[m];
+        c->h_solid[k] = closed[m];
+        cells.push_back(k);
+    }
+    int rc = apply_beds(c, cells);
+    if (rc) return rc;
+    if (c->has_state) return state_speed(c);
+    return SWE_OK;
+}
+
+int swe_step(swe_ctx* c, int32_t nsteps, double t_end, swe_step_info* info) {
+    if (!c) return fail(SWE_ERR_ARG, "null context");
+    if (nsteps < 0) return fail(SWE_ERR_ARG, "nsteps < 0");
+    if (!std::isfinite(t_end)) return fail(SWE_ERR_ARG, "t_end not finite");
+    if (!c->has_state) return fail(SWE_ERR_STATE, "swe_set_state has not been called");
+    CK(cudaSetDevice(c->dev));
+    CK(launch_set_tend(c->ctl, t_end, c->st));
+    if (c->p.mode == SWE_STAGED) {
+        for (int s = 0; s < nsteps; ++s) {
+            if (t_end > 0.0) {
+                int rc = read_ctl(c);
+                if (rc) return rc;
+                if (c->ctl_host->t >= t_end) break;
+            }
+            int rc = launch_one_step(c);
+            if (rc) return rc;
+        }
+    } else if (nsteps == 1) {
+        int rc = launch_one_step(c);
+        if (rc) return rc;
+    } else if (nsteps > 1) {
+        if (!c->gexec || c->gsteps != nsteps) {
+            drop_graph(c);
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+            int rc = SWE_OK;
+            for (int s = 0; s < nsteps && !rc; ++s) rc = launch_one_step(c);
+            cudaError_t e = cudaStreamEndCapture(c->st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(SWE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(SWE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            c->gsteps = nsteps;
+        }
+        CK(cudaGraphLaunch(c->gexec, c->st));
+    }
+    if (info) {
+        int rc = read_ctl(c);
+        if (rc) return rc;
+        const Ctl& h = *c->ctl_host;
+        info->t = h.t;
+        info->dt_last = h.tau_last;
+        info->mass = h.mass;
+        info->src_vol = h.src_vol;
+        info->clip_vol = h.clip_vol;
+        info->max_speed = h.max_speed;
+        info->wet_cells = h.wet;
+        info->step = h.step;
+        info->err_word = (int32_t)h.err;
+        info->pad = 0;
+        if (h.err & ERR_TIMEOUT) return fail(SWE_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
+        if (h.err & ERR_NONFINITE) return fail(SWE_ERR_NONFINITE, "non-finite signal speed or state");
+    }
+    return SWE_OK;
+}
+
+int swe_get_state(swe_ctx* c, double* H, double* Qx, double* Qy, double* t) {
+    if (!c) return fail(SWE_ERR_ARG, "null context");
+    if (!c->has_state) return fail(SWE_ERR_STATE, "no state");
+    CK(cudaSetDevice(c->dev));
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    const int buf = (int)(c->ctl_host->step & 1);
+    double* outs[3] = {H, Qx, Qy};
+    for (int k = 0; k < 3 && !rc; ++k)
+        if (outs[k]) rc = download_field(c, c->f[3 * buf + k], outs[k], c->p.nx, c->p.ny, 0);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->st));
+    if (t) *t = c->ctl_host->t;
+    return SWE_OK;
+}
+
+int swe_get_device_ptrs(swe_ctx* c, void** H, void** Qx, void** Qy, int64_t* pitch, int32_t* esz) {
+    if (!c) return fail(SWE_ERR_ARG, "null context");
+    CK(cudaSetDevice(c->dev));
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    const int buf = (int)(c->ctl_host->step & 1);
+    const size_t off = ((size_t)PAD * c->pitch + PAD) * c->esz;
+    if (H) *H = (char*)c->f[3 * buf + 0] + off;
+    if (Qx) *Qx = (char*)c->f[3 * buf + 1] + off;
+    if (Qy) *Qy = (char*)c->f[3 * buf + 2] + off;
+    if (pitch) *pitch = c->pitch;
+    if (esz) *esz = c->esz;
+    return SWE_OK;
+}
+
+int swe_get_stages(swe_ctx* c, double* const* out) {
+    if (!c || !out) return fail(SWE_ERR_ARG, "null argument");
+    if (c->p.mode != SWE_STAGED) return fail(SWE_ERR_STATE, "context is not in SWE_STAGED mode");
+    CK(cudaSetDevice(c->dev));
+    const int nx = c->p.nx, ny = c->p.ny;
+    int rc = ensure_staging(c, (size_t)(nx + 1) * (ny + 1) * sizeof(double));
+    if (rc) return rc;
+    // cell fields in the order of the header, then the face fluxes
+    const int order[20] = {SF_UX, SF_UY, SF_AX, SF_AY, SF_PHI, SF_USX, SF_USY, SF_HS, SF_AX2, SF_AY2,
+                           SF_PHI2, SF_UTX, SF_UTY, SF_UHX, SF_UHY, SF_HT, SF_QTX, SF_QTY, SF_UPX, SF_UPY};
+    for (int k = 0; k < 20 && !rc; ++k)
+        if (out[k]) rc = download_field(c, c->scr[order[k]], out[k], nx, ny, 0);
+    for (int q = 0; q < 3 && !rc; ++q) {
+        if (out[20]) rc = download_field(c, c->scr[SF_FX0 + q], out[20] + (size_t)q * ny * (nx + 1), nx + 1, ny, -1);
+        if (!rc && out[21])
+            rc = download_field(c, c->scr[SF_FY0 + q], out[21] + (size_t)q * (ny + 1) * nx, nx, ny + 1,
+                                -(long long)c->pitch);
+        if (!rc) CK(cudaStreamSynchronize(c->st));
+    }
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(c->st));
+    return SWE_OK;
+}
+
+int swe_sync(swe_ctx* c) {
+    if (!c) return fail(SWE_ERR_ARG, "null context");
+    CK(cudaStreamSynchronize(c->st));
+    return SWE_OK;
+}
+
+void swe_destroy(swe_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->dev);
+    if (c->st) cudaStreamSynchronize(c->st);
+    drop_graph(c);
+    for (void* q : c->f) cudaFree(q);
+    for (void* q : c->scr) cudaFree(q);
+    cudaFree(c->ctl);
+    if (c->ctl_host) cudaFreeHost(c->ctl_host);
+    cudaFree(c->parts);
+    cudaFree(c->parts2);
+    cudaFree(c->d_scell); cudaFree(c->d_shydro); cudaFree(c->d_sw); cudaFree(c->d_svx); cudaFree(c->d_svy);
+    cudaFree(c->d_hydro);
+    cudaFree(c->d_entries);
+    cudaFree(c->d_src_off);
+    cudaFree(c->staging);
+    cudaFree(c->d_tmp_i);
+    cudaFree(c->d_tmp_d);
+    if (c->own_stream && c->st) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+}  // extern "C"

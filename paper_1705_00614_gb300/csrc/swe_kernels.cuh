@@ -1,0 +1,957 @@
+// Kernels of one CSPH-TVD time step (Sec. 2.3; paper kernels K2-K8), as
+// templates over the arithmetic type.  swe_f32.cu and swe_f64.cu instantiate
+// them with different floating-point flags.
+//
+// Two organisations of the same arithmetic (swe_math.cuh):
+//  * k_fused: one launch per step.  A CTA owns a window of WIN = 128 columns
+//    (one thread per column) and streams down the rows of its segment.  Input
+//    rows (H, Qx, Qy, b, n) arrive by TMA in 4-row chunks into a 4-slot ring;
+//    every stage keeps the few rows its consumers need in shared-memory rings,
+//    so one pass over the rows runs the whole step with no intermediate in
+//    HBM.  Per row: primitives -> forces + predictor U* -> particle area H*
+//    -> forces at t_{n+1/2} + corrector + sources -> MUSCL slopes and face
+//    fluxes -> final update -> signal speed of the new state (the next step's
+//    K3, which needs one more row and column of the new state).  The
+//    dependence radius of all that is 6 cells, so a window produces its 116
+//    central columns and rows [6, 6 + seg_h) of its 12 + seg_h rows.
+//  * staged kernels: one kernel per stage with every intermediate in device
+//    memory (the paper's K2-K8 split); used for stage-by-stage comparison with
+//    the oracle and the per-stage time breakdown.
+#pragma once
+
+#include <float.h>
+
+#include "swe_launch.h"
+
+namespace swe {
+
+// ------------------------------------------------------------------ PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for a phase of an mbarrier, giving up after ~2 s.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (globaltimer_ns() - t0 > 2000000000ull) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            unsigned long long* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ------------------------------------------------------------------ time step
+
+__device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
+
+// tau_n from the max signal speed of the state at t_n (Fig. 2, K3).
+__device__ __forceinline__ double step_tau(const Ctl* ctl, const StepP& sp, int parity) {
+    double smax = __longlong_as_double((long long)ctl->smax[parity]);
+    double tau;
+    if (sp.dt_fixed > 0.0) tau = sp.dt_fixed;
+    else if (smax > 0.0) tau = dmin_(sp.dt_max, sp.cfl * sp.dx / smax);
+    else tau = sp.dt_max;
+    if (ctl->t_end > 0.0 && ctl->t + tau > ctl->t_end) tau = ctl->t_end - ctl->t;
+    return tau;
+}
+
+// ------------------------------------------------------------------ reductions
+
+__device__ __forceinline__ int lin_tid() { return threadIdx.x + threadIdx.y * blockDim.x; }
+
+// Sum over an NT-thread block in a fixed order (result valid in thread 0).
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int tid = lin_tid(), w = tid >> 5, l = tid & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (tid == 0)
+        for (int i = 0; i < NT / 32; ++i) r += red[i];
+    return r;
+}
+
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        double u = __shfl_down_sync(0xffffffffu, v, o);
+        v = (u > v || u != u) ? u : v;
+    }
+    const int tid = lin_tid(), w = tid >> 5, l = tid & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (tid == 0)
+        for (int i = 0; i < NT / 32; ++i) r = (red[i] > r || red[i] != red[i]) ? red[i] : r;
+    return r;
+}
+
+// ------------------------------------------------------------------ fused kernel
+
+template <class T>
+struct FSmem {
+    T in[NSLOT][5][RB][WIN];  // TMA ring: H, Qx, Qy, b, n
+    T pU[4][2][WIN];          // U at t_n
+    T aU[4][2][WIN];          // predictor U*
+    T bH[3][WIN];             // particle depth H*
+    T cS[3][7][WIN];          // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y
+    T fX[2][3][WIN];          // x-face fluxes F_H, F_Qx, F_Qy
+    T nS[3][3][WIN];          // new state H, Ux, Uy
+    unsigned long long bar[NSLOT];
+    double hq[MAX_HYDRO];
+    double red[WIN / 32];
+    double tau;
+    int last;
+};
+
+template <class T>
+size_t fused_smem_bytes() {
+    return sizeof(FSmem<T>) + 128;
+}
+
+template <class T>
+__device__ __forceinline__ void issue_chunk(FSmem<T>& s, const FusedArgs<T>& a, int buf, int ch,
+                                            int gx0, int gy0) {
+    const int slot = ch % NSLOT;
+    mbar_expect_tx(&s.bar[slot], 5u * RB * WIN * sizeof(T));
+    const int y = gy0 + ch * RB;
+    tma_load_2d(&s.in[slot][0][0][0], &a.tmH[buf], gx0, y, &s.bar[slot]);
+    tma_load_2d(&s.in[slot][1][0][0], &a.tmQx[buf], gx0, y, &s.bar[slot]);
+    tma_load_2d(&s.in[slot][2][0][0], &a.tmQy[buf], gx0, y, &s.bar[slot]);
+    tma_load_2d(&s.in[slot][3][0][0], &a.tmB, gx0, y, &s.bar[slot]);
+    tma_load_2d(&s.in[slot][4][0][0], &a.tmN, gx0, y, &s.bar[slot]);
+}
+
+template <class T>
+__global__ void __launch_bounds__(WIN, sizeof(T) == 4 ? 3 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    FSmem<T>& s = *reinterpret_cast<FSmem<T>*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const int c = threadIdx.x;
+    const int item = blockIdx.x;
+    const int strip = item % a.ntx, seg = item / a.ntx;
+    const int x0 = strip * TW, y0 = seg * a.seg_h;
+    const int tw = min(TW, a.g.nx - x0), sh = min(a.seg_h, a.g.ny - y0);
+    const int gx0 = PAD + x0 - HALO, gy0 = PAD + y0 - HALO;
+    const int nrows = sh + 2 * HALO;
+    const int nchunks = (nrows + RB - 1) / RB;
+    const long long step = *(volatile const long long*)&a.ctl->step;
+    const int buf = (int)(step & 1);
+    const Phys<T>& P = a.P;
+    const T eps = P.eps;
+
+    if (c == 0) {
+        s.tau = step_tau(a.ctl, a.sp, buf);
+#pragma unroll
+        for (int i = 0; i < NSLOT; ++i) mbar_init(&s.bar[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    const double tau = s.tau;
+    if (!(tau > 0.0)) return;  // t_end reached: every CTA skips the step
+    const T tauT = (T)tau;
+    const T th = T(0.5) * tauT;
+    const T dth = tauT / P.h;
+    if (c < a.nh) s.hq[c] = hydro_value(a.hydro + 4 * c, a.ctl->t + 0.5 * (double)tauT);
+    if (c == 0) issue_chunk(s, a, buf, 0, gx0, gy0);
+    __syncthreads();
+
+    T* const outH = a.g.H[buf ^ 1];
+    T* const outQx = a.g.Qx[buf ^ 1];
+    T* const outQy = a.g.Qy[buf ^ 1];
+    const bool out_col = (c >= HALO) && (c < HALO + tw);
+
+    auto inrow = [&](int f, int r) -> const T* { return s.in[(r / RB) % NSLOT][f][r % RB]; };
+
+    int sp = a.src_off[item];
+    const int se = a.src_off[item + 1];
+    T syPrev[5] = {T(0), T(0), T(0), T(0), T(0)};
+    T fyPrev[3] = {T(0), T(0), T(0)}, fyCur[3] = {T(0), T(0), T(0)};
+    double acc_mass = 0.0, acc_src = 0.0, acc_clip = 0.0, vmax = 0.0;
+    long long acc_wet = 0;
+    bool bad = false;
+
+    for (int k = 0; k <= nrows; ++k) {
+        if ((k % RB) == 0) {
+            const int ch = k / RB;
+            if (ch < nchunks) {
+                if (c == 0 && ch + 1 < nchunks) {
+                    fence_proxy_async();
+                    issue_chunk(s, a, buf, ch + 1, gx0, gy0);
+                }
+                const bool ok = mbar_wait_bounded(&s.bar[ch % NSLOT], (unsigned)((ch / NSLOT) & 1));
+                if (__syncthreads_or(!ok)) {
+                    if (c == 0) atomicOr(&a.ctl->err, (unsigned)ERR_TIMEOUT);
+                    return;
+                }
+            }
+        }
+        // (a) signal speed of the new state at row k-7; primitives at row k
+        {
+            const int r = k - 7;
+            if (r >= HALO && r < HALO + sh && out_col) {
+                const T* b0 = inrow(3, r);
+                const T* bm = inrow(3, r - 1);
+                const T* bp = inrow(3, r + 1);
+                const int i0 = r % 3, im = (r - 1) % 3, ip = (r + 1) % 3;
+                const T H = s.nS[i0][0][c], b = b0[c];
+                if (is_wet(H, b, eps)) {
+                    const T ux = s.nS[i0][1][c], uy = s.nS[i0][2][c];
+                    Nb<T> W{s.nS[i0][0][c - 1], b0[c - 1], s.nS[i0][1][c - 1], s.nS[i0][2][c - 1],
+                            is_wet(s.nS[i0][0][c - 1], b0[c - 1], eps)};
+                    Nb<T> E{s.nS[i0][0][c + 1], b0[c + 1], s.nS[i0][1][c + 1], s.nS[i0][2][c + 1],
+                            is_wet(s.nS[i0][0][c + 1], b0[c + 1], eps)};
+                    Nb<T> S{s.nS[im][0][c], bm[c], s.nS[im][1][c], s.nS[im][2][c],
+                            is_wet(s.nS[im][0][c], bm[c], eps)};
+                    Nb<T> N{s.nS[ip][0][c], bp[c], s.nS[ip][1][c], s.nS[ip][2][c],
+                            is_wet(s.nS[ip][0][c], bp[c], eps)};
+                    T ax, ay, phi;
+                    forces(P, H, b, inrow(4, r)[c], ux, uy, W, E, S, N, ax, ay, phi);
+                    const double v = (double)cell_speed(P, H, ux, uy, ax, ay);
+                    if (!(v <= DBL_MAX)) bad = true;
+                    else if (v > vmax) vmax = v;
+                }
+            }
+            if (k < nrows) {
+                const T H = inrow(0, k)[c];
+                const bool wet = is_wet(H, inrow(3, k)[c], eps);
+                s.pU[k & 3][0][c] = wet ? inrow(1, k)[c] / H : T(0);
+                s.pU[k & 3][1][c] = wet ? inrow(2, k)[c] / H : T(0);
+            }
+        }
+        __syncthreads();
+        // (b) forces at t_n and predictor velocity U* at row k-1
+        {
+            const int r = k - 1;
+            if (r >= 1 && r <= nrows - 2 && c >= 1 && c < WIN - 1) {
+                const T *H0 = inrow(0, r), *Hm = inrow(0, r - 1), *Hp = inrow(0, r + 1);
+                const T *b0 = inrow(3, r), *bm = inrow(3, r - 1), *bp = inrow(3, r + 1);
+                const T(*U0)[WIN] = s.pU[r & 3];
+                const T(*Um)[WIN] = s.pU[(r - 1) & 3];
+                const T(*Up)[WIN] = s.pU[(r + 1) & 3];
+                const T H = H0[c], b = b0[c];
+                T usx = T(0), usy = T(0);
+                if (is_wet(H, b, eps)) {
+                    Nb<T> W{H0[c - 1], b0[c - 1], U0[0][c - 1], U0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
+                    Nb<T> E{H0[c + 1], b0[c + 1], U0[0][c + 1], U0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
+                    Nb<T> S{Hm[c], bm[c], Um[0][c], Um[1][c], is_wet(Hm[c], bm[c], eps)};
+                    Nb<T> N{Hp[c], bp[c], Up[0][c], Up[1][c], is_wet(Hp[c], bp[c], eps)};
+                    T ax, ay, phi;
+                    forces(P, H, b, inrow(4, r)[c], U0[0][c], U0[1][c], W, E, S, N, ax, ay, phi);
+                    const T den = T(1) + th * phi;
+                    usx = (U0[0][c] + th * ax) / den;
+                    usy = (U0[1][c] + th * ay) / den;
+                }
+                s.aU[r & 3][0][c] = usx;
+                s.aU[r & 3][1][c] = usy;
+            }
+        }
+        __syncthreads();
+        // (c) particle area change and H* at row k-2
+        {
+            const int r = k - 2;
+            if (r >= 2 && r <= nrows - 3 && c >= 2 && c < WIN - 2) {
+                const T H = inrow(0, r)[c];
+                T hs = H;
+                if (is_wet(H, inrow(3, r)[c], eps)) {
+                    const T* Ax = s.aU[r & 3][0];
+                    const T* Ay = s.aU[r & 3][1];
+                    const T u = Ax[c], uW = Ax[c - 1], uE = Ax[c + 1];
+                    const T v = Ay[c], vS = s.aU[(r - 1) & 3][1][c], vN = s.aU[(r + 1) & 3][1][c];
+                    const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
+                    const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
+                    const T D = ((fxp - fxm) + (fyp - fym)) / P.h;
+                    hs = H / tmax(T(0.5), T(1) + th * D);
+                }
+                s.bH[r % 3][c] = hs;
+            }
+        }
+        __syncthreads();
+        // (d) forces at t_{n+1/2}, corrector and sources at row k-3
+        {
+            const int r = k - 3;
+            if (r >= 3 && r <= nrows - 4 && c >= 3 && c < WIN - 3) {
+                const T *H0 = inrow(0, r), *Hm = inrow(0, r - 1), *Hp = inrow(0, r + 1);
+                const T *b0 = inrow(3, r), *bm = inrow(3, r - 1), *bp = inrow(3, r + 1);
+                const T *B0 = s.bH[r % 3], *Bm = s.bH[(r - 1) % 3], *Bp = s.bH[(r + 1) % 3];
+                const T(*A0)[WIN] = s.aU[r & 3];
+                const T(*Am)[WIN] = s.aU[(r - 1) & 3];
+                const T(*Ap)[WIN] = s.aU[(r + 1) & 3];
+                const T H = H0[c], b = b0[c];
+                const T ux = s.pU[r & 3][0][c], uy = s.pU[r & 3][1][c];
+                T utx = T(0), uty = T(0);
+                if (is_wet(H, b, eps)) {
+                    Nb<T> W{B0[c - 1], b0[c - 1], A0[0][c - 1], A0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
+                    Nb<T> E{B0[c + 1], b0[c + 1], A0[0][c + 1], A0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
+                    Nb<T> S{Bm[c], bm[c], Am[0][c], Am[1][c], is_wet(Hm[c], bm[c], eps)};
+                    Nb<T> N{Bp[c], bp[c], Ap[0][c], Ap[1][c], is_wet(Hp[c], bp[c], eps)};
+                    T ax, ay, phi;
+                    forces(P, B0[c], b, inrow(4, r)[c], A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
+                    const T den = T(1) + tauT * phi;
+                    utx = (ux + tauT * ax) / den;
+                    uty = (uy + tauT * ay) / den;
+                }
+                const T uhx = T(0.5) * (ux + utx), uhy = T(0.5) * (uy + uty);
+                T sig = T(0), vx = T(0), vy = T(0);
+                while (sp < se && a.src[sp].r < r) ++sp;
+                for (int q = sp; q < se && a.src[q].r == r; ++q) {
+                    if (a.src[q].c == c) {
+                        sig = (T)(a.src[q].w * s.hq[a.src[q].hydro]);
+                        vx = (T)a.src[q].vx;
+                        vy = (T)a.src[q].vy;
+                    }
+                }
+                const T ts = tauT * sig;
+                const T ht = tmax(T(0), H + ts);
+                const T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
+                const T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
+                const bool wt = is_wet(ht, b, eps);
+                T(*C)[WIN] = s.cS[r % 3];
+                C[0][c] = ht;
+                C[1][c] = uhx;
+                C[2][c] = uhy;
+                C[3][c] = wt ? qtx / ht : T(0);
+                C[4][c] = wt ? qty / ht : T(0);
+                C[5][c] = qtx;
+                C[6][c] = qty;
+                if (out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
+            }
+        }
+        __syncthreads();
+        // (e) MUSCL slopes and face fluxes at row k-4 (y face below it)
+        {
+            const int r = k - 4;
+            auto ecell = [&](int rr, int col) {
+                ECell<T> e;
+                const T ht = s.cS[rr % 3][0][col];
+                const T bb = inrow(3, rr)[col];
+                e.w[0] = ht;
+                e.w[1] = s.cS[rr % 3][1][col];
+                e.w[2] = s.cS[rr % 3][2][col];
+                e.w[3] = s.cS[rr % 3][3][col];
+                e.w[4] = s.cS[rr % 3][4][col];
+                e.b = bb;
+                e.wt = is_wet(ht, bb, eps);
+                return e;
+            };
+            if (r >= 4 && r <= nrows - 5 && c >= 3 && c < WIN - 3) {
+                const ECell<T> em = ecell(r - 1, c), e0 = ecell(r, c), ep = ecell(r + 1, c);
+                T syc[5];
+                slopes(em, e0, ep, syc);
+                if (r >= 5) face_flux(P, em, syPrev, e0, syc, 2, fyCur[0], fyCur[1], fyCur[2]);
+#pragma unroll
+                for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
+                if (r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 6) {
+                    const ECell<T> xm = ecell(r, c - 1), x1 = ecell(r, c + 1), x2 = ecell(r, c + 2);
+                    T sL[5], sR[5];
+                    slopes(xm, e0, x1, sL);
+                    slopes(e0, x1, x2, sR);
+                    T FH, FQx, FQy;
+                    face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
+                    s.fX[r & 1][0][c] = FH;
+                    s.fX[r & 1][1][c] = FQx;
+                    s.fX[r & 1][2][c] = FQy;
+                }
+            }
+        }
+        __syncthreads();
+        // (f) final update at row k-5 (K8)
+        {
+            const int r = k - 5;
+            if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
+                const T(*FX)[WIN] = s.fX[r & 1];
+                const T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
+                const T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
+                const T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
+                const T(*C)[WIN] = s.cS[r % 3];
+                T hn = C[0][c] + dth * fh;
+                double clip = 0.0;
+                if (hn < T(0)) {
+                    clip = -(double)hn;
+                    hn = T(0);
+                }
+                T qxn = T(0), qyn = T(0);
+                if (hn > eps) {
+                    qxn = C[5][c] + dth * fqx;
+                    qyn = C[6][c] + dth * fqy;
+                }
+                const T b = inrow(3, r)[c];
+                const bool wetn = is_wet(hn, b, eps);
+                s.nS[r % 3][0][c] = hn;
+                s.nS[r % 3][1][c] = wetn ? qxn / hn : T(0);
+                s.nS[r % 3][2][c] = wetn ? qyn / hn : T(0);
+                if (out_col && r >= HALO && r < HALO + sh) {
+                    const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
+                    outH[gi] = hn;
+                    outQx[gi] = qxn;
+                    outQy[gi] = qyn;
+                    acc_mass += (double)hn;
+                    acc_clip += clip;
+                    acc_wet += wetn ? 1 : 0;
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < 3; ++q) fyPrev[q] = fyCur[q];
+        }
+        __syncthreads();
+    }
+
+    // per-CTA partials, the next step's signal speed, and the step report
+    const double bmax = block_max<WIN>(vmax, s.red);
+    const double bmass = block_sum<WIN>(acc_mass, s.red);
+    const double bsrc = block_sum<WIN>(acc_src, s.red);
+    const double bclip = block_sum<WIN>(acc_clip, s.red);
+    const double bwet = block_sum<WIN>((double)acc_wet, s.red);
+    const int anybad = __syncthreads_or(bad);
+    if (c == 0) {
+        Part p;
+        p.mass = bmass;
+        p.src = bsrc;
+        p.clip = bclip;
+        p.wet = (long long)bwet;
+        a.parts[item] = p;
+        if (anybad) atomicOr(&a.ctl->err, (unsigned)ERR_NONFINITE);
+        atomicMax(&a.ctl->smax[buf ^ 1], (unsigned long long)__double_as_longlong(bmax));
+        __threadfence();
+        const unsigned ticket = atomicAdd(&a.ctl->done, 1u);
+        s.last = (ticket == (unsigned)a.nitems - 1u);
+    }
+    __syncthreads();
+    if (s.last) {
+        __threadfence();
+        double m = 0.0, sr = 0.0, cl = 0.0, w = 0.0;
+        for (int i = c; i < a.nitems; i += WIN) {
+            m += __ldcg(&a.parts[i].mass);
+            sr += __ldcg(&a.parts[i].src);
+            cl += __ldcg(&a.parts[i].clip);
+            w += (double)__ldcg(&a.parts[i].wet);
+        }
+        m = block_sum<WIN>(m, s.red);
+        sr = block_sum<WIN>(sr, s.red);
+        cl = block_sum<WIN>(cl, s.red);
+        w = block_sum<WIN>(w, s.red);
+        if (c == 0) {
+            const double h = (double)P.h;
+            Ctl* ctl = a.ctl;
+            ctl->mass = m * h * h;
+            ctl->src_vol = sr * h * h;
+            ctl->clip_vol = cl * h * h;
+            ctl->wet = (long long)w;
+            ctl->tau_last = (double)tauT;
+            ctl->t = ctl->t + (double)tauT;
+            ctl->max_speed = __longlong_as_double((long long)atomicAdd(&ctl->smax[buf ^ 1], 0ull));
+            ctl->smax[buf] = 0ull;
+            ctl->step = step + 1;
+            ctl->done = 0u;
+            __threadfence();
+        }
+    }
+}
+
+// Opt the fused kernel into its shared-memory size; returns CTAs per SM.
+template <class T>
+cudaError_t prepare_fused(int* ctas_per_sm) {
+    const size_t smem = fused_smem_bytes<T>();
+    cudaError_t e = cudaFuncSetAttribute(k_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fused<T>, WIN, smem);
+}
+
+template <class T>
+cudaError_t launch_fused(const FusedArgs<T>& a, cudaStream_t st) {
+    k_fused<T><<<a.nitems, WIN, fused_smem_bytes<T>(), st>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ staged kernels
+
+template <class T>
+struct PAcc {
+    int pitch;
+    __device__ __forceinline__ size_t operator()(int i, int j) const {
+        return (size_t)(j + PAD) * (size_t)pitch + (size_t)(i + PAD);
+    }
+};
+
+__device__ __forceinline__ int ctl_buf(const Ctl* ctl) {
+    return (int)(*(volatile const long long*)&ctl->step & 1);
+}
+
+template <class T>
+__device__ __forceinline__ Nb<T> nb_at(const StagedArgs<T>& a, const T* Hwet, const T* hs, const T* ux,
+                                       const T* uy, size_t k) {
+    Nb<T> n;
+    n.hs = hs[k];
+    n.b = a.g.b[k];
+    n.ux = ux[k];
+    n.uy = uy[k];
+    n.wet = is_wet(Hwet[k], n.b, a.P.eps);
+    return n;
+}
+
+template <class T>
+__global__ void ks_prim(const StagedArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.g.nx || j >= a.g.ny) return;
+    const int buf = ctl_buf(a.ctl);
+    const size_t k = PAcc<T>{a.g.pitch}(i, j);
+    const T H = a.g.H[buf][k];
+    const bool wet = is_wet(H, a.g.b[k], a.P.eps);
+    a.ux[k] = wet ? a.g.Qx[buf][k] / H : T(0);
+    a.uy[k] = wet ? a.g.Qy[buf][k] / H : T(0);
+}
+
+// forces from depth hs and velocity (ux, uy); wet mask of the state at t_n
+template <class T>
+__global__ void ks_forces(const StagedArgs<T> a, int second) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.g.nx || j >= a.g.ny) return;
+    const int buf = ctl_buf(a.ctl);
+    const PAcc<T> at{a.g.pitch};
+    const size_t k = at(i, j);
+    const T* Hw = a.g.H[buf];
+    const T* hs = second ? a.hs : Hw;
+    const T* ux = second ? a.usx : a.ux;
+    const T* uy = second ? a.usy : a.uy;
+    T* ax = second ? a.ax2 : a.ax;
+    T* ay = second ? a.ay2 : a.ay;
+    T* phi = second ? a.phi2 : a.phi;
+    if (!is_wet(Hw[k], a.g.b[k], a.P.eps)) {
+        ax[k] = T(0); ay[k] = T(0); phi[k] = T(0);
+        return;
+    }
+    const Nb<T> W = nb_at(a, Hw, hs, ux, uy, at(i - 1, j)), E = nb_at(a, Hw, hs, ux, uy, at(i + 1, j));
+    const Nb<T> S = nb_at(a, Hw, hs, ux, uy, at(i, j - 1)), N = nb_at(a, Hw, hs, ux, uy, at(i, j + 1));
+    T fx, fy, fp;
+    forces(a.P, hs[k], a.g.b[k], a.g.n[k], ux[k], uy[k], W, E, S, N, fx, fy, fp);
+    ax[k] = fx; ay[k] = fy; phi[k] = fp;
+}
+
+template <class T>
+__global__ void ks_predict(const StagedArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.g.nx || j >= a.g.ny) return;
+    const int buf = ctl_buf(a.ctl);
+    const T tauT = (T)step_tau(a.ctl, a.sp, buf);
+    const T th = T(0.5) * tauT;
+    const size_t k = PAcc<T>{a.g.pitch}(i, j);
+    T usx = T(0), usy = T(0);
+    if (is_wet(a.g.H[buf][k], a.g.b[k], a.P.eps)) {
+        const T den = T(1) + th * a.phi[k];
+        usx = (a.ux[k] + th * a.ax[k]) / den;
+        usy = (a.uy[k] + th * a.ay[k]) / den;
+    }
+    a.usx[k] = usx;
+    a.usy[k] = usy;
+}
+
+template <class T>
+__global__ void ks_hstar(const StagedArgs<T> a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= a.g.nx || j >= a.g.ny) return;
+    const int buf = ctl_buf(a.ctl);
+    const T tauT = (T)step_tau(a.ctl, a.sp, buf);
+    const T th = T(0.5) * tauT;
+    const PAcc<T> at{a.g.pitch};
+    const size_t k = at(i, j);
+    const T H = a.g.H[buf][k];
+    T hs = H;
+    if (is_wet(H, a.g.b[k], a.P.eps)) {
+        const T u = a.usx[k], uW = a.usx[at(i - 1, j)], uE = a.usx[at(i + 1, j)];
+        const T v = a.usy[k], vS = a.usy[at(i, j - 1)], vN = a.usy[at(i, j + 1)];
+        const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
+        const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
+        const T D = ((fxp - fxm) + (fyp - fym)) / a.P.h;
+        hs = H / tmax(T(0.5), T(1) + th * D);
+    }
+    a.hs[k] = hs;
+}
+
+template <class T>
+__global__ void ks_sources(const StagedArgs<T> a) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= a.nsrc) return;
+    const int buf = ctl_buf(a.ctl);
+    const T tauT = (T)step_tau(a.ctl, a.sp, buf);
+    const double q = hydro_value(a.hydro + 4 * a.s_hydro[m], a.ctl->t + 0.5 * (double)tauT);
+    const int k = a.s_cell[m];
+    a.sig[k] = (T)(a.s_w[m] * q);
+    a.svx[k] = (T)a.s_vx[m];
+    a.svy[k] = (T)a.s_vy[m];
+}
+
+template <class T>
+__global__ void ks_correct(const StagedArgs<T> a) {
+    __shared__ double red[8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    double src = 0.0;
+    if (i < a.g.nx && j < a.g.ny) {
+        const int buf = ctl_buf(a.ctl);
+        const T tauT = (T)step_tau(a.ctl, a.sp, buf);
+        const size_t k = PAcc<T>{a.g.pitch}(i, j);
+        const T H = a.g.H[buf][k], b = a.g.b[k];
+        T utx = T(0), uty = T(0);
+        if (is_wet(H, b, a.P.eps)) {
+            const T den = T(1) + tauT * a.phi2[k];
+            utx = (a.ux[k] + tauT * a.ax2[k]) / den;
+            uty = (a.uy[k] + tauT * a.ay2[k]) / den;
+        }
+        a.utx[k] = utx;
+        a.uty[k] = uty;
+        a.uhx[k] = T(0.5) * (a.ux[k] + utx);
+        a.uhy[k] = T(0.5) * (a.uy[k] + uty);
+        const T sig = a.sig[k];
+        const T ts = tauT * sig;
+        const T ht = tmax(T(0), H + ts);
+        const T qtx = H * utx + (sig > T(0) ? ts * a.svx[k] : ts * utx);
+        const T qty = H * uty + (sig > T(0) ? ts * a.svy[k] : ts * uty);
+        const bool wt = is_wet(ht, b, a.P.eps);
+        a.ht[k] = ht;
+        a.qtx[k] = qtx;
+        a.qty[k] = qty;
+        a.upx[k] = wt ? qtx / ht : T(0);
+        a.upy[k] = wt ? qty / ht : T(0);
+        src = (double)ht - (double)H;
+    }
+    const double s = block_sum<256>(src, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) a.parts2[blockIdx.y * gridDim.x + blockIdx.x].src = s;
+}
+
+template <class T>
+__device__ __forceinline__ ECell<T> ecell_at(const StagedArgs<T>& a, size_t k) {
+    ECell<T> e;
+    const T ht = a.ht[k], bb = a.g.b[k];
+    e.w[0] = ht;
+    e.w[1] = a.uhx[k];
+    e.w[2] = a.uhy[k];
+    e.w[3] = a.upx[k];
+    e.w[4] = a.upy[k];
+    e.b = bb;
+    e.wt = is_wet(ht, bb, a.P.eps);
+    return e;
+}
+
+// fluxes of the faces i+1/2 (dir 0, i in [-1, nx-1]) or j+1/2 (dir 1)
+template <class T>
+__global__ void ks_flux(const StagedArgs<T> a, int dir) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x - (dir == 0 ? 1 : 0);
+    const int j = blockIdx.y * blockDim.y + threadIdx.y - (dir == 1 ? 1 : 0);
+    if (i >= a.g.nx || j >= a.g.ny) return;
+    const PAcc<T> at{a.g.pitch};
+    const int di = dir == 0 ? 1 : 0, dj = dir == 1 ? 1 : 0;
+    const ECell<T> l2 = ecell_at(a, at(i - di, j - dj)), l = ecell_at(a, at(i, j));
+    const ECell<T> r = ecell_at(a, at(i + di, j + dj)), r2 = ecell_at(a, at(i + 2 * di, j + 2 * dj));
+    T sL[5], sR[5];
+    slopes(l2, l, r, sL);
+    slopes(l, r, r2, sR);
+    T FH, FQx, FQy;
+    face_flux(a.P, l, sL, r, sR, dir == 0 ? 1 : 2, FH, FQx, FQy);
+    T* const* f = dir == 0 ? a.fx : a.fy;
+    const size_t k = at(i, j);
+    f[0][k] = FH;
+    f[1][k] = FQx;
+    f[2][k] = FQy;
+}
+
+template <class T>
+__global__ void ks_final(const StagedArgs<T> a) {
+    __shared__ double red[8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    double mass = 0.0, clip = 0.0, wet = 0.0;
+    if (i < a.g.nx && j < a.g.ny) {
+        const int buf = ctl_buf(a.ctl);
+        const T tauT = (T)step_tau(a.ctl, a.sp, buf);
+        const T dth = tauT / a.P.h;
+        const PAcc<T> at{a.g.pitch};
+        const size_t k = at(i, j), kw = at(i - 1, j), ks = at(i, j - 1);
+        const T fh = (a.fx[0][kw] - a.fx[0][k]) + (a.fy[0][ks] - a.fy[0][k]);
+        const T fqx = (a.fx[1][kw] - a.fx[1][k]) + (a.fy[1][ks] - a.fy[1][k]);
+        const T fqy = (a.fx[2][kw] - a.fx[2][k]) + (a.fy[2][ks] - a.fy[2][k]);
+        T hn = a.ht[k] + dth * fh;
+        if (hn < T(0)) {
+            clip = -(double)hn;
+            hn = T(0);
+        }
+        T qxn = T(0), qyn = T(0);
+        if (hn > a.P.eps) {
+            qxn = a.qtx[k] + dth * fqx;
+            qyn = a.qty[k] + dth * fqy;
+        }
+        a.g.H[buf ^ 1][k] = hn;
+        a.g.Qx[buf ^ 1][k] = qxn;
+        a.g.Qy[buf ^ 1][k] = qyn;
+        mass = (double)hn;
+        wet = is_wet(hn, a.g.b[k], a.P.eps) ? 1.0 : 0.0;
+    }
+    const int bl = blockIdx.y * gridDim.x + blockIdx.x;
+    const double m = block_sum<256>(mass, red);
+    const double c = block_sum<256>(clip, red);
+    const double w = block_sum<256>(wet, red);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        a.parts[bl].mass = m;
+        a.parts[bl].clip = c;
+        a.parts[bl].wet = (long long)w;
+    }
+}
+
+// Signal speed (and mass) of the state in buffer `which` (0: current,
+// 1: next); atomicMax into the smax slot of that state's step parity.
+template <class T>
+__global__ void ks_speed(const StagedArgs<T> a, int which) {
+    __shared__ double red[8];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int buf = ctl_buf(a.ctl) ^ which;
+    double v = 0.0, mass = 0.0, wet = 0.0;
+    bool bad = false;
+    if (i < a.g.nx && j < a.g.ny) {
+        const PAcc<T> at{a.g.pitch};
+        const T* Hs = a.g.H[buf];
+        const T* Qx = a.g.Qx[buf];
+        const T* Qy = a.g.Qy[buf];
+        const T eps = a.P.eps;
+        auto nb = [&](size_t k) {
+            Nb<T> n;
+            n.hs = Hs[k];
+            n.b = a.g.b[k];
+            n.wet = is_wet(n.hs, n.b, eps);
+            n.ux = n.wet ? Qx[k] / n.hs : T(0);
+            n.uy = n.wet ? Qy[k] / n.hs : T(0);
+            return n;
+        };
+        const size_t k = at(i, j);
+        const Nb<T> C = nb(k);
+        mass = (double)C.hs;
+        if (C.wet) {
+            wet = 1.0;
+            T ax, ay, phi;
+            forces(a.P, C.hs, C.b, a.g.n[k], C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)), nb(at(i, j - 1)),
+                   nb(at(i, j + 1)), ax, ay, phi);
+            v = (double)cell_speed(a.P, C.hs, C.ux, C.uy, ax, ay);
+            if (!(v <= DBL_MAX)) {
+                bad = true;
+                v = 0.0;
+            }
+        }
+        if (!(mass <= DBL_MAX) || !(mass >= 0.0)) bad = true;
+    }
+    const double bm = block_max<256>(v, red);
+    const double bs = block_sum<256>(mass, red);
+    const double bw = block_sum<256>(wet, red);
+    const int anybad = __syncthreads_or(bad);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const int bl = blockIdx.y * gridDim.x + blockIdx.x;
+        const int slot = (int)((*(volatile const long long*)&a.ctl->step + which) & 1);
+        atomicMax(&a.ctl->smax[slot], (unsigned long long)__double_as_longlong(bm));
+        if (anybad) atomicOr(&a.ctl->err, (unsigned)ERR_NONFINITE);
+        if (which == 0) {
+            a.parts[bl].mass = bs;
+            a.parts[bl].wet = (long long)bw;
+        }
+    }
+}
+
+// Reduce the partials of a staged step (fixed order) and advance the control
+// block; with init != 0 only report the mass of the current state.
+template <class T>
+__global__ void ks_finish(const StagedArgs<T> a, int nblocks, int init) {
+    __shared__ double red[8];
+    double m = 0.0, sr = 0.0, cl = 0.0, w = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += 256) {
+        m += a.parts[i].mass;
+        w += (double)a.parts[i].wet;
+        if (!init) {
+            sr += a.parts2[i].src;
+            cl += a.parts[i].clip;
+        }
+    }
+    m = block_sum<256>(m, red);
+    sr = block_sum<256>(sr, red);
+    cl = block_sum<256>(cl, red);
+    w = block_sum<256>(w, red);
+    if (threadIdx.x == 0) {
+        Ctl* ctl = a.ctl;
+        const double h = (double)a.P.h;
+        ctl->mass = m * h * h;
+        ctl->wet = (long long)w;
+        if (!init) {
+            const int buf = (int)(ctl->step & 1);
+            const T tauT = (T)step_tau(ctl, a.sp, buf);
+            ctl->src_vol = sr * h * h;
+            ctl->clip_vol = cl * h * h;
+            ctl->tau_last = (double)tauT;
+            ctl->t = ctl->t + (double)tauT;
+            ctl->max_speed = __longlong_as_double((long long)ctl->smax[buf ^ 1]);
+            ctl->smax[buf] = 0ull;
+            ctl->step = ctl->step + 1;
+        } else {
+            ctl->max_speed = __longlong_as_double((long long)ctl->smax[ctl->step & 1]);
+        }
+    }
+}
+
+template <class T>
+cudaError_t launch_staged(const StagedArgs<T>& a, cudaStream_t st) {
+    const dim3 blk(32, 8);
+    const dim3 grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+    const dim3 grdx((a.g.nx + 1 + 31) / 32, (a.g.ny + 7) / 8);
+    const dim3 grdy((a.g.nx + 31) / 32, (a.g.ny + 1 + 7) / 8);
+    const int nblocks = (int)(grd.x * grd.y);
+    const size_t plane = (size_t)a.g.pitch * (size_t)(a.g.ny + 2 * PAD) * sizeof(T);
+    ks_prim<T><<<grd, blk, 0, st>>>(a);
+    ks_forces<T><<<grd, blk, 0, st>>>(a, 0);
+    ks_predict<T><<<grd, blk, 0, st>>>(a);
+    ks_hstar<T><<<grd, blk, 0, st>>>(a);
+    ks_forces<T><<<grd, blk, 0, st>>>(a, 1);
+    cudaMemsetAsync(a.sig, 0, plane, st);
+    cudaMemsetAsync(a.svx, 0, plane, st);
+    cudaMemsetAsync(a.svy, 0, plane, st);
+    if (a.nsrc > 0) ks_sources<T><<<(a.nsrc + 127) / 128, 128, 0, st>>>(a);
+    ks_correct<T><<<grd, blk, 0, st>>>(a);
+    ks_flux<T><<<grdx, blk, 0, st>>>(a, 0);
+    ks_flux<T><<<grdy, blk, 0, st>>>(a, 1);
+    ks_final<T><<<grd, blk, 0, st>>>(a);
+    ks_speed<T><<<grd, blk, 0, st>>>(a, 1);
+    ks_finish<T><<<1, 256, 0, st>>>(a, nblocks, 0);
+    return cudaGetLastError();
+}
+
+static __global__ void k_zero_cur_slot(Ctl* ctl) { ctl->smax[ctl->step & 1] = 0ull; }
+
+template <class T>
+cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st) {
+    const dim3 blk(32, 8);
+    const dim3 grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+    k_zero_cur_slot<<<1, 1, 0, st>>>(a.ctl);
+    ks_speed<T><<<grd, blk, 0, st>>>(a, 0);
+    ks_finish<T><<<1, 256, 0, st>>>(a, (int)(grd.x * grd.y), 1);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ host copies
+
+// FP64 host layout -> padded field.  With flag != nullptr, values that are
+// not finite (bit 0) or negative (bit 1, when check_neg) are reported there.
+template <class T>
+__global__ void k_pack(const double* __restrict__ src, T* __restrict__ dst, int nx, int ny, int pitch,
+                       unsigned* flag, int check_neg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i < nx) {
+        const double v = src[(size_t)j * nx + i];
+        dst[(size_t)(j + PAD) * pitch + (i + PAD)] = (T)v;
+        if (flag) {
+            const T tv = (T)v;
+            unsigned bad = (!(fabs(v) <= DBL_MAX) || !(fabs((double)tv) <= DBL_MAX) || !(tv == tv) ||
+                            isinf((double)tv)) ? 1u : 0u;
+            if (check_neg && v < 0.0) bad |= 2u;
+            if (__any_sync(__activemask(), bad != 0) && bad) atomicOr(flag, bad);
+        }
+    }
+}
+
+template <class T>
+__global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, int nx, int ny, int pitch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i < nx) dst[(size_t)j * nx + i] = (double)src[(size_t)(j + PAD) * pitch + (i + PAD)];
+}
+
+// Bed of the padded layout: walls outside the interior, 0 inside.
+template <class T>
+__global__ void k_fill_bed(T* b, int nx, int ny, int pitch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= pitch) return;
+    const bool inside = i >= PAD && i < nx + PAD && j >= PAD && j < ny + PAD;
+    b[(size_t)j * pitch + i] = inside ? T(0) : T(WALL_BED);
+}
+
+template <class T>
+cudaError_t launch_fill_bed(T* b, int nx, int ny, int pitch, cudaStream_t st) {
+    k_fill_bed<T><<<dim3((pitch + 255) / 256, ny + 2 * PAD), 256, 0, st>>>(b, nx, ny, pitch);
+    return cudaGetLastError();
+}
+
+template <class T>
+__global__ void k_scatter(T* dst, const int* idx, const double* val, int n) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m < n) dst[idx[m]] = (T)val[m];
+}
+
+template <class T>
+cudaError_t launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cudaStream_t st, unsigned* flag,
+                        int check_neg) {
+    k_pack<T><<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(src, dst, nx, ny, pitch, flag, check_neg);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_unpack(const T* src, double* dst, int nx, int ny, int pitch, cudaStream_t st) {
+    k_unpack<T><<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(src, dst, nx, ny, pitch);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_scatter<T><<<(n + 127) / 128, 128, 0, st>>>(dst, idx, val, n);
+    return cudaGetLastError();
+}
+
+#define SWE_INSTANTIATE(T)                                                                           \
+    template cudaError_t launch_fused<T>(const FusedArgs<T>&, cudaStream_t);                         \
+    template cudaError_t prepare_fused<T>(int*);                                                     \
+    template cudaError_t launch_staged<T>(const StagedArgs<T>&, cudaStream_t);                       \
+    template cudaError_t launch_state_speed<T>(const StagedArgs<T>&, cudaStream_t);                  \
+    template cudaError_t launch_pack<T>(const double*, T*, int, int, int, cudaStream_t, unsigned*, int); \
+    template cudaError_t launch_unpack<T>(const T*, double*, int, int, int, cudaStream_t);           \
+    template cudaError_t launch_scatter<T>(T*, const int*, const double*, int, cudaStream_t);        \
+    template cudaError_t launch_fill_bed<T>(T*, int, int, int, cudaStream_t);                        \
+    template size_t fused_smem_bytes<T>();
+
+}  // namespace swe

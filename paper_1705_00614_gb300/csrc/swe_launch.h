@@ -1,0 +1,136 @@
+// Types shared by the host API (swe_capi.cu) and the kernel units
+// (swe_f32.cu, swe_f64.cu), and the launch functions the kernel units export.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "swe_math.cuh"
+
+namespace swe {
+
+// Ring of wall cells around every grid (>= the 6-cell dependence radius of
+// one fused step; 10 keeps every TMA box start 16-byte aligned).
+constexpr int PAD = 10;
+// Fused kernel geometry: a CTA owns a window of WIN columns (one thread per
+// column) and streams it down the rows of its segment; HALO columns on each
+// side are recomputed, so TW = WIN - 2 HALO columns are produced.
+constexpr int WIN = 128;
+constexpr int HALO = 6;
+constexpr int TW = WIN - 2 * HALO;
+constexpr int RB = 4;      // rows per TMA chunk
+constexpr int NSLOT = 4;   // chunk slots in shared memory
+constexpr int MAX_HYDRO = 32;
+
+enum ErrBits : unsigned int {
+    ERR_NONFINITE = 1u,
+    ERR_TIMEOUT = 2u,
+};
+
+// Device control block of one grid.
+struct Ctl {
+    double t;          // time at the start of the next step
+    double t_end;      // > 0: clamp
+    double tau_last;   // tau of the last completed step
+    double mass, src_vol, clip_vol, max_speed;  // report of the last completed step
+    long long wet;
+    long long step;    // steps since the state was set
+    unsigned long long smax[2];  // max signal speed (FP64 bits) for the step of that parity
+    unsigned int done;           // CTAs finished in the running step
+    unsigned int err;            // ErrBits
+};
+
+// Per-CTA partial sums of one step (reduced in a fixed order).
+struct Part {
+    double mass, src, clip;
+    long long wet;
+};
+
+// One source cell as seen by one work item (window coordinates).
+struct SrcEntry {
+    short r, c;     // window row and column
+    int hydro;
+    double w, vx, vy;
+};
+
+// Numerical step parameters (FP64, as the time step is formed in FP64).
+struct StepP {
+    double dx, cfl, dt_max, dt_fixed;
+};
+
+template <class T>
+struct Grid {
+    int nx, ny, pitch;   // interior size, row pitch in elements
+    T* H[2];             // padded arrays, pointing at padded (0, 0)
+    T* Qx[2];
+    T* Qy[2];
+    T* b;
+    T* n;
+};
+
+template <class T>
+struct FusedArgs {
+    CUtensorMap tmH[2], tmQx[2], tmQy[2], tmB, tmN;
+    Grid<T> g;
+    Phys<T> P;
+    StepP sp;
+    Ctl* ctl;
+    Part* parts;
+    const SrcEntry* src;
+    const int* src_off;   // [nitems + 1]
+    const double* hydro;  // [nh][4]
+    int nh;
+    int ntx, seg_h, nitems;
+};
+
+template <class T>
+struct StagedArgs {
+    Grid<T> g;
+    Phys<T> P;
+    StepP sp;
+    Ctl* ctl;
+    Part* parts;
+    Part* parts2;
+    // intermediates (padded like the state)
+    T *ux, *uy, *ax, *ay, *phi, *usx, *usy, *hs, *ax2, *ay2, *phi2;
+    T *utx, *uty, *uhx, *uhy, *ht, *qtx, *qty, *upx, *upy;
+    T *sig, *svx, *svy;
+    T *fx[3], *fy[3];
+    // global source list
+    const int* s_cell;    // padded linear index
+    const int* s_hydro;
+    const double* s_w;
+    const double* s_vx;
+    const double* s_vy;
+    int nsrc;
+    const double* hydro;
+    int nh;
+};
+
+template <class T>
+cudaError_t prepare_fused(int* ctas_per_sm);
+template <class T>
+cudaError_t launch_fused(const FusedArgs<T>& a, cudaStream_t st);
+template <class T>
+cudaError_t launch_staged(const StagedArgs<T>& a, cudaStream_t st);
+// Signal speed and mass of the current state (the first step's K3).
+template <class T>
+cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st);
+// FP64 row-major [ny][nx] staging -> padded field of type T, and back.
+template <class T>
+cudaError_t launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cudaStream_t st,
+                       unsigned* flag = nullptr, int check_neg = 0);
+template <class T>
+cudaError_t launch_unpack(const T* src, double* dst, int nx, int ny, int pitch, cudaStream_t st);
+// dst[idx[m]] = val[m]
+template <class T>
+cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cudaStream_t st);
+template <class T>
+cudaError_t launch_fill_bed(T* b, int nx, int ny, int pitch, cudaStream_t st);
+template <class T>
+size_t fused_smem_bytes();
+// Set the device copy of t_end (kernel argument, so it is stream ordered).
+cudaError_t launch_set_tend(Ctl* ctl, double t_end, cudaStream_t st);
+
+}  // namespace swe

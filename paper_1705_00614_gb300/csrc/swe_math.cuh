@@ -1,0 +1,229 @@
+// Per-cell and per-face arithmetic of one CSPH-TVD time step (Sec. 2.3,
+// Fig. 2; kernels K2-K8 of Sec. 3), templated on the arithmetic type.
+//
+// Every function takes values, not pointers, so the fused streaming kernel
+// (shared-memory rings) and the staged kernels (one kernel per stage, global
+// memory) run the same instructions.  The operation order of each formula is
+// fixed and is the one of the scheme's written definition, so the FP64
+// instantiation (compiled without FMA contraction) rounds like a plain
+// sequential evaluation of the same formulas, with one deliberate exception:
+// face depths eta - b* are formed as H + (b - b*) (see face_delta), which
+// differs from evaluating eta first by one rounding of eta.
+//
+// Walls: the device layout surrounds every grid by a ring of cells whose bed
+// is WALL_BED (1e30) and whose depth is 0, and a closed gate is a cell whose
+// bed is WALL_BED.  With that bed every face formula below yields exactly the
+// value of a reflective wall (no pressure difference, no flux, no viscous
+// stress), so no kernel needs a boundary branch.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace swe {
+
+constexpr double WALL_BED = 1.0e30;
+constexpr double WALL_TEST = 1.0e29;  // beds at or above this are walls
+
+template <class T>
+struct Phys {
+    T g;     // gravity
+    T h;     // cell size dx = dy
+    T eps;   // dry threshold
+    T nu;    // viscosity
+    T f;     // Coriolis parameter
+    T wx, wy;  // wind
+    T ca, ra;  // C_a and rho_a / rho
+};
+
+// Multiplications whose products must cancel exactly (h_R^2 - h_L^2 with
+// h_R == h_L at rest) are kept out of FMA contraction.
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
+template <class T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
+template <class T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+template <class T> __device__ __forceinline__ T tsgn(T a) { return a > T(0) ? T(1) : (a < T(0) ? T(-1) : T(0)); }
+
+// H^{4/3}.  FP64: H * cbrt(H).  FP32: 2^{(4/3) log2 H} (the f32 unit is built
+// with fast math, so this is two SFU operations; relative error ~2e-7).
+__device__ __forceinline__ double pow43(double x) { return x * cbrt(x); }
+__device__ __forceinline__ float pow43(float x) { return exp2f(1.33333333f * log2f(x)); }
+
+template <class T>
+__device__ __forceinline__ bool is_wet(T H, T b, T eps) { return H > eps && b < T(WALL_TEST); }
+
+// Hydrostatic reconstruction at the face between L and R (Audusse et al.):
+// b* = max(b_L, b_R), h_{L,R} = max(0, eta_{L,R} - b*); returns h_R^2 - h_L^2.
+// eta - b* is evaluated as H + (b - b*): the bed difference is exact or
+// nearly so, and a thin layer over high terrain keeps its relative
+// precision instead of cancelling in eta = H + b (which in FP32 has an
+// absolute resolution of ~2e-6 m at 30 m).  A face with a wall is closed.
+template <class T>
+__device__ __forceinline__ T face_delta(T hsL, T bL, T hsR, T bR) {
+    T bs = tmax(bL, bR);
+    if (bs >= T(WALL_TEST)) return T(0);
+    T hl = tmax(T(0), hsL + (bL - bs));
+    T hr = tmax(T(0), hsR + (bR - bs));
+    return mul_rn(hr, hr) - mul_rn(hl, hl);
+}
+
+// One neighbour as seen by the force evaluation.
+template <class T>
+struct Nb {
+    T hs, b, ux, uy;
+    bool wet;
+};
+
+// Forces of Eqs. 2-4 on a wet cell (stage I, K2; and K5 at t_{n+1/2}):
+// a = a^P + a^V + a^C + a^W and the friction coefficient phi with
+// F^fric = -phi U, phi = g n^2 |U| / H^{4/3}.
+template <class T>
+__device__ __forceinline__ void forces(const Phys<T>& P, T hs, T b, T nm, T ux, T uy,
+                                       const Nb<T>& W, const Nb<T>& E, const Nb<T>& S,
+                                       const Nb<T>& N, T& ax, T& ay, T& phi) {
+    // pressure -g grad(eta) in the well-balanced face form
+    T dxm = face_delta(W.hs, W.b, hs, b);
+    T dxp = face_delta(hs, b, E.hs, E.b);
+    T dym = face_delta(S.hs, S.b, hs, b);
+    T dyp = face_delta(hs, b, N.hs, N.b);
+    T coef = -P.g / (T(4) * P.h * hs);
+    T aPx = coef * (dxm + dxp);
+    T aPy = coef * (dym + dyp);
+    // viscosity: W, E, S, N; no stress from non-wet neighbours
+    T lx = T(0), ly = T(0);
+    lx = lx + (W.wet ? W.ux - ux : T(0)); ly = ly + (W.wet ? W.uy - uy : T(0));
+    lx = lx + (E.wet ? E.ux - ux : T(0)); ly = ly + (E.wet ? E.uy - uy : T(0));
+    lx = lx + (S.wet ? S.ux - ux : T(0)); ly = ly + (S.wet ? S.uy - uy : T(0));
+    lx = lx + (N.wet ? N.ux - ux : T(0)); ly = ly + (N.wet ? N.uy - uy : T(0));
+    T cv = P.nu / (P.h * P.h);
+    T aVx = cv * lx, aVy = cv * ly;
+    // Coriolis 2 U x Omega
+    T aCx = P.f * uy, aCy = -P.f * ux;
+    // wind stress
+    T dwx = P.wx - ux, dwy = P.wy - uy;
+    T wm = sqrt(dwx * dwx + dwy * dwy);
+    T cw = P.ca * P.ra * wm / hs;
+    T aWx = cw * dwx, aWy = cw * dwy;
+    ax = ((aPx + aVx) + aCx) + aWx;
+    ay = ((aPy + aVy) + aCy) + aWy;
+    // Manning friction coefficient
+    T um = sqrt(ux * ux + uy * uy);
+    phi = P.g * nm * nm * um / pow43(hs);
+}
+
+// Signal speed of a wet cell (Fig. 2): max(U_s, U_p).
+template <class T>
+__device__ __forceinline__ T cell_speed(const Phys<T>& P, T H, T ux, T uy, T ax, T ay) {
+    T c = sqrt(P.g * H);
+    T us = tmax(fabs(ux), fabs(uy)) + c;
+    T upx = fabs(ux + tsgn(ax) * sqrt(P.h * fabs(ax)));
+    T upy = fabs(uy + tsgn(ay) * sqrt(P.h * fabs(ay)));
+    return tmax(us, tmax(upx, upy));
+}
+
+template <class T>
+__device__ __forceinline__ T minmod(T a, T b) {
+    if (a > T(0) && b > T(0)) return a < b ? a : b;
+    if (a < T(0) && b < T(0)) return a > b ? a : b;
+    return T(0);
+}
+
+// Two-rarefaction approximate Riemann solution (Toro 2001) sampled at
+// x/t = 0; a side with depth <= eps is dry (dry-bed fan).
+template <class T>
+__device__ __forceinline__ void riemann(T g, T eps, T hl, T ul, T hr, T ur, T& h, T& u) {
+    bool dl = !(hl > eps), dr = !(hr > eps);
+    h = T(0);
+    u = T(0);
+    if (dl && dr) return;
+    T cl = dl ? T(0) : sqrt(g * hl);
+    T cr = dr ? T(0) : sqrt(g * hr);
+    if (dr) {
+        if (ul - cl >= T(0)) { h = hl; u = ul; }
+        else if (ul + T(2) * cl > T(0)) { T c = (ul + T(2) * cl) / T(3); h = c * c / g; u = c; }
+    } else if (dl) {
+        if (ur + cr <= T(0)) { h = hr; u = ur; }
+        else if (ur - T(2) * cr < T(0)) { T c = (T(2) * cr - ur) / T(3); h = c * c / g; u = -c; }
+    } else if (T(2) * (cl + cr) <= ur - ul) {
+        if (ul - cl >= T(0)) { h = hl; u = ul; }
+        else if (ul + T(2) * cl > T(0)) { T c = (ul + T(2) * cl) / T(3); h = c * c / g; u = c; }
+        else if (ur + cr <= T(0)) { h = hr; u = ur; }
+        else if (ur - T(2) * cr < T(0)) { T c = (T(2) * cr - ur) / T(3); h = c * c / g; u = -c; }
+    } else {
+        T us = T(0.5) * (ul + ur) + cl - cr;
+        T cs = T(0.5) * (cl + cr) + T(0.25) * (ul - ur);
+        if (us >= T(0)) {
+            if (ul - cl >= T(0)) { h = hl; u = ul; }
+            else if (us - cs >= T(0)) { T c = (ul + T(2) * cl) / T(3); h = c * c / g; u = c; }
+            else { h = cs * cs / g; u = us; }
+        } else {
+            if (ur + cr <= T(0)) { h = hr; u = ur; }
+            else if (us + cs <= T(0)) { T c = (T(2) * cr - ur) / T(3); h = c * c / g; u = -c; }
+            else { h = cs * cs / g; u = us; }
+        }
+    }
+}
+
+// Eulerian cell values (after the Lagrangian stage) used by the face fluxes:
+// w = (H~, U^x, U^y, U~'x, U~'y), the bed, and whether the cell is wet.  The
+// free surface eta~ = H~ + b is reconstructed through its differences
+// (H~ and b differenced separately), never formed directly.
+template <class T>
+struct ECell {
+    T w[5];
+    T b;
+    bool wt;
+};
+
+// MUSCL slope of one cell along the face normal (minmod; zero unless the
+// cell and both neighbours along the normal are wet).
+template <class T>
+__device__ __forceinline__ void slopes(const ECell<T>& m, const ECell<T>& c, const ECell<T>& p, T s[5]) {
+    bool lim = m.wt && c.wt && p.wt;
+    s[0] = lim ? minmod((c.w[0] - m.w[0]) + (c.b - m.b), (p.w[0] - c.w[0]) + (p.b - c.b)) : T(0);
+#pragma unroll
+    for (int q = 1; q < 5; ++q) s[q] = lim ? minmod(c.w[q] - m.w[q], p.w[q] - c.w[q]) : T(0);
+}
+
+// Flux through the face between L and R (stage III, K7) given the cells'
+// slopes along the normal; nq = 1 for x faces (normal velocity U^x), 2 for
+// y faces.  Mass flux F_H = h u of the sampled Riemann state; momentum flux
+// F_H times the upwind reconstructed U~'.
+template <class T>
+__device__ __forceinline__ void face_flux(const Phys<T>& P, const ECell<T>& L, const T sL[5],
+                                          const ECell<T>& R, const T sR[5], int nq, T& FH,
+                                          T& FQx, T& FQy) {
+    T wl[5], wr[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        wl[q] = L.w[q] + T(0.5) * sL[q];
+        wr[q] = R.w[q] - T(0.5) * sR[q];
+    }
+    T bs = tmax(L.b, R.b);
+    FH = T(0);
+    FQx = T(0);
+    FQy = T(0);
+    if (bs >= T(WALL_TEST)) return;
+    // eta~ at the face minus b*: (H~ + half slope) + (b - b*)
+    T hl = tmax(T(0), wl[0] + (L.b - bs)), hr = tmax(T(0), wr[0] + (R.b - bs));
+    T un_l = nq == 1 ? wl[1] : wl[2];
+    T un_r = nq == 1 ? wr[1] : wr[2];
+    T hs, us;
+    riemann(P.g, P.eps, hl, un_l, hr, un_r, hs, us);
+    FH = hs * us;
+    FQx = FH * (FH >= T(0) ? wl[3] : wr[3]);
+    FQy = FH * (FH >= T(0) ? wl[4] : wr[4]);
+}
+
+// Hydrograph value q(t) of one row (kind, peak, t_p, s), in FP64.
+__device__ __forceinline__ double hydro_value(const double* row, double t) {
+    if (row[0] == 0.0) {
+        double z = (t - row[2]) / row[3];
+        return row[1] * exp(-0.5 * z * z);
+    }
+    return row[1];
+}
+
+}  // namespace swe

@@ -373,6 +373,8 @@ def workload(name: str) -> Problem:
         return dam_break(256, 1.0)
     if name == "floodplain-2048sq-dx10m":
         return floodplain(2048, 10.0, 2017, 2018)
+    if name == "floodplain-4096sq-dx5m":
+        return floodplain(4096, 5.0, 2021, 2022)
     if name == "floodplain-16384sq-dx2m":
         return floodplain(16384, 2.0, 2019, 2020)
     raise KeyError(name)

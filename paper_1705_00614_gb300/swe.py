@@ -1,0 +1,232 @@
+"""Python binding of libswe (include/swe.h): argument marshalling only.
+
+Every step of the time-step path runs in the library's CUDA kernels.  The
+library must have been built (``paper_1705_00614_gb300.build.build()``);
+loading fails loudly otherwise, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+SWE_OK = 0
+SWE_F32, SWE_F64 = 0, 1
+SWE_FUSED, SWE_STAGED = 0, 1
+
+STATUS = {0: "SWE_OK", -1: "SWE_ERR_ARG", -2: "SWE_ERR_CUDA", -3: "SWE_ERR_OOM", -4: "SWE_ERR_NONFINITE",
+          -5: "SWE_ERR_DT", -6: "SWE_ERR_DEVICE_TIMEOUT", -7: "SWE_ERR_STATE"}
+
+API = ["swe_params_default", "swe_create", "swe_set_terrain", "swe_set_state", "swe_set_sources",
+       "swe_set_solid", "swe_step", "swe_get_state", "swe_get_device_ptrs", "swe_get_stages", "swe_sync",
+       "swe_destroy", "swe_status_str", "swe_last_error"]
+
+STAGE_NAMES = ["ux", "uy", "ax", "ay", "phi", "usx", "usy", "hs", "ax2", "ay2", "phi2", "utx", "uty", "uhx",
+               "uhy", "ht", "qtx", "qty", "upx", "upy", "fx", "fy"]
+
+
+class SweError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("mode", ctypes.c_int32), ("dx", ctypes.c_double), ("g", ctypes.c_double),
+                ("cfl", ctypes.c_double), ("eps_dry", ctypes.c_double), ("dt_max", ctypes.c_double),
+                ("dt_fixed", ctypes.c_double), ("nu", ctypes.c_double), ("coriolis_f", ctypes.c_double),
+                ("wind_x", ctypes.c_double), ("wind_y", ctypes.c_double), ("c_a", ctypes.c_double),
+                ("rho_air_over_rho", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("tile_w", ctypes.c_int32), ("seg_h", ctypes.c_int32)]
+
+
+class StepInfo(ctypes.Structure):
+    _fields_ = [("t", ctypes.c_double), ("dt_last", ctypes.c_double), ("mass", ctypes.c_double),
+                ("src_vol", ctypes.c_double), ("clip_vol", ctypes.c_double), ("max_speed", ctypes.c_double),
+                ("wet_cells", ctypes.c_int64), ("step", ctypes.c_int64), ("err_word", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+_lib = None
+
+
+def library_path():
+    return _build.LIB
+
+
+def load(path=None):
+    """Load libswe.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or _build.LIB
+    if not os.path.exists(p):
+        raise RuntimeError(f"libswe is not built ({p} missing); run paper_1705_00614_gb300.build.build()")
+    L = ctypes.CDLL(p)
+    L.swe_params_default.restype = None
+    L.swe_params_default.argtypes = [ctypes.POINTER(Params)]
+    L.swe_create.restype = ctypes.c_int
+    L.swe_create.argtypes = [ctypes.POINTER(Params), ctypes.POINTER(ctypes.c_void_p)]
+    L.swe_set_terrain.argtypes = [ctypes.c_void_p, _dp, _dp]
+    L.swe_set_state.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, ctypes.c_double]
+    L.swe_set_sources.argtypes = [ctypes.c_void_p, ctypes.c_int32, _ip, _ip, _dp, _dp, _dp, _ip, ctypes.c_int32,
+                                  _dp]
+    L.swe_set_solid.argtypes = [ctypes.c_void_p, ctypes.c_int32, _ip, _ip, ctypes.POINTER(ctypes.c_uint8)]
+    L.swe_step.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(StepInfo)]
+    L.swe_get_state.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+    L.swe_get_device_ptrs.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
+                                      ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
+    L.swe_get_stages.argtypes = [ctypes.c_void_p, ctypes.POINTER(_dp)]
+    L.swe_sync.argtypes = [ctypes.c_void_p]
+    L.swe_destroy.restype = None
+    L.swe_destroy.argtypes = [ctypes.c_void_p]
+    L.swe_status_str.restype = ctypes.c_char_p
+    L.swe_status_str.argtypes = [ctypes.c_int]
+    L.swe_last_error.restype = ctypes.c_char_p
+    L.swe_last_error.argtypes = []
+    for name in ("swe_create", "swe_set_terrain", "swe_set_state", "swe_set_sources", "swe_set_solid",
+                 "swe_step", "swe_get_state", "swe_get_device_ptrs", "swe_get_stages", "swe_sync"):
+        getattr(L, name).restype = ctypes.c_int
+    if path is None:
+        _lib = L
+    return L
+
+
+def _check(L, rc):
+    if rc != SWE_OK:
+        raise SweError(rc, L.swe_last_error().decode(errors="replace"))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_dp) if a is not None else None
+
+
+class Solver:
+    """One grid: a libswe context.  Arrays are [ny, nx] float64 on the host."""
+
+    def __init__(self, params, precision="f32", mode="fused", stream=None, seg_h=0):
+        self.L = load()
+        p = Params()
+        self.L.swe_params_default(ctypes.byref(p))
+        for k in ("nx", "ny", "dx", "g", "cfl", "dt_max", "dt_fixed", "nu", "coriolis_f", "wind_x", "wind_y",
+                  "c_a", "rho_air_over_rho"):
+            setattr(p, k, getattr(params, k))
+        p.eps_dry = params.eps
+        p.precision = SWE_F64 if precision == "f64" else SWE_F32
+        p.mode = SWE_STAGED if mode == "staged" else SWE_FUSED
+        p.cuda_stream = stream
+        p.seg_h = seg_h
+        self.params = params
+        self.nx, self.ny = params.nx, params.ny
+        h = ctypes.c_void_p()
+        _check(self.L, self.L.swe_create(ctypes.byref(p), ctypes.byref(h)))
+        self.h = h
+
+    @classmethod
+    def from_problem(cls, prob, precision="f32", mode="fused", stream=None, seg_h=0):
+        s = cls(prob.params, precision, mode, stream, seg_h)
+        s.set_terrain(prob.b, prob.n_manning)
+        if len(prob.sources):
+            s.set_sources(prob.sources)
+        if prob.solid is not None and prob.solid.any():
+            iy, ix = np.nonzero(prob.solid)
+            s.set_solid(ix, iy, np.ones(len(ix), dtype=np.uint8))
+        s.set_state(prob.H, prob.Qx, prob.Qy, prob.t0)
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.swe_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_terrain(self, b, n=None):
+        b = _f64(b)
+        n = None if n is None else _f64(n)
+        _check(self.L, self.L.swe_set_terrain(self.h, _ptr(b), _ptr(n)))
+
+    def set_state(self, H, Qx, Qy, t=0.0):
+        H, Qx, Qy = _f64(H), _f64(Qx), _f64(Qy)
+        _check(self.L, self.L.swe_set_state(self.h, _ptr(H), _ptr(Qx), _ptr(Qy), float(t)))
+
+    def set_sources(self, src):
+        n = len(src)
+        ix = np.ascontiguousarray(src.ix, dtype=np.int32)
+        iy = np.ascontiguousarray(src.iy, dtype=np.int32)
+        hy = np.ascontiguousarray(src.hydro, dtype=np.int32)
+        w, vx, vy = _f64(src.weight), _f64(src.vx), _f64(src.vy)
+        tab = _f64(src.hydro_table()).reshape(-1)
+        _check(self.L, self.L.swe_set_sources(self.h, n, ix.ctypes.data_as(_ip), iy.ctypes.data_as(_ip),
+                                              _ptr(w), _ptr(vx), _ptr(vy), hy.ctypes.data_as(_ip),
+                                              len(tab) // 4, _ptr(tab)))
+
+    def set_solid(self, ix, iy, closed):
+        ix = np.ascontiguousarray(ix, dtype=np.int32)
+        iy = np.ascontiguousarray(iy, dtype=np.int32)
+        cl = np.ascontiguousarray(closed, dtype=np.uint8)
+        _check(self.L, self.L.swe_set_solid(self.h, len(ix), ix.ctypes.data_as(_ip), iy.ctypes.data_as(_ip),
+                                            cl.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+    def step(self, nsteps=1, t_end=0.0, report=True):
+        info = StepInfo()
+        _check(self.L, self.L.swe_step(self.h, int(nsteps), float(t_end),
+                                       ctypes.byref(info) if report else None))
+        return info.as_dict() if report else None
+
+    def get_state(self):
+        H = np.empty((self.ny, self.nx))
+        Qx = np.empty_like(H)
+        Qy = np.empty_like(H)
+        t = ctypes.c_double()
+        _check(self.L, self.L.swe_get_state(self.h, _ptr(H), _ptr(Qx), _ptr(Qy), ctypes.byref(t)))
+        return H, Qx, Qy, t.value
+
+    def get_state_into(self, H, Qx, Qy):
+        """Copy the state into caller-owned (e.g. pinned) float64 arrays."""
+        t = ctypes.c_double()
+        _check(self.L, self.L.swe_get_state(self.h, _ptr(H), _ptr(Qx), _ptr(Qy), ctypes.byref(t)))
+        return t.value
+
+    def device_ptrs(self):
+        H, Qx, Qy = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        pitch, esz = ctypes.c_int64(), ctypes.c_int32()
+        _check(self.L, self.L.swe_get_device_ptrs(self.h, ctypes.byref(H), ctypes.byref(Qx), ctypes.byref(Qy),
+                                                  ctypes.byref(pitch), ctypes.byref(esz)))
+        return H.value, Qx.value, Qy.value, pitch.value, esz.value
+
+    def stages(self):
+        nx, ny = self.nx, self.ny
+        out = {k: np.empty((ny, nx)) for k in STAGE_NAMES[:20]}
+        out["fx"] = np.empty((3, ny, nx + 1))
+        out["fy"] = np.empty((3, ny + 1, nx))
+        arr = (_dp * 22)(*[_ptr(out[k]) for k in STAGE_NAMES])
+        _check(self.L, self.L.swe_get_stages(self.h, arr))
+        return out
+
+    def sync(self):
+        _check(self.L, self.L.swe_sync(self.h))
