@@ -219,7 +219,10 @@ def main():
 
     prob, eta0 = flooded_workload(args.workload)
     cells = prob.params.nx * prob.params.ny
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream: the library launches on it and the
+    # CUDA events below are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     solver = swe.Solver.from_problem(prob, args.precision, stream=stream.cuda_stream)
 
     # instantiate the CUDA graph of K steps once, restart, then W untimed

@@ -20,10 +20,11 @@
  *    for the staging buffer of host copies, at the first host copy) and
  *    frees it in swe_destroy.  Device pointers returned by
  *    swe_get_device_ptrs stay owned by the context.
- *  - A context is bound to one CUDA stream (swe_params.cuda_stream, or the
- *    legacy default stream when NULL) and is not thread safe.  Calls that
- *    return data to the host synchronise that stream; the others only
- *    enqueue work.
+ *  - A context is bound to one CUDA stream: swe_params.cuda_stream, or, when
+ *    that is NULL, a non-blocking stream the context creates and destroys
+ *    (the legacy default stream cannot hold the CUDA graphs swe_step uses).
+ *    A context is not thread safe.  Calls that return data to the host
+ *    synchronise that stream; the others only enqueue work.
  *  - Depth H (m), momentum Q = H U (m^2/s, the paper's HV of K8), bed b (m).
  */
 #ifndef SWE_H

@@ -207,32 +207,42 @@ def test_overflowing_state_is_reported(swe):
 def test_floodplain_2048_f32_1000_steps(swe):
     """2048^2 floodplain, dx 10 m, fractal terrain with a carved channel,
     Manning patches, viscosity, Coriolis at 48N, wind, a 100-cell Gaussian
-    inflow strip, dry start, 1000 FP32 steps on the GPU.  The oracle runs
-    the window that holds all the water (water never comes near the
-    window's edges, so walls there change nothing): rel L2 of H <= 1e-3 and
-    mass drift <= 1e-6."""
+    inflow strip, dry start.  The oracle takes 1000 FP64 steps on the window
+    that holds all the water (water never comes near the window's edges, so
+    walls there change nothing); the GPU runs the full grid in FP32 up to the
+    same simulated time (its own CFL steps, landing on it with t_end).  The
+    CFL step is set by the fastest signal at thin wet fronts and is itself
+    sensitive to FP32 rounding, so states are compared at equal time, not
+    equal step count.  Bars: rel L2 of H <= 1e-3; the GPU's FP64 mass budget
+    (mass - sources - clipping) drifts by <= 1e-6."""
     full = I.workload("floodplain-2048sq-dx10m").to_f32_values()
-    with swe.Solver.from_problem(full, "f32") as s:
-        info = s.step(1000)
-        Hg, Qxg, Qyg, tg = s.get_state()
-    # window around the inflow strip
-    j0, j1, i1 = int(full.sources.iy.min()) - 100, int(full.sources.iy.max()) + 100, 200
-    wet = np.argwhere(Hg > 0.0)
-    assert wet[:, 0].min() > j0 + 8 and wet[:, 0].max() < j1 - 8 and wet[:, 1].max() < i1 - 8
     src = full.sources
+    j0, j1, i1 = int(src.iy.min()) - 100, int(src.iy.max()) + 100, 200
     crop = I.Problem("crop", I.Params(**{**full.params.__dict__, "nx": i1, "ny": j1 - j0}),
                      full.b[j0:j1, :i1], full.n_manning[j0:j1, :i1], full.H[j0:j1, :i1],
                      full.Qx[j0:j1, :i1], full.Qy[j0:j1, :i1],
                      I.Sources(src.ix, src.iy - j0, src.weight, src.vx, src.vy, src.hydro, src.hydrographs))
     H, Qx, Qy, t, infos = oracle.run(crop, 1000)
     assert np.abs(H[:8]).max() == 0 and np.abs(H[-8:]).max() == 0 and np.abs(H[:, -8:]).max() == 0
+    budget = 0.0
+    with swe.Solver.from_problem(full, "f32") as s:
+        m0 = s.step(0)["mass"]
+        steps = 0
+        while True:
+            gi = s.step(1, t_end=t)
+            if gi["step"] == steps:
+                break
+            steps = gi["step"]
+            budget += gi["src_vol"] + gi["clip_vol"]
+        Hg, Qxg, Qyg, tg = s.get_state()
+    assert tg == t and 950 <= steps <= 1050, (tg, t, steps)
+    wet = np.argwhere(Hg > 0.0)
+    assert wet[:, 0].min() > j0 + 8 and wet[:, 0].max() < j1 - 8 and wet[:, 1].max() < i1 - 8
     Hc = Hg[j0:j1, :i1]
     l2 = np.linalg.norm(Hc - H) / np.linalg.norm(H)
     assert l2 <= 1e-3, l2
-    assert abs(tg - t) <= 1e-5 * t
-    vol_in = sum(i["src_vol"] for i in infos)
-    assert abs(info["mass"] - infos[-1]["mass"]) <= 1e-6 * infos[-1]["mass"]
-    assert vol_in > 0
+    assert abs(gi["mass"] - (m0 + budget)) <= 1e-6 * gi["mass"]
+    assert sum(i["src_vol"] for i in infos) > 0
 
 
 def test_full_size_16384_sampled_cells(swe):
