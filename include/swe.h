@@ -170,6 +170,56 @@ SWE_API void swe_destroy(swe_ctx* ctx);
 SWE_API const char* swe_status_str(int status);
 SWE_API const char* swe_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Allocation-free step.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory -- programs whose
+ * device memory all comes from a host framework's own pool or arena, that
+ * run under a fixed device-memory budget, or that must not call cudaMalloc
+ * or cudaFree because those calls can synchronise the whole device.  It
+ * performs one FP32 time step with the same fused kernel as swe_step and
+ * calls no cudaMalloc, cudaFree or other allocating routine.
+ *
+ * Planes: H, Qx, Qy (state at time t), b, n (bed, Manning) and the outputs
+ * H_out, Qx_out, Qy_out are caller-owned FP32 device arrays in this
+ * library's padded layout: ny + 2*SWE_PAD rows of `pitch` floats, with
+ * pitch >= nx + 2*SWE_PAD and a multiple of 4, each array starting on a
+ * 16-byte boundary; cell (i, j) is element (j + SWE_PAD) * pitch + i +
+ * SWE_PAD.  The SWE_PAD-wide ring around the grid must hold H = Qx = Qy = 0,
+ * n = 0 and b >= 1e30 (walls; a closed gate is a cell with b >= 1e30).  The
+ * step writes the grid's cells of the outputs only; the outputs must not
+ * overlap the inputs.  No sources.
+ *
+ * Time step: tau = dt_fixed if p->dt_fixed > 0, else min(dt_max, cfl * dx /
+ * max_speed) with max_speed the largest signal speed of the input state,
+ * i.e. the max_speed reported for it by swe_step or by the previous call of
+ * this function (0 for still water); max_speed < 0 without dt_fixed is
+ * rejected.  With info != NULL the stream is synchronised and the report
+ * (new t, tau, mass, wet cells, max_speed of the output state) filled.
+ * Runs on p->cuda_stream (NULL: the legacy default stream).
+ *
+ * Scratch: the kernel's control block, one partial-sum record per CTA and
+ * an empty source table live in a file-scope device array of
+ * SWE_NOALLOC_SCRATCH_BYTES bytes that every GPU loading this library keeps
+ * until the process exits.  Grids needing more than SWE_NOALLOC_MAX_ITEMS
+ * CTAs (nx > 7000 * 116 cells) are rejected with SWE_ERR_ARG.  The first
+ * call on a device looks up the array's device address and sets the
+ * kernel's shared-memory size (once per device); make that first call
+ * before any stream capture.  Every call resets what must start at zero,
+ * but all calls share the one array: calls whose work can overlap on the
+ * GPU (other streams, other host threads) race and corrupt each other's
+ * results, so serialise them.
+ * Errors: SWE_ERR_ARG (sizes, alignment, layout, parameters; checked before
+ * any device work), SWE_ERR_CUDA, SWE_ERR_NONFINITE, SWE_ERR_DT,
+ * SWE_ERR_DEVICE_TIMEOUT.
+ * ------------------------------------------------------------------------ */
+#define SWE_PAD 10
+#define SWE_NOALLOC_MAX_ITEMS 7000
+#define SWE_NOALLOC_SCRATCH_BYTES 252416
+SWE_API int swe_step_f32_noalloc(const swe_params* p, const float* H, const float* Qx, const float* Qy,
+                                 const float* b, const float* n, float* H_out, float* Qx_out,
+                                 float* Qy_out, int64_t pitch, double t, double max_speed,
+                                 swe_step_info* info);
+
 #ifdef __cplusplus
 }
 #endif

@@ -22,6 +22,7 @@ UNITS = [
     ("swe_f32.cu", ["-use_fast_math"]),
     ("swe_f64.cu", ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"]),
     ("swe_capi.cu", []),
+    ("swe_noalloc.cu", []),
 ]
 
 

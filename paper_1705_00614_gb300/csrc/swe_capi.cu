@@ -59,6 +59,8 @@ enum StageField {
 
 }  // namespace
 
+void swe::set_last_error(const char* msg) { g_err = msg; }
+
 struct swe_ctx {
     swe_params p;
     int dev = 0;

@@ -130,6 +130,8 @@ template <class T>
 cudaError_t launch_fill_bed(T* b, int nx, int ny, int pitch, cudaStream_t st);
 template <class T>
 size_t fused_smem_bytes();
+// The message swe_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
 // Set the device copy of t_end (kernel argument, so it is stream ordered).
 cudaError_t launch_set_tend(Ctl* ctl, double t_end, cudaStream_t st);
 

@@ -22,7 +22,9 @@ STATUS = {0: "SWE_OK", -1: "SWE_ERR_ARG", -2: "SWE_ERR_CUDA", -3: "SWE_ERR_OOM",
 
 API = ["swe_params_default", "swe_create", "swe_set_terrain", "swe_set_state", "swe_set_sources",
        "swe_set_solid", "swe_step", "swe_get_state", "swe_get_device_ptrs", "swe_get_stages", "swe_sync",
-       "swe_destroy", "swe_status_str", "swe_last_error"]
+       "swe_destroy", "swe_status_str", "swe_last_error", "swe_step_f32_noalloc"]
+SWE_PAD = 10
+NOALLOC_MAX_ITEMS = 7000
 
 STAGE_NAMES = ["ux", "uy", "ax", "ay", "phi", "usx", "usy", "hs", "ax2", "ay2", "phi2", "utx", "uty", "uhx",
                "uhy", "ht", "qtx", "qty", "upx", "upy", "fx", "fy"]
@@ -94,6 +96,9 @@ def load(path=None):
     L.swe_status_str.argtypes = [ctypes.c_int]
     L.swe_last_error.restype = ctypes.c_char_p
     L.swe_last_error.argtypes = []
+    L.swe_step_f32_noalloc.restype = ctypes.c_int
+    L.swe_step_f32_noalloc.argtypes = [ctypes.POINTER(Params)] + [ctypes.c_void_p] * 8 + [
+        ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.POINTER(StepInfo)]
     for name in ("swe_create", "swe_set_terrain", "swe_set_state", "swe_set_sources", "swe_set_solid",
                  "swe_step", "swe_get_state", "swe_get_device_ptrs", "swe_get_stages", "swe_sync"):
         getattr(L, name).restype = ctypes.c_int
@@ -115,21 +120,39 @@ def _ptr(a):
     return a.ctypes.data_as(_dp) if a is not None else None
 
 
+def make_params(params, precision="f32", mode="fused", stream=None, seg_h=0):
+    """swe_params from an inputs.Params-like object."""
+    L = load()
+    p = Params()
+    L.swe_params_default(ctypes.byref(p))
+    for k in ("nx", "ny", "dx", "g", "cfl", "dt_max", "dt_fixed", "nu", "coriolis_f", "wind_x", "wind_y",
+              "c_a", "rho_air_over_rho"):
+        setattr(p, k, getattr(params, k))
+    p.eps_dry = params.eps
+    p.precision = SWE_F64 if precision == "f64" else SWE_F32
+    p.mode = SWE_STAGED if mode == "staged" else SWE_FUSED
+    p.cuda_stream = stream
+    p.seg_h = seg_h
+    return p
+
+
+def step_f32_noalloc(params, H, Qx, Qy, b, n, H_out, Qx_out, Qy_out, pitch, t, max_speed, stream=None):
+    """swe_step_f32_noalloc on caller-owned device planes (integer device
+    addresses in the library's padded layout); returns the step report."""
+    L = load()
+    p = make_params(params, "f32", stream=stream)
+    info = StepInfo()
+    _check(L, L.swe_step_f32_noalloc(ctypes.byref(p), H, Qx, Qy, b, n, H_out, Qx_out, Qy_out, int(pitch),
+                                     float(t), float(max_speed), ctypes.byref(info)))
+    return info.as_dict()
+
+
 class Solver:
     """One grid: a libswe context.  Arrays are [ny, nx] float64 on the host."""
 
     def __init__(self, params, precision="f32", mode="fused", stream=None, seg_h=0):
         self.L = load()
-        p = Params()
-        self.L.swe_params_default(ctypes.byref(p))
-        for k in ("nx", "ny", "dx", "g", "cfl", "dt_max", "dt_fixed", "nu", "coriolis_f", "wind_x", "wind_y",
-                  "c_a", "rho_air_over_rho"):
-            setattr(p, k, getattr(params, k))
-        p.eps_dry = params.eps
-        p.precision = SWE_F64 if precision == "f64" else SWE_F32
-        p.mode = SWE_STAGED if mode == "staged" else SWE_FUSED
-        p.cuda_stream = stream
-        p.seg_h = seg_h
+        p = make_params(params, precision, mode, stream, seg_h)
         self.params = params
         self.nx, self.ny = params.nx, params.ny
         h = ctypes.c_void_p()
