@@ -135,19 +135,43 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 }
 
 // ------------------------------------------------------------------ fused kernel
+//
+// Skewed row pipeline.  Window row r of stage s is processed in iteration
+// k = r + LAG_s.  Lags are chosen so that every stage reads only rows that
+// other threads finished in earlier iterations; one CTA barrier per
+// iteration then orders everything.  Two warp groups of 128 threads (one
+// thread per window column each) share the work of an iteration:
+//   group L (Lagrangian, stage I-II):  S0 primitives (row k), S1 forces at
+//     t_n and U* (k-2), S2 particle area and H* (k-4), S3 forces at
+//     t_{n+1/2}, corrector and sources (k-6);
+//   group E (Eulerian, stage III-IV):  S4 MUSCL slopes and face fluxes
+//     (k-8), S6 final update (k-9), S7 signal speed of the new state for the
+//     next step's K3 (k-11).
+// Input rows (H, Qx, Qy, b, n) arrive by TMA in chunks of RB rows; each
+// field has a ring of chunk slots as deep as its oldest reader needs.
+
+constexpr int NT = 2 * WIN;
+constexpr int LAG1 = 2, LAG2 = 4, LAG3 = 6, LAG4 = 8, LAG6 = 9, LAG7 = 11;
+constexpr int DP = 7, DA = 6, DB = 4, DC = 4, DF = 2, DN = 4;   // stage ring depths (rows)
+constexpr int SLOT_Q = 2, SLOT_H = 4, SLOT_B = 5, SLOT_N = 5;   // chunk slots per input field
+constexpr int NBAR = 5;
 
 template <class T>
 struct FSmem {
-    T in[NSLOT][5][RB][WIN];  // TMA ring: H, Qx, Qy, b, n
-    T pU[4][2][WIN];          // U at t_n
-    T aU[4][2][WIN];          // predictor U*
-    T bH[3][WIN];             // particle depth H*
-    T cS[3][7][WIN];          // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y
-    T fX[2][3][WIN];          // x-face fluxes F_H, F_Qx, F_Qy
-    T nS[3][3][WIN];          // new state H, Ux, Uy
-    unsigned long long bar[NSLOT];
+    T inH[SLOT_H][RB][WIN];
+    T inQx[SLOT_Q][RB][WIN];
+    T inQy[SLOT_Q][RB][WIN];
+    T inB[SLOT_B][RB][WIN];
+    T inN[SLOT_N][RB][WIN];
+    T pU[DP][2][WIN];      // U at t_n
+    T aU[DA][2][WIN];      // predictor U*
+    T bH[DB][WIN];         // particle depth H*
+    T cS[DC][7][WIN];      // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y
+    T fX[DF][3][WIN];      // x-face fluxes F_H, F_Qx, F_Qy
+    T nS[DN][3][WIN];      // new state H, Ux, Uy
+    unsigned long long bar[NBAR];
     double hq[MAX_HYDRO];
-    double red[WIN / 32];
+    double red[NT / 32];
     double tau;
     int last;
 };
@@ -160,22 +184,24 @@ size_t fused_smem_bytes() {
 template <class T>
 __device__ __forceinline__ void issue_chunk(FSmem<T>& s, const FusedArgs<T>& a, int buf, int ch,
                                             int gx0, int gy0) {
-    const int slot = ch % NSLOT;
-    mbar_expect_tx(&s.bar[slot], 5u * RB * WIN * sizeof(T));
+    unsigned long long* bar = &s.bar[ch % NBAR];
+    mbar_expect_tx(bar, 5u * RB * WIN * sizeof(T));
     const int y = gy0 + ch * RB;
-    tma_load_2d(&s.in[slot][0][0][0], &a.tmH[buf], gx0, y, &s.bar[slot]);
-    tma_load_2d(&s.in[slot][1][0][0], &a.tmQx[buf], gx0, y, &s.bar[slot]);
-    tma_load_2d(&s.in[slot][2][0][0], &a.tmQy[buf], gx0, y, &s.bar[slot]);
-    tma_load_2d(&s.in[slot][3][0][0], &a.tmB, gx0, y, &s.bar[slot]);
-    tma_load_2d(&s.in[slot][4][0][0], &a.tmN, gx0, y, &s.bar[slot]);
+    tma_load_2d(&s.inH[ch % SLOT_H][0][0], &a.tmH[buf], gx0, y, bar);
+    tma_load_2d(&s.inQx[ch % SLOT_Q][0][0], &a.tmQx[buf], gx0, y, bar);
+    tma_load_2d(&s.inQy[ch % SLOT_Q][0][0], &a.tmQy[buf], gx0, y, bar);
+    tma_load_2d(&s.inB[ch % SLOT_B][0][0], &a.tmB, gx0, y, bar);
+    tma_load_2d(&s.inN[ch % SLOT_N][0][0], &a.tmN, gx0, y, bar);
 }
 
 template <class T>
-__global__ void __launch_bounds__(WIN, sizeof(T) == 4 ? 3 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     FSmem<T>& s = *reinterpret_cast<FSmem<T>*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-    const int c = threadIdx.x;
+    const int tid = threadIdx.x;
+    const int c = tid & (WIN - 1);
+    const bool groupL = tid < WIN;
     const int item = blockIdx.x;
     const int strip = item % a.ntx, seg = item / a.ntx;
     const int x0 = strip * TW, y0 = seg * a.seg_h;
@@ -188,10 +214,10 @@ __global__ void __launch_bounds__(WIN, sizeof(T) == 4 ? 3 : 1) k_fused(const __g
     const Phys<T>& P = a.P;
     const T eps = P.eps;
 
-    if (c == 0) {
+    if (tid == 0) {
         s.tau = step_tau(a.ctl, a.sp, buf);
 #pragma unroll
-        for (int i = 0; i < NSLOT; ++i) mbar_init(&s.bar[i], 1);
+        for (int i = 0; i < NBAR; ++i) mbar_init(&s.bar[i], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -200,8 +226,8 @@ __global__ void __launch_bounds__(WIN, sizeof(T) == 4 ? 3 : 1) k_fused(const __g
     const T tauT = (T)tau;
     const T th = T(0.5) * tauT;
     const T dth = tauT / P.h;
-    if (c < a.nh) s.hq[c] = hydro_value(a.hydro + 4 * c, a.ctl->t + 0.5 * (double)tauT);
-    if (c == 0) issue_chunk(s, a, buf, 0, gx0, gy0);
+    if (tid < a.nh) s.hq[tid] = hydro_value(a.hydro + 4 * tid, a.ctl->t + 0.5 * (double)tauT);
+    if (tid == 0) issue_chunk(s, a, buf, 0, gx0, gy0);
     __syncthreads();
 
     T* const outH = a.g.H[buf ^ 1];
@@ -209,7 +235,11 @@ __global__ void __launch_bounds__(WIN, sizeof(T) == 4 ? 3 : 1) k_fused(const __g
     T* const outQy = a.g.Qy[buf ^ 1];
     const bool out_col = (c >= HALO) && (c < HALO + tw);
 
-    auto inrow = [&](int f, int r) -> const T* { return s.in[(r / RB) % NSLOT][f][r % RB]; };
+    auto rH = [&](int r) -> const T* { return s.inH[(r / RB) % SLOT_H][r % RB]; };
+    auto rQx = [&](int r) -> const T* { return s.inQx[(r / RB) % SLOT_Q][r % RB]; };
+    auto rQy = [&](int r) -> const T* { return s.inQy[(r / RB) % SLOT_Q][r % RB]; };
+    auto rB = [&](int r) -> const T* { return s.inB[(r / RB) % SLOT_B][r % RB]; };
+    auto rN = [&](int r) -> const T* { return s.inN[(r / RB) % SLOT_N][r % RB]; };
 
     int sp = a.src_off[item];
     const int se = a.src_off[item + 1];
@@ -219,239 +249,236 @@ __global__ void __launch_bounds__(WIN, sizeof(T) == 4 ? 3 : 1) k_fused(const __g
     long long acc_wet = 0;
     bool bad = false;
 
-    for (int k = 0; k <= nrows; ++k) {
+    for (int k = 0; k <= nrows + LAG7 - HALO - 1; ++k) {
         if ((k % RB) == 0) {
             const int ch = k / RB;
             if (ch < nchunks) {
-                if (c == 0 && ch + 1 < nchunks) {
+                if (tid == 0 && ch + 1 < nchunks) {
                     fence_proxy_async();
                     issue_chunk(s, a, buf, ch + 1, gx0, gy0);
                 }
-                const bool ok = mbar_wait_bounded(&s.bar[ch % NSLOT], (unsigned)((ch / NSLOT) & 1));
+                const bool ok = mbar_wait_bounded(&s.bar[ch % NBAR], (unsigned)((ch / NBAR) & 1));
                 if (__syncthreads_or(!ok)) {
-                    if (c == 0) atomicOr(&a.ctl->err, (unsigned)ERR_TIMEOUT);
+                    if (tid == 0) atomicOr(&a.ctl->err, (unsigned)ERR_TIMEOUT);
                     return;
                 }
             }
         }
-        // (a) signal speed of the new state at row k-7; primitives at row k
-        {
-            const int r = k - 7;
-            if (r >= HALO && r < HALO + sh && out_col) {
-                const T* b0 = inrow(3, r);
-                const T* bm = inrow(3, r - 1);
-                const T* bp = inrow(3, r + 1);
-                const int i0 = r % 3, im = (r - 1) % 3, ip = (r + 1) % 3;
-                const T H = s.nS[i0][0][c], b = b0[c];
-                if (is_wet(H, b, eps)) {
-                    const T ux = s.nS[i0][1][c], uy = s.nS[i0][2][c];
-                    Nb<T> W{s.nS[i0][0][c - 1], b0[c - 1], s.nS[i0][1][c - 1], s.nS[i0][2][c - 1],
-                            is_wet(s.nS[i0][0][c - 1], b0[c - 1], eps)};
-                    Nb<T> E{s.nS[i0][0][c + 1], b0[c + 1], s.nS[i0][1][c + 1], s.nS[i0][2][c + 1],
-                            is_wet(s.nS[i0][0][c + 1], b0[c + 1], eps)};
-                    Nb<T> S{s.nS[im][0][c], bm[c], s.nS[im][1][c], s.nS[im][2][c],
-                            is_wet(s.nS[im][0][c], bm[c], eps)};
-                    Nb<T> N{s.nS[ip][0][c], bp[c], s.nS[ip][1][c], s.nS[ip][2][c],
-                            is_wet(s.nS[ip][0][c], bp[c], eps)};
-                    T ax, ay, phi;
-                    forces(P, H, b, inrow(4, r)[c], ux, uy, W, E, S, N, ax, ay, phi);
-                    const double v = (double)cell_speed(P, H, ux, uy, ax, ay);
-                    if (!(v <= DBL_MAX)) bad = true;
-                    else if (v > vmax) vmax = v;
-                }
-            }
+        if (groupL) {
+            // S0: primitives at row k
             if (k < nrows) {
-                const T H = inrow(0, k)[c];
-                const bool wet = is_wet(H, inrow(3, k)[c], eps);
-                s.pU[k & 3][0][c] = wet ? inrow(1, k)[c] / H : T(0);
-                s.pU[k & 3][1][c] = wet ? inrow(2, k)[c] / H : T(0);
+                const T H = rH(k)[c];
+                const bool wet = is_wet(H, rB(k)[c], eps);
+                s.pU[k % DP][0][c] = wet ? rQx(k)[c] / H : T(0);
+                s.pU[k % DP][1][c] = wet ? rQy(k)[c] / H : T(0);
             }
-        }
-        __syncthreads();
-        // (b) forces at t_n and predictor velocity U* at row k-1
-        {
-            const int r = k - 1;
-            if (r >= 1 && r <= nrows - 2 && c >= 1 && c < WIN - 1) {
-                const T *H0 = inrow(0, r), *Hm = inrow(0, r - 1), *Hp = inrow(0, r + 1);
-                const T *b0 = inrow(3, r), *bm = inrow(3, r - 1), *bp = inrow(3, r + 1);
-                const T(*U0)[WIN] = s.pU[r & 3];
-                const T(*Um)[WIN] = s.pU[(r - 1) & 3];
-                const T(*Up)[WIN] = s.pU[(r + 1) & 3];
-                const T H = H0[c], b = b0[c];
-                T usx = T(0), usy = T(0);
-                if (is_wet(H, b, eps)) {
-                    Nb<T> W{H0[c - 1], b0[c - 1], U0[0][c - 1], U0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
-                    Nb<T> E{H0[c + 1], b0[c + 1], U0[0][c + 1], U0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
-                    Nb<T> S{Hm[c], bm[c], Um[0][c], Um[1][c], is_wet(Hm[c], bm[c], eps)};
-                    Nb<T> N{Hp[c], bp[c], Up[0][c], Up[1][c], is_wet(Hp[c], bp[c], eps)};
-                    T ax, ay, phi;
-                    forces(P, H, b, inrow(4, r)[c], U0[0][c], U0[1][c], W, E, S, N, ax, ay, phi);
-                    const T den = T(1) + th * phi;
-                    usx = (U0[0][c] + th * ax) / den;
-                    usy = (U0[1][c] + th * ay) / den;
+            // S1: forces at t_n and predictor velocity U*
+            {
+                const int r = k - LAG1;
+                if (r >= 1 && r <= nrows - 2 && c >= 1 && c < WIN - 1) {
+                    const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
+                    const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
+                    const T(*U0)[WIN] = s.pU[r % DP];
+                    const T(*Um)[WIN] = s.pU[(r - 1) % DP];
+                    const T(*Up)[WIN] = s.pU[(r + 1) % DP];
+                    const T H = H0[c], b = b0[c];
+                    T usx = T(0), usy = T(0);
+                    if (is_wet(H, b, eps)) {
+                        Nb<T> W{H0[c - 1], b0[c - 1], U0[0][c - 1], U0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
+                        Nb<T> E{H0[c + 1], b0[c + 1], U0[0][c + 1], U0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
+                        Nb<T> S{Hm[c], bm[c], Um[0][c], Um[1][c], is_wet(Hm[c], bm[c], eps)};
+                        Nb<T> N{Hp[c], bp[c], Up[0][c], Up[1][c], is_wet(Hp[c], bp[c], eps)};
+                        T ax, ay, phi;
+                        forces(P, H, b, rN(r)[c], U0[0][c], U0[1][c], W, E, S, N, ax, ay, phi);
+                        const T den = T(1) + th * phi;
+                        usx = (U0[0][c] + th * ax) / den;
+                        usy = (U0[1][c] + th * ay) / den;
+                    }
+                    s.aU[r % DA][0][c] = usx;
+                    s.aU[r % DA][1][c] = usy;
                 }
-                s.aU[r & 3][0][c] = usx;
-                s.aU[r & 3][1][c] = usy;
             }
-        }
-        __syncthreads();
-        // (c) particle area change and H* at row k-2
-        {
-            const int r = k - 2;
-            if (r >= 2 && r <= nrows - 3 && c >= 2 && c < WIN - 2) {
-                const T H = inrow(0, r)[c];
-                T hs = H;
-                if (is_wet(H, inrow(3, r)[c], eps)) {
-                    const T* Ax = s.aU[r & 3][0];
-                    const T* Ay = s.aU[r & 3][1];
-                    const T u = Ax[c], uW = Ax[c - 1], uE = Ax[c + 1];
-                    const T v = Ay[c], vS = s.aU[(r - 1) & 3][1][c], vN = s.aU[(r + 1) & 3][1][c];
-                    const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
-                    const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
-                    const T D = ((fxp - fxm) + (fyp - fym)) / P.h;
-                    hs = H / tmax(T(0.5), T(1) + th * D);
+            // S2: particle area change and H*
+            {
+                const int r = k - LAG2;
+                if (r >= 2 && r <= nrows - 3 && c >= 2 && c < WIN - 2) {
+                    const T H = rH(r)[c];
+                    T hs = H;
+                    if (is_wet(H, rB(r)[c], eps)) {
+                        const T* Ax = s.aU[r % DA][0];
+                        const T* Ay = s.aU[r % DA][1];
+                        const T u = Ax[c], uW = Ax[c - 1], uE = Ax[c + 1];
+                        const T v = Ay[c], vS = s.aU[(r - 1) % DA][1][c], vN = s.aU[(r + 1) % DA][1][c];
+                        const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
+                        const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
+                        const T D = ((fxp - fxm) + (fyp - fym)) / P.h;
+                        hs = H / tmax(T(0.5), T(1) + th * D);
+                    }
+                    s.bH[r % DB][c] = hs;
                 }
-                s.bH[r % 3][c] = hs;
             }
-        }
-        __syncthreads();
-        // (d) forces at t_{n+1/2}, corrector and sources at row k-3
-        {
-            const int r = k - 3;
-            if (r >= 3 && r <= nrows - 4 && c >= 3 && c < WIN - 3) {
-                const T *H0 = inrow(0, r), *Hm = inrow(0, r - 1), *Hp = inrow(0, r + 1);
-                const T *b0 = inrow(3, r), *bm = inrow(3, r - 1), *bp = inrow(3, r + 1);
-                const T *B0 = s.bH[r % 3], *Bm = s.bH[(r - 1) % 3], *Bp = s.bH[(r + 1) % 3];
-                const T(*A0)[WIN] = s.aU[r & 3];
-                const T(*Am)[WIN] = s.aU[(r - 1) & 3];
-                const T(*Ap)[WIN] = s.aU[(r + 1) & 3];
-                const T H = H0[c], b = b0[c];
-                const T ux = s.pU[r & 3][0][c], uy = s.pU[r & 3][1][c];
-                T utx = T(0), uty = T(0);
-                if (is_wet(H, b, eps)) {
-                    Nb<T> W{B0[c - 1], b0[c - 1], A0[0][c - 1], A0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
-                    Nb<T> E{B0[c + 1], b0[c + 1], A0[0][c + 1], A0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
-                    Nb<T> S{Bm[c], bm[c], Am[0][c], Am[1][c], is_wet(Hm[c], bm[c], eps)};
-                    Nb<T> N{Bp[c], bp[c], Ap[0][c], Ap[1][c], is_wet(Hp[c], bp[c], eps)};
-                    T ax, ay, phi;
-                    forces(P, B0[c], b, inrow(4, r)[c], A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
-                    const T den = T(1) + tauT * phi;
-                    utx = (ux + tauT * ax) / den;
-                    uty = (uy + tauT * ay) / den;
+            // S3: forces at t_{n+1/2}, corrector and sources
+            {
+                const int r = k - LAG3;
+                if (r >= 3 && r <= nrows - 4 && c >= 3 && c < WIN - 3) {
+                    const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
+                    const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
+                    const T *B0 = s.bH[r % DB], *Bm = s.bH[(r - 1) % DB], *Bp = s.bH[(r + 1) % DB];
+                    const T(*A0)[WIN] = s.aU[r % DA];
+                    const T(*Am)[WIN] = s.aU[(r - 1) % DA];
+                    const T(*Ap)[WIN] = s.aU[(r + 1) % DA];
+                    const T H = H0[c], b = b0[c];
+                    const T ux = s.pU[r % DP][0][c], uy = s.pU[r % DP][1][c];
+                    T utx = T(0), uty = T(0);
+                    if (is_wet(H, b, eps)) {
+                        Nb<T> W{B0[c - 1], b0[c - 1], A0[0][c - 1], A0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
+                        Nb<T> E{B0[c + 1], b0[c + 1], A0[0][c + 1], A0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
+                        Nb<T> S{Bm[c], bm[c], Am[0][c], Am[1][c], is_wet(Hm[c], bm[c], eps)};
+                        Nb<T> N{Bp[c], bp[c], Ap[0][c], Ap[1][c], is_wet(Hp[c], bp[c], eps)};
+                        T ax, ay, phi;
+                        forces(P, B0[c], b, rN(r)[c], A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
+                        const T den = T(1) + tauT * phi;
+                        utx = (ux + tauT * ax) / den;
+                        uty = (uy + tauT * ay) / den;
+                    }
+                    const T uhx = T(0.5) * (ux + utx), uhy = T(0.5) * (uy + uty);
+                    T sig = T(0), vx = T(0), vy = T(0);
+                    while (sp < se && a.src[sp].r < r) ++sp;
+                    for (int q = sp; q < se && a.src[q].r == r; ++q) {
+                        if (a.src[q].c == c) {
+                            sig = (T)(a.src[q].w * s.hq[a.src[q].hydro]);
+                            vx = (T)a.src[q].vx;
+                            vy = (T)a.src[q].vy;
+                        }
+                    }
+                    const T ts = tauT * sig;
+                    const T ht = tmax(T(0), H + ts);
+                    const T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
+                    const T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
+                    const bool wt = is_wet(ht, b, eps);
+                    T(*C)[WIN] = s.cS[r % DC];
+                    C[0][c] = ht;
+                    C[1][c] = uhx;
+                    C[2][c] = uhy;
+                    C[3][c] = wt ? qtx / ht : T(0);
+                    C[4][c] = wt ? qty / ht : T(0);
+                    C[5][c] = qtx;
+                    C[6][c] = qty;
+                    if (out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
                 }
-                const T uhx = T(0.5) * (ux + utx), uhy = T(0.5) * (uy + uty);
-                T sig = T(0), vx = T(0), vy = T(0);
-                while (sp < se && a.src[sp].r < r) ++sp;
-                for (int q = sp; q < se && a.src[q].r == r; ++q) {
-                    if (a.src[q].c == c) {
-                        sig = (T)(a.src[q].w * s.hq[a.src[q].hydro]);
-                        vx = (T)a.src[q].vx;
-                        vy = (T)a.src[q].vy;
+            }
+        } else {
+            // S4: MUSCL slopes and face fluxes of row k-8 (and its y face below)
+            {
+                const int r = k - LAG4;
+                auto ecell = [&](int rr, int col) {
+                    ECell<T> e;
+                    const T(*C)[WIN] = s.cS[rr % DC];
+                    const T bb = rB(rr)[col];
+                    e.w[0] = C[0][col];
+                    e.w[1] = C[1][col];
+                    e.w[2] = C[2][col];
+                    e.w[3] = C[3][col];
+                    e.w[4] = C[4][col];
+                    e.b = bb;
+                    e.wt = is_wet(e.w[0], bb, eps);
+                    return e;
+                };
+                if (r >= 4 && r <= nrows - 5 && c >= 3 && c < WIN - 3) {
+                    const ECell<T> em = ecell(r - 1, c), e0 = ecell(r, c), ep = ecell(r + 1, c);
+                    T syc[5];
+                    slopes(em, e0, ep, syc);
+                    if (r >= 5) face_flux(P, em, syPrev, e0, syc, 2, fyCur[0], fyCur[1], fyCur[2]);
+#pragma unroll
+                    for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
+                    if (r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 6) {
+                        const ECell<T> xm = ecell(r, c - 1), x1 = ecell(r, c + 1), x2 = ecell(r, c + 2);
+                        T sL[5], sR[5];
+                        slopes(xm, e0, x1, sL);
+                        slopes(e0, x1, x2, sR);
+                        T FH, FQx, FQy;
+                        face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
+                        s.fX[r % DF][0][c] = FH;
+                        s.fX[r % DF][1][c] = FQx;
+                        s.fX[r % DF][2][c] = FQy;
                     }
                 }
-                const T ts = tauT * sig;
-                const T ht = tmax(T(0), H + ts);
-                const T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
-                const T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
-                const bool wt = is_wet(ht, b, eps);
-                T(*C)[WIN] = s.cS[r % 3];
-                C[0][c] = ht;
-                C[1][c] = uhx;
-                C[2][c] = uhy;
-                C[3][c] = wt ? qtx / ht : T(0);
-                C[4][c] = wt ? qty / ht : T(0);
-                C[5][c] = qtx;
-                C[6][c] = qty;
-                if (out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
             }
-        }
-        __syncthreads();
-        // (e) MUSCL slopes and face fluxes at row k-4 (y face below it)
-        {
-            const int r = k - 4;
-            auto ecell = [&](int rr, int col) {
-                ECell<T> e;
-                const T ht = s.cS[rr % 3][0][col];
-                const T bb = inrow(3, rr)[col];
-                e.w[0] = ht;
-                e.w[1] = s.cS[rr % 3][1][col];
-                e.w[2] = s.cS[rr % 3][2][col];
-                e.w[3] = s.cS[rr % 3][3][col];
-                e.w[4] = s.cS[rr % 3][4][col];
-                e.b = bb;
-                e.wt = is_wet(ht, bb, eps);
-                return e;
-            };
-            if (r >= 4 && r <= nrows - 5 && c >= 3 && c < WIN - 3) {
-                const ECell<T> em = ecell(r - 1, c), e0 = ecell(r, c), ep = ecell(r + 1, c);
-                T syc[5];
-                slopes(em, e0, ep, syc);
-                if (r >= 5) face_flux(P, em, syPrev, e0, syc, 2, fyCur[0], fyCur[1], fyCur[2]);
+            // S6: final update of row k-9 (K8)
+            {
+                const int r = k - LAG6;
+                if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
+                    const T(*FX)[WIN] = s.fX[r % DF];
+                    const T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
+                    const T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
+                    const T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
+                    const T(*C)[WIN] = s.cS[r % DC];
+                    T hn = C[0][c] + dth * fh;
+                    double clip = 0.0;
+                    if (hn < T(0)) {
+                        clip = -(double)hn;
+                        hn = T(0);
+                    }
+                    T qxn = T(0), qyn = T(0);
+                    if (hn > eps) {
+                        qxn = C[5][c] + dth * fqx;
+                        qyn = C[6][c] + dth * fqy;
+                    }
+                    const T b = rB(r)[c];
+                    const bool wetn = is_wet(hn, b, eps);
+                    s.nS[r % DN][0][c] = hn;
+                    s.nS[r % DN][1][c] = wetn ? qxn / hn : T(0);
+                    s.nS[r % DN][2][c] = wetn ? qyn / hn : T(0);
+                    if (out_col && r >= HALO && r < HALO + sh) {
+                        const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
+                        outH[gi] = hn;
+                        outQx[gi] = qxn;
+                        outQy[gi] = qyn;
+                        acc_mass += (double)hn;
+                        acc_clip += clip;
+                        acc_wet += wetn ? 1 : 0;
+                    }
+                }
 #pragma unroll
-                for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
-                if (r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 6) {
-                    const ECell<T> xm = ecell(r, c - 1), x1 = ecell(r, c + 1), x2 = ecell(r, c + 2);
-                    T sL[5], sR[5];
-                    slopes(xm, e0, x1, sL);
-                    slopes(e0, x1, x2, sR);
-                    T FH, FQx, FQy;
-                    face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
-                    s.fX[r & 1][0][c] = FH;
-                    s.fX[r & 1][1][c] = FQx;
-                    s.fX[r & 1][2][c] = FQy;
+                for (int q = 0; q < 3; ++q) fyPrev[q] = fyCur[q];
+            }
+            // S7: signal speed of the new state at row k-11 (next step's K3)
+            {
+                const int r = k - LAG7;
+                if (r >= HALO && r < HALO + sh && out_col) {
+                    const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
+                    const int i0 = r % DN, im = (r - 1) % DN, ip = (r + 1) % DN;
+                    const T H = s.nS[i0][0][c], b = b0[c];
+                    if (is_wet(H, b, eps)) {
+                        const T ux = s.nS[i0][1][c], uy = s.nS[i0][2][c];
+                        Nb<T> W{s.nS[i0][0][c - 1], b0[c - 1], s.nS[i0][1][c - 1], s.nS[i0][2][c - 1],
+                                is_wet(s.nS[i0][0][c - 1], b0[c - 1], eps)};
+                        Nb<T> E{s.nS[i0][0][c + 1], b0[c + 1], s.nS[i0][1][c + 1], s.nS[i0][2][c + 1],
+                                is_wet(s.nS[i0][0][c + 1], b0[c + 1], eps)};
+                        Nb<T> S{s.nS[im][0][c], bm[c], s.nS[im][1][c], s.nS[im][2][c],
+                                is_wet(s.nS[im][0][c], bm[c], eps)};
+                        Nb<T> N{s.nS[ip][0][c], bp[c], s.nS[ip][1][c], s.nS[ip][2][c],
+                                is_wet(s.nS[ip][0][c], bp[c], eps)};
+                        T ax, ay, phi;
+                        forces(P, H, b, rN(r)[c], ux, uy, W, E, S, N, ax, ay, phi);
+                        const double v = (double)cell_speed(P, H, ux, uy, ax, ay);
+                        if (!(v <= DBL_MAX)) bad = true;
+                        else if (v > vmax) vmax = v;
+                    }
                 }
             }
-        }
-        __syncthreads();
-        // (f) final update at row k-5 (K8)
-        {
-            const int r = k - 5;
-            if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
-                const T(*FX)[WIN] = s.fX[r & 1];
-                const T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
-                const T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
-                const T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
-                const T(*C)[WIN] = s.cS[r % 3];
-                T hn = C[0][c] + dth * fh;
-                double clip = 0.0;
-                if (hn < T(0)) {
-                    clip = -(double)hn;
-                    hn = T(0);
-                }
-                T qxn = T(0), qyn = T(0);
-                if (hn > eps) {
-                    qxn = C[5][c] + dth * fqx;
-                    qyn = C[6][c] + dth * fqy;
-                }
-                const T b = inrow(3, r)[c];
-                const bool wetn = is_wet(hn, b, eps);
-                s.nS[r % 3][0][c] = hn;
-                s.nS[r % 3][1][c] = wetn ? qxn / hn : T(0);
-                s.nS[r % 3][2][c] = wetn ? qyn / hn : T(0);
-                if (out_col && r >= HALO && r < HALO + sh) {
-                    const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
-                    outH[gi] = hn;
-                    outQx[gi] = qxn;
-                    outQy[gi] = qyn;
-                    acc_mass += (double)hn;
-                    acc_clip += clip;
-                    acc_wet += wetn ? 1 : 0;
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < 3; ++q) fyPrev[q] = fyCur[q];
         }
         __syncthreads();
     }
 
     // per-CTA partials, the next step's signal speed, and the step report
-    const double bmax = block_max<WIN>(vmax, s.red);
-    const double bmass = block_sum<WIN>(acc_mass, s.red);
-    const double bsrc = block_sum<WIN>(acc_src, s.red);
-    const double bclip = block_sum<WIN>(acc_clip, s.red);
-    const double bwet = block_sum<WIN>((double)acc_wet, s.red);
+    const double bmax = block_max<NT>(vmax, s.red);
+    const double bmass = block_sum<NT>(acc_mass, s.red);
+    const double bsrc = block_sum<NT>(acc_src, s.red);
+    const double bclip = block_sum<NT>(acc_clip, s.red);
+    const double bwet = block_sum<NT>((double)acc_wet, s.red);
     const int anybad = __syncthreads_or(bad);
-    if (c == 0) {
+    if (tid == 0) {
         Part p;
         p.mass = bmass;
         p.src = bsrc;
@@ -468,17 +495,17 @@ __global__ void __launch_bounds__(WIN, sizeof(T) == 4 ? 3 : 1) k_fused(const __g
     if (s.last) {
         __threadfence();
         double m = 0.0, sr = 0.0, cl = 0.0, w = 0.0;
-        for (int i = c; i < a.nitems; i += WIN) {
+        for (int i = tid; i < a.nitems; i += NT) {
             m += __ldcg(&a.parts[i].mass);
             sr += __ldcg(&a.parts[i].src);
             cl += __ldcg(&a.parts[i].clip);
             w += (double)__ldcg(&a.parts[i].wet);
         }
-        m = block_sum<WIN>(m, s.red);
-        sr = block_sum<WIN>(sr, s.red);
-        cl = block_sum<WIN>(cl, s.red);
-        w = block_sum<WIN>(w, s.red);
-        if (c == 0) {
+        m = block_sum<NT>(m, s.red);
+        sr = block_sum<NT>(sr, s.red);
+        cl = block_sum<NT>(cl, s.red);
+        w = block_sum<NT>(w, s.red);
+        if (tid == 0) {
             const double h = (double)P.h;
             Ctl* ctl = a.ctl;
             ctl->mass = m * h * h;
@@ -502,12 +529,12 @@ cudaError_t prepare_fused(int* ctas_per_sm) {
     const size_t smem = fused_smem_bytes<T>();
     cudaError_t e = cudaFuncSetAttribute(k_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fused<T>, WIN, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fused<T>, NT, smem);
 }
 
 template <class T>
 cudaError_t launch_fused(const FusedArgs<T>& a, cudaStream_t st) {
-    k_fused<T><<<a.nitems, WIN, fused_smem_bytes<T>(), st>>>(a);
+    k_fused<T><<<a.nitems, NT, fused_smem_bytes<T>(), st>>>(a);
     return cudaGetLastError();
 }
 
