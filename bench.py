@@ -63,6 +63,65 @@ def flooded_workload(name):
     return I.Problem(name, p.params, p.b, p.n_manning, H, z, z.copy(), p.sources).to_f32_values(), eta0
 
 
+def flooded_ensemble(n):
+    """The batched-ensemble workload: n scenarios with N uniform in
+    [512, 2048], each filled to its median terrain height."""
+    probs, gates = I.ensemble(n)
+    out = []
+    for p in probs:
+        eta0 = float(np.median(p.b))
+        H = np.maximum(0.0, eta0 - p.b)
+        z = np.zeros_like(H)
+        out.append(I.Problem(p.name, p.params, p.b, p.n_manning, H, z, z.copy(), p.sources, p.solid).to_f32_values())
+    return out, gates
+
+
+def run_ensemble(args, torch, swe, stream, rank, world):
+    """Batched ensemble: all scenarios advance in one persistent launch per
+    step (CUDA graph of K steps); value counts every scenario's cells."""
+    n = int(args.workload.split("-")[1])
+    probs, gates = flooded_ensemble(n)
+    cells = sum(p.params.nx * p.params.ny for p in probs)
+    sols = [swe.Solver.from_problem(p, args.precision, stream=stream.cuda_stream) for p in probs]
+    batch = swe.Batch(sols)
+    seg = batch.autotune(2)
+    batch.step(args.steps, report=False)
+    for _ in range(args.warmup):
+        batch.step(1, report=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        batch.step(args.steps, report=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    infos = batch.step(0)
+    batch.close()
+    for x in sols:
+        x.close()
+    value = world * cells * args.steps / (ms * 1e-3) / 1e9
+    achieved = BYTES_PER_CELL[args.precision] * cells / (ms / args.steps * 1e-3) / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = json.load(open(peaks_path))["hbm_gbs"] if os.path.exists(peaks_path) else 6800.0
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": args.workload, "scenarios": n, "cells": cells,
+                           "sizes": [min(p.params.nx for p in probs), max(p.params.nx for p in probs)],
+                           "seg_h_autotuned": seg, "gates": int(sum(len(g.ix) for g in gates)),
+                           "wet_cells_end": int(sum(i["wet_cells"] for i in infos)),
+                           "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None, "kernel": "k_fused_batch<float>",
+                             "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision]},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def crop(prob, y0, x0, n):
     s = prob.sources
     keep = (s.ix >= x0) & (s.ix < x0 + n) & (s.iy >= y0) & (s.iy < y0 + n)
@@ -216,6 +275,14 @@ def main():
     from paper_1705_00614_gb300 import build as B
     from paper_1705_00614_gb300 import swe
     B.build()
+
+    if args.workload.startswith("ensemble-"):
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        run_ensemble(args, torch, swe, stream, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     prob, eta0 = flooded_workload(args.workload)
     cells = prob.params.nx * prob.params.ny

@@ -170,6 +170,50 @@ SWE_API void swe_destroy(swe_ctx* ctx);
 SWE_API const char* swe_status_str(int status);
 SWE_API const char* swe_last_error(void);
 
+/* Pick the fused kernel's rows per CTA for this grid by timing trial_steps
+ * steps for each candidate (16 ... 1024 rows) on the current state, which is
+ * restored afterwards (time, step counter and state unchanged).  The choice
+ * does not change any result, only the speed; *seg_h_out (may be NULL)
+ * receives it.  Allocates and frees a temporary copy of the state. */
+SWE_API int swe_autotune(swe_ctx* ctx, int32_t trial_steps, int32_t* seg_h_out);
+
+/* ------------------------------------------------------------------------
+ * Batched ensembles.  The paper's applications need hundreds of simulations
+ * of the same floodplain with different inflow hydrographs and settings of
+ * tens of hydraulic structures (Sec. 1).  A batch advances n contexts
+ * (scenarios of any grid sizes) together: one persistent kernel launch per
+ * step hands the CTAs (scenario, tile) work items from a device list, largest
+ * first; every scenario keeps its own time, time step (its own K3 max),
+ * sources, walls, error word and report, and ends bitwise equal to the same
+ * scenario stepped alone with swe_step (same tiling).
+ * ------------------------------------------------------------------------ */
+typedef struct swe_batch swe_batch; /* opaque */
+
+/* Batch over n >= 1 distinct SWE_FUSED contexts of one precision on one
+ * device, each with a state set.  The batch borrows the contexts (destroy it
+ * before them) and runs on the first context's stream.  Contexts may still
+ * be changed (sources, terrain, gates, state) between batch steps. */
+SWE_API int swe_batch_create(swe_ctx* const* ctxs, int32_t n, swe_batch** out);
+
+/* Gate toggles applied on the device inside the batch's step sequence:
+ * event m closes (closed[m] = 1) or opens cell (ix[m], iy[m]) of scenario
+ * scen[m] just before batch step step[m] (counted from the batch's creation),
+ * then recomputes that scenario's time-step speed, exactly as swe_set_solid
+ * between two swe_step calls would.  Replaces earlier events. */
+SWE_API int swe_batch_set_gate_events(swe_batch* b, int32_t n, const int32_t* scen, const int32_t* ix,
+                                      const int32_t* iy, const int64_t* step, const uint8_t* closed);
+
+/* Advance every scenario nsteps steps (one CUDA graph: per step, the gate
+ * events due, then one batched launch).  With infos != NULL (n entries) the
+ * stream is synchronised and each scenario's report copied out. */
+SWE_API int swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos);
+
+/* Autotuner: one rows-per-CTA value for all scenarios, chosen by timing
+ * trial_steps batched steps per candidate; states are restored. */
+SWE_API int swe_batch_autotune(swe_batch* b, int32_t trial_steps, int32_t* seg_h_out);
+
+SWE_API void swe_batch_destroy(swe_batch* b);
+
 /* ------------------------------------------------------------------------
  * Allocation-free step.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- programs whose

@@ -2,6 +2,7 @@
 // tiling, CUDA graphs and the C ABI declared in include/swe.h.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <cstring>
 #include <new>
 #include <string>
@@ -103,6 +104,10 @@ struct swe_ctx {
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0;
     bool has_state = false;
+    // host copies of the sources (to rebuild the per-item tables on retiling)
+    std::vector<int32_t> hs_ix, hs_iy, hs_hy;
+    std::vector<double> hs_w, hs_vx, hs_vy;
+    unsigned long long generation = 0;  // bumps when device pointers or tiling change
 };
 
 namespace {
@@ -393,6 +398,198 @@ int apply_beds(swe_ctx* c, const std::vector<int>& cells) {
     return SWE_OK;
 }
 
+// Re-tile a fused context: new segment height, per-item source tables and
+// partial-sum capacity.
+int retile(swe_ctx* c, int seg_h) {
+    c->p.seg_h = seg_h;
+    choose_tiling(c);
+    if (c->nitems > c->parts_cap) {
+        CK(cudaStreamSynchronize(c->st));
+        cudaFree(c->parts);
+        cudaFree(c->parts2);
+        c->parts = nullptr;
+        c->parts2 = nullptr;
+        c->parts_cap = c->nitems;
+        if (cudaMalloc(&c->parts, c->parts_cap * sizeof(Part)) != cudaSuccess ||
+            cudaMalloc(&c->parts2, c->parts_cap * sizeof(Part)) != cudaSuccess)
+            return fail(SWE_ERR_OOM, "partials");
+    }
+    drop_graph(c);
+    c->generation++;
+    const int n = c->nsrc;
+    return build_source_tables(c, n ? c->hs_ix.data() : nullptr, n ? c->hs_iy.data() : nullptr,
+                               n ? c->hs_w.data() : nullptr, n ? c->hs_vx.data() : nullptr,
+                               n ? c->hs_vy.data() : nullptr, n ? c->hs_hy.data() : nullptr);
+}
+
+// Device copy of a context's current state and control block, for trial
+// runs that must leave the state as it was.
+struct Snapshot {
+    void* planes[3] = {nullptr, nullptr, nullptr};
+    Ctl ctl;
+    int buf = 0;
+};
+
+int snapshot_take(swe_ctx* c, Snapshot& sn) {
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    sn.ctl = *c->ctl_host;
+    sn.buf = (int)(sn.ctl.step & 1);
+    for (int k = 0; k < 3; ++k) {
+        if (cudaMalloc(&sn.planes[k], c->plane) != cudaSuccess) return fail(SWE_ERR_OOM, "snapshot");
+        CK(cudaMemcpyAsync(sn.planes[k], c->f[3 * sn.buf + k], c->plane, cudaMemcpyDeviceToDevice, c->st));
+    }
+    return SWE_OK;
+}
+
+int snapshot_restore(swe_ctx* c, Snapshot& sn) {
+    for (int k = 0; k < 3; ++k)
+        CK(cudaMemcpyAsync(c->f[3 * sn.buf + k], sn.planes[k], c->plane, cudaMemcpyDeviceToDevice, c->st));
+    *c->ctl_host = sn.ctl;
+    CK(cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    return SWE_OK;
+}
+
+void snapshot_free(Snapshot& sn) {
+    for (void*& q : sn.planes) {
+        cudaFree(q);
+        q = nullptr;
+    }
+}
+
+const int kTileCandidates[] = {16, 32, 64, 128, 256, 512, 1024};
+
+}  // namespace
+
+struct swe_batch {
+    std::vector<swe_ctx*> ctx;
+    bool f64 = false;
+    int dev = 0;
+    cudaStream_t st = nullptr;
+    void* d_descs = nullptr;
+    int2* d_work = nullptr;
+    int nwork = 0;
+    BatchCtl* bc = nullptr;
+    int grid = 0;
+    std::vector<unsigned long long> gen;
+    struct Ev {
+        long long step;
+        int scen;
+        int cell;
+        uint8_t closed;
+    };
+    std::vector<Ev> events;   // sorted by step
+    int* d_ev_idx = nullptr;  // padded bed index of each event
+    double* d_ev_val = nullptr;
+    long long step = 0;       // batch steps taken since creation
+    cudaGraphExec_t gexec = nullptr;  // graph of a step window with gate events
+    long long gbase = -1;
+    int gsteps = 0;
+    std::map<int, cudaGraphExec_t> plain;  // event-free windows, by length
+};
+
+namespace {
+
+void batch_drop_graph(swe_batch* b) {
+    if (b->gexec) {
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+        b->gsteps = 0;
+        b->gbase = -1;
+    }
+    for (auto& kv : b->plain) cudaGraphExecDestroy(kv.second);
+    b->plain.clear();
+}
+
+// Scenario descriptors and the work list (largest items first, so the
+// persistent CTAs end together).
+int batch_build(swe_batch* b) {
+    const int n = (int)b->ctx.size();
+    const size_t dsz = b->f64 ? sizeof(FusedArgs<double>) : sizeof(FusedArgs<float>);
+    std::vector<unsigned char> host(dsz * n);
+    struct W {
+        long long cost;
+        int s, i;
+    };
+    std::vector<W> work;
+    for (int k = 0; k < n; ++k) {
+        swe_ctx* c = b->ctx[k];
+        if (b->f64) {
+            FusedArgs<double> a = fused_args<double>(c);
+            std::memcpy(host.data() + dsz * k, &a, dsz);
+        } else {
+            FusedArgs<float> a = fused_args<float>(c);
+            std::memcpy(host.data() + dsz * k, &a, dsz);
+        }
+        for (int i = 0; i < c->nitems; ++i) {
+            const int x0 = (i % c->ntx) * TW, y0 = (i / c->ntx) * c->seg_h;
+            const long long cost = (long long)(std::min(TW, c->p.nx - x0) + 2 * HALO) *
+                                   (std::min(c->seg_h, c->p.ny - y0) + 2 * HALO + 5);
+            work.push_back({cost, k, i});
+        }
+    }
+    std::stable_sort(work.begin(), work.end(), [](const W& x, const W& y) { return x.cost > y.cost; });
+    std::vector<int2> wl(work.size());
+    for (size_t m = 0; m < work.size(); ++m) wl[m] = make_int2(work[m].s, work[m].i);
+    CK(cudaStreamSynchronize(b->st));
+    cudaFree(b->d_descs);
+    cudaFree(b->d_work);
+    b->d_descs = nullptr;
+    b->d_work = nullptr;
+    if (cudaMalloc(&b->d_descs, host.size()) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_work, wl.size() * sizeof(int2)) != cudaSuccess)
+        return fail(SWE_ERR_OOM, "batch descriptors");
+    CK(cudaMemcpy(b->d_descs, host.data(), host.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_work, wl.data(), wl.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    b->nwork = (int)wl.size();
+    b->gen.resize(n);
+    for (int k = 0; k < n; ++k) b->gen[k] = b->ctx[k]->generation;
+    batch_drop_graph(b);
+    return SWE_OK;
+}
+
+int batch_launch_step(swe_batch* b) {
+    if (b->f64) {
+        BatchArgs<double> a{(const FusedArgs<double>*)b->d_descs, b->d_work, b->nwork, b->bc};
+        CK(launch_fused_batch<double>(a, b->grid, b->st));
+    } else {
+        BatchArgs<float> a{(const FusedArgs<float>*)b->d_descs, b->d_work, b->nwork, b->bc};
+        CK(launch_fused_batch<float>(a, b->grid, b->st));
+    }
+    return SWE_OK;
+}
+
+// Gate events scheduled before batch step `s`: new beds, then the signal
+// speed of each touched scenario (as swe_set_solid does for one context).
+int batch_launch_events(swe_batch* b, long long s) {
+    auto lo = std::lower_bound(b->events.begin(), b->events.end(), s,
+                               [](const swe_batch::Ev& e, long long v) { return e.step < v; });
+    auto hi = std::upper_bound(b->events.begin(), b->events.end(), s,
+                               [](long long v, const swe_batch::Ev& e) { return v < e.step; });
+    if (lo == hi) return SWE_OK;
+    std::vector<int> scen;
+    for (auto it = lo; it != hi; ++it) {
+        const size_t m = (size_t)(it - b->events.begin());
+        swe_ctx* c = b->ctx[it->scen];
+        if (b->f64) CK(launch_scatter<double>((double*)c->f[6], b->d_ev_idx + m, b->d_ev_val + m, 1, b->st));
+        else CK(launch_scatter<float>((float*)c->f[6], b->d_ev_idx + m, b->d_ev_val + m, 1, b->st));
+        if (std::find(scen.begin(), scen.end(), it->scen) == scen.end()) scen.push_back(it->scen);
+    }
+    for (int k : scen) {
+        swe_ctx* c = b->ctx[k];
+        if (b->f64) CK(launch_state_speed<double>(staged_args<double>(c), b->st));
+        else CK(launch_state_speed<float>(staged_args<float>(c), b->st));
+    }
+    return SWE_OK;
+}
+
+int batch_sync_all(swe_batch* b) {
+    for (swe_ctx* c : b->ctx) CK(cudaStreamSynchronize(c->st));
+    CK(cudaStreamSynchronize(b->st));
+    return SWE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -603,6 +800,15 @@ int swe_set_sources(swe_ctx* c, int32_t n, const int32_t* ix, const int32_t* iy,
     c->d_hydro = nullptr;
     c->nsrc = n;
     c->nh = nh;
+    c->generation++;
+    c->hs_ix.assign(ix, ix + n);
+    c->hs_iy.assign(iy, iy + n);
+    c->hs_hy.assign(hy, hy + n);
+    c->hs_w.assign(w, w + n);
+    c->hs_vx.assign(n, 0.0);
+    c->hs_vy.assign(n, 0.0);
+    if (vx) c->hs_vx.assign(vx, vx + n);
+    if (vy) c->hs_vy.assign(vy, vy + n);
     const size_t nn = std::max(1, n);
     if (cudaMalloc(&c->d_scell, nn * sizeof(int)) != cudaSuccess ||
         cudaMalloc(&c->d_shydro, nn * sizeof(int)) != cudaSuccess ||
@@ -764,6 +970,268 @@ int swe_sync(swe_ctx* c) {
     if (!c) return fail(SWE_ERR_ARG, "null context");
     CK(cudaStreamSynchronize(c->st));
     return SWE_OK;
+}
+
+int swe_autotune(swe_ctx* c, int32_t trial_steps, int32_t* seg_h_out) {
+    if (!c || trial_steps < 1) return fail(SWE_ERR_ARG, "null context or trial_steps < 1");
+    if (c->p.mode != SWE_FUSED) return fail(SWE_ERR_STATE, "autotuning applies to SWE_FUSED contexts");
+    if (!c->has_state) return fail(SWE_ERR_STATE, "swe_set_state has not been called");
+    CK(cudaSetDevice(c->dev));
+    Snapshot sn;
+    int rc = snapshot_take(c, sn);
+    if (rc) {
+        snapshot_free(sn);
+        return rc;
+    }
+    const int saved = c->p.seg_h;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = c->seg_h;
+    for (int cand : kTileCandidates) {
+        if (cand > 2 * c->p.ny && cand != kTileCandidates[0]) break;
+        rc = retile(c, cand);
+        if (!rc) rc = launch_one_step(c);  // warm-up
+        if (!rc) rc = snapshot_restore(c, sn);
+        if (rc) break;
+        cudaEventRecord(e0, c->st);
+        for (int s = 0; s < trial_steps && !rc; ++s) rc = launch_one_step(c);
+        cudaEventRecord(e1, c->st);
+        if (!rc && cudaEventSynchronize(e1) == cudaSuccess) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+        if (!rc) rc = snapshot_restore(c, sn);
+        if (rc) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!rc) rc = retile(c, best);
+    else retile(c, saved);
+    if (!rc) rc = snapshot_restore(c, sn);
+    snapshot_free(sn);
+    if (!rc && seg_h_out) *seg_h_out = best;
+    return rc;
+}
+
+int swe_batch_create(swe_ctx* const* ctxs, int32_t n, swe_batch** out) {
+    if (!ctxs || !out || n < 1) return fail(SWE_ERR_ARG, "null argument or n < 1");
+    *out = nullptr;
+    for (int k = 0; k < n; ++k) {
+        if (!ctxs[k]) return fail(SWE_ERR_ARG, "null context");
+        if (ctxs[k]->p.mode != SWE_FUSED) return fail(SWE_ERR_ARG, "batched contexts must be SWE_FUSED");
+        if (ctxs[k]->p.precision != ctxs[0]->p.precision) return fail(SWE_ERR_ARG, "mixed precisions");
+        if (ctxs[k]->dev != ctxs[0]->dev) return fail(SWE_ERR_ARG, "contexts on different devices");
+        if (!ctxs[k]->has_state) return fail(SWE_ERR_STATE, "a context has no state");
+        for (int j = 0; j < k; ++j)
+            if (ctxs[j] == ctxs[k]) return fail(SWE_ERR_ARG, "a context appears twice");
+    }
+    swe_batch* b = new (std::nothrow) swe_batch();
+    if (!b) return fail(SWE_ERR_OOM, "batch");
+    b->ctx.assign(ctxs, ctxs + n);
+    b->f64 = ctxs[0]->p.precision == SWE_F64;
+    b->dev = ctxs[0]->dev;
+    b->st = ctxs[0]->st;
+    auto bail = [&](int code) {
+        std::string m = g_err;
+        swe_batch_destroy(b);
+        return fail(code, m);
+    };
+    if (cudaSetDevice(b->dev) != cudaSuccess) return bail(fail(SWE_ERR_CUDA, "cudaSetDevice"));
+    int occ = 0;
+    cudaError_t e = b->f64 ? prepare_fused_batch<double>(&occ) : prepare_fused_batch<float>(&occ);
+    if (e != cudaSuccess || occ < 1) return bail(fail(SWE_ERR_CUDA, "batch kernel setup"));
+    b->grid = ctxs[0]->sm_count * occ;
+    if (cudaMalloc(&b->bc, sizeof(BatchCtl)) != cudaSuccess) return bail(fail(SWE_ERR_OOM, "batch control"));
+    if (cudaMemset(b->bc, 0, sizeof(BatchCtl)) != cudaSuccess) return bail(fail(SWE_ERR_CUDA, "memset"));
+    int rc = batch_sync_all(b);
+    if (!rc) rc = batch_build(b);
+    if (rc) return bail(rc);
+    *out = b;
+    return SWE_OK;
+}
+
+int swe_batch_set_gate_events(swe_batch* b, int32_t n, const int32_t* scen, const int32_t* ix, const int32_t* iy,
+                              const int64_t* step, const uint8_t* closed) {
+    if (!b || n < 0 || (n > 0 && (!scen || !ix || !iy || !step || !closed))) return fail(SWE_ERR_ARG, "event arrays");
+    std::vector<swe_batch::Ev> ev;
+    for (int m = 0; m < n; ++m) {
+        if (scen[m] < 0 || scen[m] >= (int)b->ctx.size()) return fail(SWE_ERR_ARG, "event scenario");
+        swe_ctx* c = b->ctx[scen[m]];
+        if (ix[m] < 0 || ix[m] >= c->p.nx || iy[m] < 0 || iy[m] >= c->p.ny) return fail(SWE_ERR_ARG, "event cell");
+        if (closed[m] > 1 || step[m] < 0) return fail(SWE_ERR_ARG, "event step or state");
+        ev.push_back({(long long)step[m], scen[m], iy[m] * c->p.nx + ix[m], closed[m]});
+    }
+    std::stable_sort(ev.begin(), ev.end(), [](const swe_batch::Ev& x, const swe_batch::Ev& y) { return x.step < y.step; });
+    CK(cudaSetDevice(b->dev));
+    int rc = batch_sync_all(b);
+    if (rc) return rc;
+    batch_drop_graph(b);
+    cudaFree(b->d_ev_idx);
+    cudaFree(b->d_ev_val);
+    b->d_ev_idx = nullptr;
+    b->d_ev_val = nullptr;
+    b->events = ev;
+    if (ev.empty()) return SWE_OK;
+    std::vector<int> idx(ev.size());
+    std::vector<double> val(ev.size());
+    for (size_t m = 0; m < ev.size(); ++m) {
+        swe_ctx* c = b->ctx[ev[m].scen];
+        const int i = ev[m].cell % c->p.nx, j = ev[m].cell / c->p.nx;
+        idx[m] = (j + PAD) * c->pitch + (i + PAD);
+        val[m] = ev[m].closed ? WALL_BED : c->h_b[ev[m].cell];
+    }
+    if (cudaMalloc(&b->d_ev_idx, idx.size() * sizeof(int)) != cudaSuccess ||
+        cudaMalloc(&b->d_ev_val, val.size() * sizeof(double)) != cudaSuccess)
+        return fail(SWE_ERR_OOM, "events");
+    CK(cudaMemcpy(b->d_ev_idx, idx.data(), idx.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(b->d_ev_val, val.data(), val.size() * sizeof(double), cudaMemcpyHostToDevice));
+    return SWE_OK;
+}
+
+int swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos) {
+    if (!b || nsteps < 0) return fail(SWE_ERR_ARG, "null batch or nsteps < 0");
+    CK(cudaSetDevice(b->dev));
+    int rc = SWE_OK;
+    bool stale = false;
+    for (size_t k = 0; k < b->ctx.size(); ++k) stale |= b->ctx[k]->generation != b->gen[k];
+    rc = batch_sync_all(b);
+    if (!rc && stale) rc = batch_build(b);
+    if (rc) return rc;
+    for (swe_ctx* c : b->ctx) CK(launch_set_tend(c->ctl, 0.0, b->st));
+    if (nsteps > 0) {
+        // a window without gate events is the same graph at every base step
+        const bool has_ev = std::any_of(b->events.begin(), b->events.end(), [&](const swe_batch::Ev& e) {
+            return e.step >= b->step && e.step < b->step + nsteps;
+        });
+        cudaGraphExec_t* slot = nullptr;
+        if (!has_ev) {
+            slot = &b->plain[nsteps];
+        } else {
+            if (!(b->gexec && b->gbase == b->step && b->gsteps == nsteps) && b->gexec) {
+                cudaGraphExecDestroy(b->gexec);
+                b->gexec = nullptr;
+            }
+            slot = &b->gexec;
+        }
+        if (!*slot) {
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal));
+            for (int s = 0; s < nsteps && !rc; ++s) {
+                rc = batch_launch_events(b, b->step + s);
+                if (!rc) rc = batch_launch_step(b);
+            }
+            cudaError_t e = cudaStreamEndCapture(b->st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(SWE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(slot, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(SWE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            if (has_ev) {
+                b->gbase = b->step;
+                b->gsteps = nsteps;
+            }
+        }
+        CK(cudaGraphLaunch(*slot, b->st));
+        // host record of the walls the events have set
+        for (const auto& ev : b->events)
+            if (ev.step >= b->step && ev.step < b->step + nsteps) b->ctx[ev.scen]->h_solid[ev.cell] = ev.closed;
+        b->step += nsteps;
+    }
+    if (infos) {
+        for (size_t k = 0; k < b->ctx.size(); ++k)
+            CK(cudaMemcpyAsync(&b->ctx[k]->ctl_host[0], b->ctx[k]->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, b->st));
+        CK(cudaStreamSynchronize(b->st));
+        for (size_t k = 0; k < b->ctx.size(); ++k) {
+            const Ctl& h = *b->ctx[k]->ctl_host;
+            swe_step_info* info = &infos[k];
+            info->t = h.t;
+            info->dt_last = h.tau_last;
+            info->mass = h.mass;
+            info->src_vol = h.src_vol;
+            info->clip_vol = h.clip_vol;
+            info->max_speed = h.max_speed;
+            info->wet_cells = h.wet;
+            info->step = h.step;
+            info->err_word = (int32_t)h.err;
+            info->pad = 0;
+            if (h.err & ERR_TIMEOUT) rc = fail(SWE_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
+            else if ((h.err & ERR_NONFINITE) && !rc) rc = fail(SWE_ERR_NONFINITE, "non-finite signal speed");
+        }
+    }
+    return rc;
+}
+
+int swe_batch_autotune(swe_batch* b, int32_t trial_steps, int32_t* seg_h_out) {
+    if (!b || trial_steps < 1) return fail(SWE_ERR_ARG, "null batch or trial_steps < 1");
+    CK(cudaSetDevice(b->dev));
+    int rc = batch_sync_all(b);
+    if (rc) return rc;
+    const size_t n = b->ctx.size();
+    std::vector<Snapshot> sn(n);
+    for (size_t k = 0; k < n && !rc; ++k) rc = snapshot_take(b->ctx[k], sn[k]);
+    auto restore_all = [&]() {
+        int r = SWE_OK;
+        for (size_t k = 0; k < n && !r; ++k) r = snapshot_restore(b->ctx[k], sn[k]);
+        return r;
+    };
+    int maxny = 0;
+    for (swe_ctx* c : b->ctx) maxny = std::max(maxny, c->p.ny);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best_ms = 1e30f;
+    int best = kTileCandidates[0];
+    for (int cand : kTileCandidates) {
+        if (rc) break;
+        if (cand > 2 * maxny && cand != kTileCandidates[0]) break;
+        for (size_t k = 0; k < n && !rc; ++k) rc = retile(b->ctx[k], cand);
+        if (!rc) rc = batch_build(b);
+        if (!rc) rc = batch_launch_step(b);
+        if (!rc) rc = restore_all();
+        if (rc) break;
+        cudaEventRecord(e0, b->st);
+        for (int s = 0; s < trial_steps && !rc; ++s) rc = batch_launch_step(b);
+        cudaEventRecord(e1, b->st);
+        if (!rc && cudaEventSynchronize(e1) == cudaSuccess) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = cand;
+            }
+        }
+        if (!rc) rc = restore_all();
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (size_t k = 0; k < n && !rc; ++k) rc = retile(b->ctx[k], best);
+    if (!rc) rc = batch_build(b);
+    if (!rc) rc = restore_all();
+    for (auto& x : sn) snapshot_free(x);
+    if (!rc && seg_h_out) *seg_h_out = best;
+    return rc;
+}
+
+void swe_batch_destroy(swe_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->dev);
+    if (b->st) cudaStreamSynchronize(b->st);
+    batch_drop_graph(b);
+    cudaFree(b->d_descs);
+    cudaFree(b->d_work);
+    cudaFree(b->bc);
+    cudaFree(b->d_ev_idx);
+    cudaFree(b->d_ev_val);
+    delete b;
 }
 
 void swe_destroy(swe_ctx* c) {

@@ -174,6 +174,7 @@ struct FSmem {
     double red[NT / 32];
     double tau;
     int last;
+    int witem;
 };
 
 template <class T>
@@ -183,8 +184,8 @@ size_t fused_smem_bytes() {
 
 template <class T>
 __device__ __forceinline__ void issue_chunk(FSmem<T>& s, const FusedArgs<T>& a, int buf, int ch,
-                                            int gx0, int gy0) {
-    unsigned long long* bar = &s.bar[ch % NBAR];
+                                            int gx0, int gy0, unsigned cbase) {
+    unsigned long long* bar = &s.bar[(cbase + (unsigned)ch) % NBAR];
     mbar_expect_tx(bar, 5u * RB * WIN * sizeof(T));
     const int y = gy0 + ch * RB;
     tma_load_2d(&s.inH[ch % SLOT_H][0][0], &a.tmH[buf], gx0, y, bar);
@@ -194,15 +195,15 @@ __device__ __forceinline__ void issue_chunk(FSmem<T>& s, const FusedArgs<T>& a, 
     tma_load_2d(&s.inN[ch % SLOT_N][0][0], &a.tmN, gx0, y, bar);
 }
 
+// One work item (a window of one grid's segment): the whole step for it.
+// `cbase` counts the TMA chunks this CTA has waited for so far, so the
+// mbarrier phases stay consistent across the items a persistent CTA runs.
+// Returns false when a bounded wait gave up (the CTA must stop).
 template <class T>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    FSmem<T>& s = *reinterpret_cast<FSmem<T>*>(
-        (reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+__device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, const int item, unsigned& cbase) {
     const int tid = threadIdx.x;
     const int c = tid & (WIN - 1);
     const bool groupL = tid < WIN;
-    const int item = blockIdx.x;
     const int strip = item % a.ntx, seg = item / a.ntx;
     const int x0 = strip * TW, y0 = seg * a.seg_h;
     const int tw = min(TW, a.g.nx - x0), sh = min(a.seg_h, a.g.ny - y0);
@@ -214,20 +215,18 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __gr
     const Phys<T>& P = a.P;
     const T eps = P.eps;
 
-    if (tid == 0) {
-        s.tau = step_tau(a.ctl, a.sp, buf);
-#pragma unroll
-        for (int i = 0; i < NBAR; ++i) mbar_init(&s.bar[i], 1);
-        fence_mbar_init();
-    }
+    if (tid == 0) s.tau = step_tau(a.ctl, a.sp, buf);
     __syncthreads();
     const double tau = s.tau;
-    if (!(tau > 0.0)) return;  // t_end reached: every CTA skips the step
+    if (!(tau > 0.0)) return true;  // t_end reached: every CTA skips the step
     const T tauT = (T)tau;
     const T th = T(0.5) * tauT;
     const T dth = tauT / P.h;
     if (tid < a.nh) s.hq[tid] = hydro_value(a.hydro + 4 * tid, a.ctl->t + 0.5 * (double)tauT);
-    if (tid == 0) issue_chunk(s, a, buf, 0, gx0, gy0);
+    if (tid == 0) {
+        fence_proxy_async();
+        issue_chunk(s, a, buf, 0, gx0, gy0, cbase);
+    }
     __syncthreads();
 
     T* const outH = a.g.H[buf ^ 1];
@@ -255,12 +254,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __gr
             if (ch < nchunks) {
                 if (tid == 0 && ch + 1 < nchunks) {
                     fence_proxy_async();
-                    issue_chunk(s, a, buf, ch + 1, gx0, gy0);
+                    issue_chunk(s, a, buf, ch + 1, gx0, gy0, cbase);
                 }
-                const bool ok = mbar_wait_bounded(&s.bar[ch % NBAR], (unsigned)((ch / NBAR) & 1));
+                const unsigned gch = cbase + (unsigned)ch;
+                const bool ok = mbar_wait_bounded(&s.bar[gch % NBAR], (gch / NBAR) & 1u);
                 if (__syncthreads_or(!ok)) {
                     if (tid == 0) atomicOr(&a.ctl->err, (unsigned)ERR_TIMEOUT);
-                    return;
+                    return false;
                 }
             }
         }
@@ -521,6 +521,61 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __gr
             __threadfence();
         }
     }
+    cbase += (unsigned)nchunks;
+    __syncthreads();
+    return true;
+}
+
+template <class T>
+__device__ __forceinline__ FSmem<T>& fused_smem() {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    return *reinterpret_cast<FSmem<T>*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+}
+
+template <class T>
+__device__ __forceinline__ void fused_init_barriers(FSmem<T>& s) {
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NBAR; ++i) mbar_init(&s.bar[i], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+}
+
+// One grid: CTA b runs work item b.
+template <class T>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
+    FSmem<T>& s = fused_smem<T>();
+    fused_init_barriers(s);
+    unsigned cbase = 0;
+    fused_item(s, a, blockIdx.x, cbase);
+}
+
+// Many grids in one persistent launch (batched ensemble): CTAs take
+// (scenario, item) entries from a device work list until it is exhausted;
+// each scenario keeps its own time, time step, sources, walls and report.
+template <class T>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused_batch(const __grid_constant__ BatchArgs<T> b) {
+    FSmem<T>& s = fused_smem<T>();
+    fused_init_barriers(s);
+    unsigned cbase = 0;
+    while (true) {
+        if (threadIdx.x == 0) s.witem = (int)atomicAdd(&b.bc->next, 1u);
+        __syncthreads();
+        const int w = s.witem;
+        __syncthreads();
+        if (w >= b.nwork) break;
+        const int2 e = b.work[w];
+        if (!fused_item(s, b.descs[e.x], e.y, cbase)) break;
+    }
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (atomicAdd(&b.bc->exited, 1u) == gridDim.x - 1u) {
+            b.bc->next = 0u;
+            b.bc->exited = 0u;
+            __threadfence();
+        }
+    }
 }
 
 // Opt the fused kernel into its shared-memory size; returns CTAs per SM.
@@ -530,6 +585,20 @@ cudaError_t prepare_fused(int* ctas_per_sm) {
     cudaError_t e = cudaFuncSetAttribute(k_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fused<T>, NT, smem);
+}
+
+template <class T>
+cudaError_t prepare_fused_batch(int* ctas_per_sm) {
+    const size_t smem = fused_smem_bytes<T>();
+    cudaError_t e = cudaFuncSetAttribute(k_fused_batch<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fused_batch<T>, NT, smem);
+}
+
+template <class T>
+cudaError_t launch_fused_batch(const BatchArgs<T>& b, int grid, cudaStream_t st) {
+    k_fused_batch<T><<<grid, NT, fused_smem_bytes<T>(), st>>>(b);
+    return cudaGetLastError();
 }
 
 template <class T>
@@ -973,6 +1042,8 @@ cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cud
 #define SWE_INSTANTIATE(T)                                                                           \
     template cudaError_t launch_fused<T>(const FusedArgs<T>&, cudaStream_t);                         \
     template cudaError_t prepare_fused<T>(int*);                                                     \
+    template cudaError_t prepare_fused_batch<T>(int*);                                               \
+    template cudaError_t launch_fused_batch<T>(const BatchArgs<T>&, int, cudaStream_t);              \
     template cudaError_t launch_staged<T>(const StagedArgs<T>&, cudaStream_t);                       \
     template cudaError_t launch_state_speed<T>(const StagedArgs<T>&, cudaStream_t);                  \
     template cudaError_t launch_pack<T>(const double*, T*, int, int, int, cudaStream_t, unsigned*, int); \

@@ -84,6 +84,21 @@ struct FusedArgs {
     int ntx, seg_h, nitems;
 };
 
+// Control block of a batched launch: the next work-list entry to hand out and
+// the CTAs that have run out of work (the last one resets both).
+struct BatchCtl {
+    unsigned next;
+    unsigned exited;
+};
+
+template <class T>
+struct BatchArgs {
+    const FusedArgs<T>* descs;  // one per scenario, in device memory (64-byte aligned)
+    const int2* work;           // (scenario, item), largest items first
+    int nwork;
+    BatchCtl* bc;
+};
+
 template <class T>
 struct StagedArgs {
     Grid<T> g;
@@ -110,6 +125,10 @@ struct StagedArgs {
 
 template <class T>
 cudaError_t prepare_fused(int* ctas_per_sm);
+template <class T>
+cudaError_t prepare_fused_batch(int* ctas_per_sm);
+template <class T>
+cudaError_t launch_fused_batch(const BatchArgs<T>& b, int grid, cudaStream_t st);
 template <class T>
 cudaError_t launch_fused(const FusedArgs<T>& a, cudaStream_t st);
 template <class T>

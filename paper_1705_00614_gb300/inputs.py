@@ -367,6 +367,57 @@ def with_gates(prob: Problem, seed: int, ngates: int) -> Problem:
     return dataclasses.replace(prob, solid=solid)
 
 
+@dataclasses.dataclass
+class GateSchedule:
+    """Gate cells of one scenario: initial state and one toggle step each."""
+    ix: np.ndarray
+    iy: np.ndarray
+    closed0: np.ndarray   # uint8, state at step 0
+    toggle_step: np.ndarray  # int64, step before which the gate flips
+
+
+def ensemble(n: int, seed_base: int = 10000, nmin: int = 512, nmax: int = 2048, dx: float = 10.0,
+             toggle_steps: int = 2000, max_gates: int = 8):
+    """Seeded flood-scenario ensemble: scenario s has a square grid with N
+    uniform in [nmin, nmax], its own fractal terrain (seed seed_base + s)
+    with the carved channel, a 100-cell inflow strip fed by a Gaussian
+    hydrograph with peak time uniform in [1, 6] h, peak uniform in
+    [1, 10] m/s*cells and width t_p / 3, and 0..max_gates gate cells on the
+    channel with a seeded initial state and one seeded toggle step in
+    [0, toggle_steps).  Returns (problems, gate schedules)."""
+    probs, gates = [], []
+    for s in range(n):
+        u = uniform(seed_base, 20, np.arange(4) + 4 * s)
+        N = int(nmin + int(u[0] * (nmax - nmin + 1)))
+        tp = 3600.0 * (1.0 + 5.0 * u[1])
+        peak = 1.0 + 9.0 * u[2]
+        p = floodplain(N, dx, seed_base + s, seed_base + 5000 + s, hydro=Hydrograph(0, peak, tp, tp / 3.0),
+                       nsrc=min(100, N))
+        ng = int(u[3] * (max_gates + 1))
+        g = uniform(seed_base + s, 21, np.arange(3 * max(ng, 1)))
+        xs = (0.2 + 0.7 * g[:ng]) * N
+        ix = xs.astype(np.int64)
+        yc = channel_centre_y((ix + 0.5) * dx, N * dx, N * dx)
+        iy = np.clip((yc // dx).astype(np.int64), 0, N - 1)
+        cells, keep = set(), []
+        for m in range(ng):
+            key = (int(iy[m]), int(ix[m]))
+            if key not in cells:
+                cells.add(key)
+                keep.append(m)
+        keep = np.array(keep, dtype=np.int64)
+        sched = GateSchedule(ix[keep].astype(np.int32) if ng else np.zeros(0, np.int32),
+                             iy[keep].astype(np.int32) if ng else np.zeros(0, np.int32),
+                             (g[ng:2 * ng][keep] < 0.5).astype(np.uint8) if ng else np.zeros(0, np.uint8),
+                             (g[2 * ng:3 * ng][keep] * toggle_steps).astype(np.int64) if ng else np.zeros(0, np.int64))
+        solid = np.zeros((N, N), dtype=np.uint8)
+        if ng:
+            solid[sched.iy, sched.ix] = sched.closed0
+        probs.append(dataclasses.replace(p, name=f"scenario{s}", solid=solid))
+        gates.append(sched)
+    return probs, gates
+
+
 # Named workloads of the benchmark suite, by what they are.
 def workload(name: str) -> Problem:
     if name == "dambreak-256sq-dx1m":

@@ -22,7 +22,9 @@ STATUS = {0: "SWE_OK", -1: "SWE_ERR_ARG", -2: "SWE_ERR_CUDA", -3: "SWE_ERR_OOM",
 
 API = ["swe_params_default", "swe_create", "swe_set_terrain", "swe_set_state", "swe_set_sources",
        "swe_set_solid", "swe_step", "swe_get_state", "swe_get_device_ptrs", "swe_get_stages", "swe_sync",
-       "swe_destroy", "swe_status_str", "swe_last_error", "swe_step_f32_noalloc"]
+       "swe_destroy", "swe_status_str", "swe_last_error", "swe_step_f32_noalloc", "swe_autotune",
+       "swe_batch_create", "swe_batch_set_gate_events", "swe_batch_step", "swe_batch_autotune",
+       "swe_batch_destroy"]
 SWE_PAD = 10
 NOALLOC_MAX_ITEMS = 7000
 
@@ -96,6 +98,19 @@ def load(path=None):
     L.swe_status_str.argtypes = [ctypes.c_int]
     L.swe_last_error.restype = ctypes.c_char_p
     L.swe_last_error.argtypes = []
+    L.swe_autotune.restype = ctypes.c_int
+    L.swe_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    L.swe_batch_create.restype = ctypes.c_int
+    L.swe_batch_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32, ctypes.POINTER(ctypes.c_void_p)]
+    L.swe_batch_set_gate_events.restype = ctypes.c_int
+    L.swe_batch_set_gate_events.argtypes = [ctypes.c_void_p, ctypes.c_int32, _ip, _ip, _ip,
+                                            ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_uint8)]
+    L.swe_batch_step.restype = ctypes.c_int
+    L.swe_batch_step.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(StepInfo)]
+    L.swe_batch_autotune.restype = ctypes.c_int
+    L.swe_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+    L.swe_batch_destroy.restype = None
+    L.swe_batch_destroy.argtypes = [ctypes.c_void_p]
     L.swe_step_f32_noalloc.restype = ctypes.c_int
     L.swe_step_f32_noalloc.argtypes = [ctypes.POINTER(Params)] + [ctypes.c_void_p] * 8 + [
         ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.POINTER(StepInfo)]
@@ -253,3 +268,57 @@ class Solver:
 
     def sync(self):
         _check(self.L, self.L.swe_sync(self.h))
+
+    def autotune(self, trial_steps=3):
+        v = ctypes.c_int32()
+        _check(self.L, self.L.swe_autotune(self.h, int(trial_steps), ctypes.byref(v)))
+        return v.value
+
+
+class Batch:
+    """A batched ensemble over Solver contexts (swe_batch_*)."""
+
+    def __init__(self, solvers):
+        self.L = load()
+        self.solvers = list(solvers)
+        arr = (ctypes.c_void_p * len(self.solvers))(*[x.h.value for x in self.solvers])
+        h = ctypes.c_void_p()
+        _check(self.L, self.L.swe_batch_create(arr, len(self.solvers), ctypes.byref(h)))
+        self.h = h
+
+    def set_gate_events(self, scen, ix, iy, step, closed):
+        scen = np.ascontiguousarray(scen, dtype=np.int32)
+        ix = np.ascontiguousarray(ix, dtype=np.int32)
+        iy = np.ascontiguousarray(iy, dtype=np.int32)
+        step = np.ascontiguousarray(step, dtype=np.int64)
+        closed = np.ascontiguousarray(closed, dtype=np.uint8)
+        _check(self.L, self.L.swe_batch_set_gate_events(
+            self.h, len(scen), scen.ctypes.data_as(_ip), ix.ctypes.data_as(_ip), iy.ctypes.data_as(_ip),
+            step.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), closed.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+
+    def step(self, nsteps=1, report=True):
+        infos = (StepInfo * len(self.solvers))() if report else None
+        _check(self.L, self.L.swe_batch_step(self.h, int(nsteps), infos))
+        return [i.as_dict() for i in infos] if report else None
+
+    def autotune(self, trial_steps=2):
+        v = ctypes.c_int32()
+        _check(self.L, self.L.swe_batch_autotune(self.h, int(trial_steps), ctypes.byref(v)))
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.swe_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
