@@ -215,6 +215,61 @@ SWE_API int swe_batch_autotune(swe_batch* b, int32_t trial_steps, int32_t* seg_h
 SWE_API void swe_batch_destroy(swe_batch* b);
 
 /* ------------------------------------------------------------------------
+ * Learned closure for a 4x coarser grid level.  The paper simulates on
+ * hierarchical grids, a coarse grid for deep channels and finer grids where
+ * the flow needs them (Sec. 2.2, Fig. 1), with fine-to-coarse feedback; it
+ * gives no closure model.  This library adds one: a 4-layer network of 3x3
+ * convolutions, channels 5 -> 32 -> 32 -> 32 -> 3 with ReLU between layers,
+ * that maps standardised coarse inputs (H, Ux, Uy, b, n_M) to corrections of
+ * the coarse cells' net face-flux sums (the Fh, Fv of K8).  Convolutions run
+ * on tensor cores with BF16 weights and activations and FP32 accumulation.
+ *
+ * A swe_cnn holds FP32 master parameters (flat: for each layer l, weights
+ * [3][3][c_l][c_{l+1}] then biases [c_{l+1}]), Adam moments and the
+ * activation buffers of one batch shape: n images of h x w pixels (h a
+ * multiple of 8, w a multiple of 16).  Inputs x are device BF16
+ * [n][h][w][16] (channels 5..15 zero); targets and outputs are device FP32
+ * [n][h][w][3].  Runs on `stream` (NULL: a stream the object owns).
+ * ------------------------------------------------------------------------ */
+typedef struct swe_cnn swe_cnn; /* opaque */
+SWE_API int swe_cnn_create(int32_t n, int32_t h, int32_t w, void* stream, swe_cnn** out);
+SWE_API int swe_cnn_num_params(const swe_cnn* c);
+/* Parameters from/to host FP32 (setting them resets the Adam moments). */
+SWE_API int swe_cnn_set_params(swe_cnn* c, const float* params);
+SWE_API int swe_cnn_get_params(swe_cnn* c, float* params);
+/* Forward pass; y (device FP32 [n][h][w][3]) may be NULL. */
+SWE_API int swe_cnn_forward(swe_cnn* c, const void* x, float* y);
+/* Mean-squared-error loss against target and its gradient with respect to
+ * every parameter (host FP32, flat layout); synchronises. */
+SWE_API int swe_cnn_gradients(swe_cnn* c, const void* x, const float* target, float* grads, double* loss);
+/* One training step: forward, loss, backward, Adam (beta 0.9/0.999, eps 1e-8,
+ * learning rate lr).  loss may be NULL (then nothing is synchronised). */
+SWE_API int swe_cnn_train_step(swe_cnn* c, const void* x, const float* target, float lr, double* loss);
+SWE_API void swe_cnn_destroy(swe_cnn* c);
+
+/* Coarse state := 4x4 block means of the fine state (H, Qx, Qy: mass and
+ * momentum preserving), time := the fine time, step counter 0; fine is
+ * exactly 4x coarse in both directions.  Synchronises both streams. */
+SWE_API int swe_restrict_state(swe_ctx* fine, swe_ctx* coarse);
+/* Standardised network inputs of the context's state into x (device BF16
+ * [ny][nx][16]); norm_in = mu[5], sd[5] (host).  Synchronises. */
+SWE_API int swe_closure_features(swe_ctx* ctx, const float* norm_in, void* x);
+/* Standardised training targets into t (device FP32 [ny][nx][3]): the flux-
+ * sum corrections (ref - pred) h / tau that turn the coarse step just taken
+ * by `pred` into the restricted fine state held by `ref`; norm_out = mu[3],
+ * sd[3] (host).  Synchronises. */
+SWE_API int swe_closure_targets(swe_ctx* pred, swe_ctx* ref, const float* norm_out, float* t);
+/* Attach (cnn != NULL) or detach a trained network of batch shape
+ * (1, ny, nx) to a fused context, with norm = input mu[5], sd[5], output
+ * mu[3], sd[3] (host).  The context borrows the network. */
+SWE_API int swe_closure_attach(swe_ctx* ctx, swe_cnn* cnn, const float* norm);
+/* Closed coarse steps: per step, the network predicts corrections of the net
+ * face-flux sums from the state at t_n, their depth part is centred over
+ * wet cells (the corrections add no mass), and the fused step adds them in
+ * its final update (K8).  nsteps >= 2 run as one CUDA graph. */
+SWE_API int swe_step_closed(swe_ctx* ctx, int32_t nsteps, swe_step_info* info);
+
+/* ------------------------------------------------------------------------
  * Allocation-free step.  The paper has no counterpart: this entry point
  * exists for callers that cannot allocate device memory -- programs whose
  * device memory all comes from a host framework's own pool or arena, that

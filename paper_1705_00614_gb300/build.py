@@ -23,6 +23,7 @@ UNITS = [
     ("swe_f64.cu", ["--fmad=false", "-prec-div=true", "-prec-sqrt=true"]),
     ("swe_capi.cu", []),
     ("swe_noalloc.cu", []),
+    ("swe_cnn.cu", []),
 ]
 
 

@@ -108,6 +108,14 @@ struct swe_ctx {
     std::vector<int32_t> hs_ix, hs_iy, hs_hy;
     std::vector<double> hs_w, hs_vx, hs_vy;
     unsigned long long generation = 0;  // bumps when device pointers or tiling change
+    // learned closure (attached network, its normalisation, buffers)
+    swe_cnn* cnn = nullptr;
+    float* d_norm = nullptr;   // 16 floats: in mu[5], in sd[5], out mu[3], out sd[3]
+    void* d_feat = nullptr;    // BF16 [ny][nx][16]
+    void* d_corr = nullptr;    // 3 padded planes
+    double* d_acc = nullptr;
+    cudaGraphExec_t cexec = nullptr;
+    int csteps = 0;
 };
 
 namespace {
@@ -178,7 +186,7 @@ StagedArgs<T> staged_args(const swe_ctx* c) {
 }
 
 template <class T>
-FusedArgs<T> fused_args(const swe_ctx* c) {
+FusedArgs<T> fused_args(const swe_ctx* c, bool closed = false) {
     FusedArgs<T> a;
     std::memset(&a, 0, sizeof(a));
     for (int b = 0; b < 2; ++b) {
@@ -200,6 +208,8 @@ FusedArgs<T> fused_args(const swe_ctx* c) {
     a.ntx = c->ntx;
     a.seg_h = c->seg_h;
     a.nitems = c->nitems;
+    a.corr = closed ? (const T*)c->d_corr : nullptr;
+    a.corr_plane = (size_t)c->pitch * (size_t)c->rows;
     return a;
 }
 
@@ -580,6 +590,31 @@ int batch_launch_events(swe_batch* b, long long s) {
         swe_ctx* c = b->ctx[k];
         if (b->f64) CK(launch_state_speed<double>(staged_args<double>(c), b->st));
         else CK(launch_state_speed<float>(staged_args<float>(c), b->st));
+    }
+    return SWE_OK;
+}
+
+// One closed coarse step: features of the current state, network, mass-
+// centred corrections, fused step with the corrections in its final update.
+int launch_closed_step(swe_ctx* c) {
+    const float* nin = c->d_norm;
+    const float* nout = c->d_norm + 10;
+    if (is64(c)) {
+        CK(launch_features<double>(grid_of<double>(c), c->ctl, (double)c->p.eps_dry, nin, c->d_feat, c->st));
+    } else {
+        CK(launch_features<float>(grid_of<float>(c), c->ctl, (float)c->p.eps_dry, nin, c->d_feat, c->st));
+    }
+    int rc = cnn_forward_on(c->cnn, c->d_feat, c->st);
+    if (rc) return rc;
+    const size_t plane = (size_t)c->pitch * (size_t)c->rows;
+    if (is64(c)) {
+        CK(launch_corrections<double>(grid_of<double>(c), c->ctl, (double)c->p.eps_dry, cnn_output(c->cnn), nout,
+                                      (double*)c->d_corr, plane, c->d_acc, c->st));
+        CK(launch_fused<double>(fused_args<double>(c, true), c->st));
+    } else {
+        CK(launch_corrections<float>(grid_of<float>(c), c->ctl, (float)c->p.eps_dry, cnn_output(c->cnn), nout,
+                                     (float*)c->d_corr, plane, c->d_acc, c->st));
+        CK(launch_fused<float>(fused_args<float>(c, true), c->st));
     }
     return SWE_OK;
 }
@@ -1234,6 +1269,139 @@ void swe_batch_destroy(swe_batch* b) {
     delete b;
 }
 
+int swe_restrict_state(swe_ctx* fine, swe_ctx* coarse) {
+    if (!fine || !coarse) return fail(SWE_ERR_ARG, "null context");
+    if (fine->p.nx != 4 * coarse->p.nx || fine->p.ny != 4 * coarse->p.ny)
+        return fail(SWE_ERR_ARG, "the fine grid must be exactly 4x the coarse grid in both directions");
+    if (fine->p.precision != coarse->p.precision || fine->dev != coarse->dev)
+        return fail(SWE_ERR_ARG, "contexts differ in precision or device");
+    if (!fine->has_state) return fail(SWE_ERR_STATE, "the fine context has no state");
+    CK(cudaSetDevice(coarse->dev));
+    CK(cudaStreamSynchronize(fine->st));
+    if (is64(coarse)) CK(launch_restrict<double>(grid_of<double>(fine), fine->ctl, grid_of<double>(coarse), coarse->ctl, coarse->st));
+    else CK(launch_restrict<float>(grid_of<float>(fine), fine->ctl, grid_of<float>(coarse), coarse->ctl, coarse->st));
+    int rc = state_speed(coarse);
+    if (rc) return rc;
+    CK(cudaStreamSynchronize(coarse->st));
+    coarse->has_state = true;
+    return SWE_OK;
+}
+
+static int ensure_norm(swe_ctx* c) {
+    if (!c->d_norm && cudaMalloc(&c->d_norm, 16 * sizeof(float)) != cudaSuccess) return fail(SWE_ERR_OOM, "norm");
+    return SWE_OK;
+}
+
+int swe_closure_features(swe_ctx* c, const float* norm_in, void* x) {
+    if (!c || !norm_in || !x) return fail(SWE_ERR_ARG, "null argument");
+    if (!c->has_state) return fail(SWE_ERR_STATE, "no state");
+    for (int k = 0; k < 5; ++k)
+        if (!(norm_in[5 + k] > 0.f) || !std::isfinite(norm_in[k])) return fail(SWE_ERR_ARG, "normalisation");
+    CK(cudaSetDevice(c->dev));
+    float* d = nullptr;
+    CK(cudaMalloc(&d, 10 * sizeof(float)));
+    CK(cudaMemcpyAsync(d, norm_in, 10 * sizeof(float), cudaMemcpyHostToDevice, c->st));
+    cudaError_t e = is64(c) ? launch_features<double>(grid_of<double>(c), c->ctl, (double)c->p.eps_dry, d, x, c->st)
+                            : launch_features<float>(grid_of<float>(c), c->ctl, (float)c->p.eps_dry, d, x, c->st);
+    cudaError_t e2 = cudaStreamSynchronize(c->st);
+    cudaFree(d);
+    CK(e);
+    CK(e2);
+    return SWE_OK;
+}
+
+int swe_closure_targets(swe_ctx* pred, swe_ctx* ref, const float* norm_out, float* t) {
+    if (!pred || !ref || !norm_out || !t) return fail(SWE_ERR_ARG, "null argument");
+    if (pred->p.nx != ref->p.nx || pred->p.ny != ref->p.ny || pred->p.precision != ref->p.precision)
+        return fail(SWE_ERR_ARG, "contexts differ in size or precision");
+    for (int k = 0; k < 3; ++k)
+        if (!(norm_out[3 + k] > 0.f) || !std::isfinite(norm_out[k])) return fail(SWE_ERR_ARG, "normalisation");
+    CK(cudaSetDevice(pred->dev));
+    CK(cudaStreamSynchronize(ref->st));
+    float* d = nullptr;
+    CK(cudaMalloc(&d, 6 * sizeof(float)));
+    CK(cudaMemcpyAsync(d, norm_out, 6 * sizeof(float), cudaMemcpyHostToDevice, pred->st));
+    cudaError_t e = is64(pred) ? launch_targets<double>(grid_of<double>(pred), pred->ctl, grid_of<double>(ref), ref->ctl,
+                                                        pred->p.dx, pred->p.eps_dry, d, t, pred->st)
+                               : launch_targets<float>(grid_of<float>(pred), pred->ctl, grid_of<float>(ref), ref->ctl,
+                                                       pred->p.dx, pred->p.eps_dry, d, t, pred->st);
+    cudaError_t e2 = cudaStreamSynchronize(pred->st);
+    cudaFree(d);
+    CK(e);
+    CK(e2);
+    return SWE_OK;
+}
+
+int swe_closure_attach(swe_ctx* c, swe_cnn* cnn, const float* norm) {
+    if (!c || !norm) return fail(SWE_ERR_ARG, "null argument");
+    if (c->p.mode != SWE_FUSED) return fail(SWE_ERR_ARG, "the closure runs on SWE_FUSED contexts");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->st));
+    if (c->cexec) {
+        cudaGraphExecDestroy(c->cexec);
+        c->cexec = nullptr;
+        c->csteps = 0;
+    }
+    if (!cnn) {
+        c->cnn = nullptr;
+        return SWE_OK;
+    }
+    int n, h, w;
+    cnn_shape(cnn, &n, &h, &w);
+    if (n != 1 || h != c->p.ny || w != c->p.nx) return fail(SWE_ERR_ARG, "the network's batch shape must be (1, ny, nx)");
+    for (int k = 0; k < 5; ++k)
+        if (!(norm[5 + k] > 0.f)) return fail(SWE_ERR_ARG, "normalisation");
+    for (int k = 0; k < 3; ++k)
+        if (!(norm[13 + k] > 0.f)) return fail(SWE_ERR_ARG, "normalisation");
+    int rc = ensure_norm(c);
+    if (rc) return rc;
+    if (!c->d_feat && cudaMalloc(&c->d_feat, (size_t)c->p.nx * c->p.ny * 16 * 2) != cudaSuccess)
+        return fail(SWE_ERR_OOM, "closure features");
+    if (!c->d_corr) {
+        if (cudaMalloc(&c->d_corr, 3 * c->plane) != cudaSuccess) return fail(SWE_ERR_OOM, "closure corrections");
+        CK(cudaMemsetAsync(c->d_corr, 0, 3 * c->plane, c->st));
+    }
+    if (!c->d_acc && cudaMalloc(&c->d_acc, 2 * sizeof(double)) != cudaSuccess) return fail(SWE_ERR_OOM, "closure scratch");
+    CK(cudaMemcpyAsync(c->d_norm, norm, 16 * sizeof(float), cudaMemcpyHostToDevice, c->st));
+    CK(cudaStreamSynchronize(c->st));
+    c->cnn = cnn;
+    return SWE_OK;
+}
+
+int swe_step_closed(swe_ctx* c, int32_t nsteps, swe_step_info* info) {
+    if (!c || nsteps < 0) return fail(SWE_ERR_ARG, "null context or nsteps < 0");
+    if (!c->cnn) return fail(SWE_ERR_STATE, "no closure network attached");
+    if (!c->has_state) return fail(SWE_ERR_STATE, "no state");
+    CK(cudaSetDevice(c->dev));
+    CK(launch_set_tend(c->ctl, 0.0, c->st));
+    int rc = SWE_OK;
+    if (nsteps == 1) {
+        rc = launch_closed_step(c);
+    } else if (nsteps > 1) {
+        if (!c->cexec || c->csteps != nsteps) {
+            if (c->cexec) cudaGraphExecDestroy(c->cexec);
+            c->cexec = nullptr;
+            cudaGraph_t g = nullptr;
+            CK(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+            for (int s = 0; s < nsteps && !rc; ++s) rc = launch_closed_step(c);
+            cudaError_t e = cudaStreamEndCapture(c->st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(SWE_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&c->cexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(SWE_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+            c->csteps = nsteps;
+        }
+        CK(cudaGraphLaunch(c->cexec, c->st));
+    }
+    if (rc) return rc;
+    if (info) return swe_step(c, 0, 0.0, info);
+    return SWE_OK;
+}
+
 void swe_destroy(swe_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->dev);
@@ -1252,6 +1420,11 @@ void swe_destroy(swe_ctx* c) {
     cudaFree(c->staging);
     cudaFree(c->d_tmp_i);
     cudaFree(c->d_tmp_d);
+    if (c->cexec) cudaGraphExecDestroy(c->cexec);
+    cudaFree(c->d_norm);
+    cudaFree(c->d_feat);
+    cudaFree(c->d_corr);
+    cudaFree(c->d_acc);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
 }

@@ -1,0 +1,738 @@
+// Learned sub-grid closure for the 4x coarser level of the hierarchical grid
+// system (Sec. 2.2, Fig. 1): a 4-layer 3x3 convolutional network
+// (5 -> 32 -> 32 -> 32 -> 3 channels, ReLU between layers) that maps the
+// coarse state (H, Ux, Uy, b, n_M) to corrections of the coarse cells' net
+// face-flux sums (the Fh, Fv that the final update K8 applies).
+//
+// Tensor-core kernels: BF16 operands, FP32 accumulation, mma.sync m16n8k16,
+// NHWC activations.  Forward and data-gradient convolutions are implicit
+// GEMMs over (pixel) x (tap, input channel); the weight gradient is an
+// implicit GEMM over (input channel) x (pixel) per tap, reduced over CTAs
+// in a fixed order.  Channel counts are padded: inputs to multiples of 16
+// (the MMA K step), outputs to multiples of 8 (the MMA N step).
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/swe.h"
+#include "swe_launch.h"
+
+using namespace swe;
+
+namespace {
+
+int cfail(int code, const std::string& m) {
+    set_last_error(m.c_str());
+    return code;
+}
+
+#define CKC(call)                                                                            \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return cfail(SWE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
+    } while (0)
+
+constexpr int TY = 8, TX = 16;   // pixels per CTA tile (one warp per row)
+constexpr int NLAYER = 4;
+constexpr int CH[NLAYER + 1] = {5, 32, 32, 32, 3};
+constexpr int CIP[NLAYER] = {16, 32, 32, 32};  // padded input channels
+constexpr int COP[NLAYER] = {32, 32, 32, 8};   // padded output channels
+
+__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+    return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float d[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// Output handling of the convolution kernel.
+enum ConvMode {
+    MODE_RELU_BF16 = 0,    // + bias, ReLU, BF16 output (hidden layers)
+    MODE_LINEAR_F32 = 1,   // + bias, FP32 output (last layer)
+    MODE_MASK_BF16 = 2,    // no bias; output x (mask > 0), BF16 (data gradient through a ReLU)
+};
+
+// y[n, i, j, o] = sum_{tap, c} x[n, i+dy-1, j+dx-1, c] * W[tap][o][c] (+ bias)
+// x: BF16 [N][H][W][CI]; W: BF16 [9][CO][CI]; H % TY == 0, W % TX == 0.
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(32 * TY) k_conv(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w,
+                                                  const float* __restrict__ bias, void* __restrict__ out,
+                                                  const __nv_bfloat16* __restrict__ mask, int H, int W, int CO_STORE) {
+    constexpr int PS = CI + 8;  // padded pixel stride in shared memory (bank-conflict free fragments)
+    constexpr int WS = CI + 8;
+    __shared__ __align__(16) __nv_bfloat16 sx[(TY + 2) * (TX + 2) * PS];
+    __shared__ __align__(16) __nv_bfloat16 sw[9 * CO * WS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = blockIdx.z, i0 = blockIdx.y * TY, j0 = blockIdx.x * TX;
+    // weights
+    for (int e = tid; e < 9 * CO * (CI / 2); e += blockDim.x) {
+        const int tc = e / (CI / 2), c2 = e % (CI / 2);
+        *reinterpret_cast<uint32_t*>(&sw[tc * WS + 2 * c2]) =
+            *reinterpret_cast<const uint32_t*>(&w[(size_t)tc * CI + 2 * c2]);
+    }
+    // input tile with a one-pixel halo, zero outside the image
+    for (int e = tid; e < (TY + 2) * (TX + 2) * (CI / 8); e += blockDim.x) {
+        const int p = e / (CI / 8), c8 = e % (CI / 8);
+        const int ti = p / (TX + 2), tj = p % (TX + 2);
+        const int gi = i0 + ti - 1, gj = j0 + tj - 1;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gi >= 0 && gi < H && gj >= 0 && gj < W)
+            v = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * c8]);
+        *reinterpret_cast<uint4*>(&sx[p * PS + 8 * c8]) = v;
+    }
+    __syncthreads();
+    float acc[CO / 8][4];
+#pragma unroll
+    for (int f = 0; f < CO / 8; ++f) acc[f][0] = acc[f][1] = acc[f][2] = acc[f][3] = 0.f;
+    const int r0 = lane >> 2, kc = (lane & 3) * 2;
+#pragma unroll
+    for (int tap = 0; tap < 9; ++tap) {
+        const int ky = tap / 3, kx = tap % 3;
+        const __nv_bfloat16* rowp = &sx[((warp + ky) * (TX + 2) + kx) * PS];
+#pragma unroll
+        for (int q = 0; q < CI / 16; ++q) {
+            const int cb = 16 * q + kc;
+            const uint32_t a0 = ld_u32(rowp + r0 * PS + cb);
+            const uint32_t a1 = ld_u32(rowp + (r0 + 8) * PS + cb);
+            const uint32_t a2 = ld_u32(rowp + r0 * PS + cb + 8);
+            const uint32_t a3 = ld_u32(rowp + (r0 + 8) * PS + cb + 8);
+#pragma unroll
+            for (int f = 0; f < CO / 8; ++f) {
+                const __nv_bfloat16* wp = &sw[(tap * CO + 8 * f + r0) * WS + cb];
+                mma_bf16(acc[f], a0, a1, a2, a3, ld_u32(wp), ld_u32(wp + 8));
+            }
+        }
+    }
+    // epilogue: rows r0 and r0 + 8 of the warp's 16 pixels, columns kc, kc+1
+    const int gi = i0 + warp;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int gj = j0 + r0 + 8 * half;
+        const size_t pix = ((size_t)n * H + gi) * W + gj;
+#pragma unroll
+        for (int f = 0; f < CO / 8; ++f) {
+            const int o = 8 * f + kc;
+            float v0 = acc[f][2 * half], v1 = acc[f][2 * half + 1];
+            if (MODE != MODE_MASK_BF16) {
+                v0 += bias[o];
+                v1 += bias[o + 1];
+            }
+            if (MODE == MODE_RELU_BF16) {
+                v0 = fmaxf(v0, 0.f);
+                v1 = fmaxf(v1, 0.f);
+            }
+            if (MODE == MODE_MASK_BF16) {
+                const __nv_bfloat16* mp = &mask[pix * CO + o];
+                if (!(__bfloat162float(mp[0]) > 0.f)) v0 = 0.f;
+                if (!(__bfloat162float(mp[1]) > 0.f)) v1 = 0.f;
+            }
+            if (MODE == MODE_LINEAR_F32) {
+                float* y = reinterpret_cast<float*>(out);
+                if (o < CO_STORE) y[pix * CO_STORE + o] = v0;
+                if (o + 1 < CO_STORE) y[pix * CO_STORE + o + 1] = v1;
+            } else {
+                __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(out);
+                *reinterpret_cast<uint32_t*>(&y[pix * CO + o]) = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
+            }
+        }
+    }
+}
+
+// Weight gradient partials of one CTA tile:
+// P[blk][tap][c][o] = sum_{pixels of the tile} x[p + off(tap)][c] * g[p][o].
+// GEMM per tap: M = c (16-row blocks), N = o (8-column blocks), K = pixels.
+template <int CI, int CO>
+__global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ g,
+                                                   float* __restrict__ part, float* __restrict__ bpart, int H, int W) {
+    constexpr int PS = CI + 8, GS = CO + 8;
+    __shared__ __align__(16) __nv_bfloat16 sx[(TY + 2) * (TX + 2) * PS];
+    __shared__ __align__(16) __nv_bfloat16 sg[TY * TX * GS];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = blockIdx.z, i0 = blockIdx.y * TY, j0 = blockIdx.x * TX;
+    const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    for (int e = tid; e < (TY + 2) * (TX + 2) * (CI / 8); e += blockDim.x) {
+        const int p = e / (CI / 8), c8 = e % (CI / 8);
+        const int ti = p / (TX + 2), tj = p % (TX + 2);
+        const int gi = i0 + ti - 1, gj = j0 + tj - 1;
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (gi >= 0 && gi < H && gj >= 0 && gj < W)
+            v = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * c8]);
+        *reinterpret_cast<uint4*>(&sx[p * PS + 8 * c8]) = v;
+    }
+    for (int e = tid; e < TY * TX * (CO / 8); e += blockDim.x) {
+        const int p = e / (CO / 8), c8 = e % (CO / 8);
+        const int ti = p / TX, tj = p % TX;
+        const uint4 v = *reinterpret_cast<const uint4*>(&g[(((size_t)n * H + i0 + ti) * W + j0 + tj) * CO + 8 * c8]);
+        *reinterpret_cast<uint4*>(&sg[p * GS + 8 * c8]) = v;
+    }
+    __syncthreads();
+    const int r0 = lane >> 2, kc = (lane & 3) * 2;
+    // work units: (tap, c-block); each warp takes every 8th unit, all o-blocks
+    constexpr int UNITS = 9 * (CI / 16);
+    for (int u = warp; u < UNITS; u += TY) {
+        const int tap = u / (CI / 16), cb = (u % (CI / 16)) * 16;
+        const int ky = tap / 3, kx = tap % 3;
+        float acc[CO / 8][4];
+#pragma unroll
+        for (int f = 0; f < CO / 8; ++f) acc[f][0] = acc[f][1] = acc[f][2] = acc[f][3] = 0.f;
+        // K = 128 pixels of the tile, 16 per MMA (one tile row)
+        for (int ti = 0; ti < TY; ++ti) {
+            const __nv_bfloat16* xr = &sx[((ti + ky) * (TX + 2) + kx) * PS];
+            const __nv_bfloat16* gr = &sg[(ti * TX) * GS];
+            // A[m = c][k = p] = x[p][c]: pairs of consecutive pixels
+            const uint32_t a0 = pack2(xr[kc * PS + cb + r0], xr[(kc + 1) * PS + cb + r0]);
+            const uint32_t a1 = pack2(xr[kc * PS + cb + r0 + 8], xr[(kc + 1) * PS + cb + r0 + 8]);
+            const uint32_t a2 = pack2(xr[(kc + 8) * PS + cb + r0], xr[(kc + 9) * PS + cb + r0]);
+            const uint32_t a3 = pack2(xr[(kc + 8) * PS + cb + r0 + 8], xr[(kc + 9) * PS + cb + r0 + 8]);
+#pragma unroll
+            for (int f = 0; f < CO / 8; ++f) {
+                // B[k = p][n = o] = g[p][o]
+                const int o = 8 * f + r0;
+                const uint32_t b0 = pack2(gr[kc * GS + o], gr[(kc + 1) * GS + o]);
+                const uint32_t b1 = pack2(gr[(kc + 8) * GS + o], gr[(kc + 9) * GS + o]);
+                mma_bf16(acc[f], a0, a1, a2, a3, b0, b1);
+            }
+        }
+        float* P = part + (size_t)blk * 9 * CI * CO + (size_t)tap * CI * CO;
+#pragma unroll
+        for (int f = 0; f < CO / 8; ++f) {
+            const int o = 8 * f + kc;
+            P[(cb + r0) * CO + o] = acc[f][0];
+            P[(cb + r0) * CO + o + 1] = acc[f][1];
+            P[(cb + r0 + 8) * CO + o] = acc[f][2];
+            P[(cb + r0 + 8) * CO + o + 1] = acc[f][3];
+        }
+    }
+    // bias gradient partial: sum of g over the tile
+    for (int o = tid; o < CO; o += blockDim.x) {
+        float sacc = 0.f;
+        for (int p = 0; p < TY * TX; ++p) sacc += __bfloat162float(sg[p * GS + o]);
+        bpart[(size_t)blk * CO + o] = sacc;
+    }
+}
+
+// Fixed-order sum of the per-CTA partials -> FP32 gradients in the master
+// layout [3][3][ci][co] (real channels) and [co].
+__global__ void k_wgrad_reduce(const float* __restrict__ part, const float* __restrict__ bpart, int nblk, int CIp, int COp,
+                               int ci, int co, float* __restrict__ gw, float* __restrict__ gb) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = 9 * ci * co;
+    if (e < nw) {
+        const int tap = e / (ci * co), c = (e / co) % ci, o = e % co;
+        const size_t off = (size_t)tap * CIp * COp + (size_t)c * COp + o;
+        float s = 0.f;
+        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 9 * CIp * COp + off];
+        gw[e] = s;
+    } else if (e < nw + co) {
+        const int o = e - nw;
+        float s = 0.f;
+        for (int b = 0; b < nblk; ++b) s += bpart[(size_t)b * COp + o];
+        gb[o] = s;
+    }
+}
+
+// Master FP32 weights [3][3][ci][co] -> BF16 kernel layout [9][COp][CIp]
+// (zero padded).  flip != 0 gives the data-gradient weights: W'[tap][c][o]
+// = W[8 - tap][o][c] (taps reversed, channels swapped).
+__global__ void k_pack_w(const float* __restrict__ wm, __nv_bfloat16* __restrict__ wk, int ci, int co, int CIp, int COp,
+                         int flip) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (!flip) {
+        if (e >= 9 * COp * CIp) return;
+        const int tap = e / (COp * CIp), o = (e / CIp) % COp, c = e % CIp;
+        const float v = (o < co && c < ci) ? wm[(size_t)tap * ci * co + (size_t)c * co + o] : 0.f;
+        wk[e] = __float2bfloat16(v);
+    } else {
+        // output channels of the gradient conv are the layer's inputs (CIp)
+        if (e >= 9 * CIp * COp) return;
+        const int tap = e / (CIp * COp), c = (e / COp) % CIp, o = e % COp;
+        const float v = (o < co && c < ci) ? wm[(size_t)(8 - tap) * ci * co + (size_t)c * co + o] : 0.f;
+        wk[e] = __float2bfloat16(v);
+    }
+}
+
+// Mean-squared error over the real output channels and its gradient, as
+// BF16 [N][H][W][16] (channels 3.. zero) for the last layer's backward pass.
+__global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, __nv_bfloat16* __restrict__ gy,
+                      double* __restrict__ part, long long npix, int co, float scale) {
+    __shared__ double red[8];
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    double l = 0.0;
+    if (p < npix) {
+        for (int o = 0; o < 16; ++o) {
+            float g = 0.f;
+            if (o < co) {
+                const float d = y[p * co + o] - t[p * co + o];
+                l += (double)d * d;
+                g = 2.f * d * scale;
+            }
+            gy[p * 16 + o] = __float2bfloat16(g);
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < 8; ++i) s += red[i];
+        part[blockIdx.x] = s;
+    }
+}
+
+__global__ void k_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += part[i];
+    *out = s;
+}
+
+// Adam (Kingma & Ba 2015) on all parameters, FP32.
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float gg = g[e];
+    const float mm = b1 * m[e] + (1.f - b1) * gg;
+    const float vv = b2 * v[e] + (1.f - b2) * gg * gg;
+    m[e] = mm;
+    v[e] = vv;
+    p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+// Corrections apply to interior wet cells only: the cell and its four
+// neighbours wet, and at least CORR_HMIN deep.  At shorelines the coarse
+// and fine wet areas differ by whole sub-cells, which no flux correction of
+// the coarse cell can represent.
+constexpr float CORR_HMIN = 0.05f;
+// Standardised network inputs and outputs are clipped to +-CLIP.
+constexpr float CLIP = 10.f;
+
+template <class T>
+__device__ __forceinline__ bool corr_cell(const Grid<T>& g, int buf, size_t k, T eps) {
+    const T* H = g.H[buf];
+    const size_t p = (size_t)g.pitch;
+    return (float)H[k] >= CORR_HMIN && is_wet(H[k], g.b[k], eps) && is_wet(H[k - 1], g.b[k - 1], eps) &&
+           is_wet(H[k + 1], g.b[k + 1], eps) && is_wet(H[k - p], g.b[k - p], eps) && is_wet(H[k + p], g.b[k + p], eps);
+}
+
+// Coarse-grid input features: (H, Ux, Uy, b, n) of the state at the
+// control block's step parity, standardised per channel and clipped,
+// BF16 [ny][nx][16].
+template <class T>
+__global__ void k_features(const Grid<T> g, const Ctl* __restrict__ ctl, T eps, const float* __restrict__ nrm,
+                           __nv_bfloat16* __restrict__ xf) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= g.nx) return;
+    const int buf = (int)(ctl->step & 1);
+    const size_t k = (size_t)(j + PAD) * g.pitch + (i + PAD);
+    const T h = g.H[buf][k], bb = g.b[k];
+    const bool wet = is_wet(h, bb, eps);
+    const bool wall = !(bb < T(WALL_TEST));
+    const float v[5] = {(float)h, wet ? (float)(g.Qx[buf][k] / h) : 0.f, wet ? (float)(g.Qy[buf][k] / h) : 0.f,
+                        wall ? 0.f : (float)bb, (float)g.n[k]};
+    __nv_bfloat16* o = &xf[((size_t)j * g.nx + i) * 16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c)
+        o[c] = __float2bfloat16(c < 5 ? fminf(CLIP, fmaxf(-CLIP, (v[c] - nrm[c]) / nrm[5 + c])) : 0.f);
+}
+
+// CNN output -> corrections of interior wet cells (pass 0: write, sum the
+// depth correction; pass 1: subtract its mean over those cells, so the
+// corrections add no mass).
+template <class T>
+__global__ void k_corrections(const Grid<T> g, const Ctl* __restrict__ ctl, T eps, const float* __restrict__ y,
+                              const float* __restrict__ nrm, T* __restrict__ corr, size_t plane,
+                              double* __restrict__ acc, int pass) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    double s = 0.0, cnt = 0.0;
+    if (i < g.nx) {
+        const int buf = (int)(ctl->step & 1);
+        const size_t k = (size_t)(j + PAD) * g.pitch + (i + PAD);
+        const bool on = corr_cell(g, buf, k, eps);
+        if (pass == 0) {
+            const float* yy = &y[((size_t)j * g.nx + i) * 3];
+            auto val = [&](int q) { return fminf(CLIP, fmaxf(-CLIP, yy[q])) * nrm[3 + q] + nrm[q]; };
+            const T c0 = on ? (T)val(0) : T(0);
+            corr[k] = c0;
+            corr[plane + k] = on ? (T)val(1) : T(0);
+            corr[2 * plane + k] = on ? (T)val(2) : T(0);
+            if (on) {
+                s = (double)c0;
+                cnt = 1.0;
+            }
+        } else if (on) {
+            corr[k] = (T)((double)corr[k] - acc[0] / fmax(acc[1], 1.0));
+        }
+    }
+    if (pass == 0) {
+        for (int o = 16; o > 0; o >>= 1) {
+            s += __shfl_down_sync(0xffffffffu, s, o);
+            cnt += __shfl_down_sync(0xffffffffu, cnt, o);
+        }
+        if ((threadIdx.x & 31) == 0 && cnt > 0.0) {
+            atomicAdd(&acc[0], s);
+            atomicAdd(&acc[1], cnt);
+        }
+    }
+}
+
+template <class T>
+__global__ void k_restrict(const Grid<T> f, const Ctl* __restrict__ fctl, const Grid<T> c, Ctl* __restrict__ cctl) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x, J = blockIdx.y;
+    const int fb = (int)(fctl->step & 1);
+    if (I < c.nx) {
+        double sh = 0.0, sx = 0.0, sy = 0.0;
+        for (int dj = 0; dj < 4; ++dj)
+            for (int di = 0; di < 4; ++di) {
+                const size_t k = (size_t)(4 * J + dj + PAD) * f.pitch + (4 * I + di + PAD);
+                sh += (double)f.H[fb][k];
+                sx += (double)f.Qx[fb][k];
+                sy += (double)f.Qy[fb][k];
+            }
+        const size_t kc = (size_t)(J + PAD) * c.pitch + (I + PAD);
+        c.H[0][kc] = (T)(sh / 16.0);
+        c.Qx[0][kc] = (T)(sx / 16.0);
+        c.Qy[0][kc] = (T)(sy / 16.0);
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        const double t = fctl->t;
+        memset(cctl, 0, sizeof(Ctl));
+        cctl->t = t;
+    }
+}
+
+// Training targets: the flux-sum corrections that turn the coarse step
+// into the restricted fine state, standardised; zero correction outside the
+// cells the closure acts on (judged on the state before the step).
+template <class T>
+__global__ void k_targets(const Grid<T> p, const Ctl* __restrict__ pctl, const Grid<T> r, const Ctl* __restrict__ rctl,
+                          double h, T eps, const float* __restrict__ nrm, float* __restrict__ t) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= p.nx) return;
+    const int pb = (int)(pctl->step & 1), rb = (int)(rctl->step & 1);
+    const double s = h / pctl->tau_last;
+    const size_t k = (size_t)(j + PAD) * p.pitch + (i + PAD);
+    const bool on = corr_cell(p, pb ^ 1, k, eps);
+    const double d[3] = {((double)r.H[rb][k] - (double)p.H[pb][k]) * s, ((double)r.Qx[rb][k] - (double)p.Qx[pb][k]) * s,
+                         ((double)r.Qy[rb][k] - (double)p.Qy[pb][k]) * s};
+    float* o = &t[((size_t)j * p.nx + i) * 3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) o[q] = (float)(((on ? d[q] : 0.0) - nrm[q]) / nrm[3 + q]);
+}
+
+}  // namespace
+
+namespace swe {
+
+template <class T>
+cudaError_t launch_features(const Grid<T>& g, const Ctl* ctl, T eps, const float* norm, void* x, cudaStream_t st) {
+    k_features<T><<<dim3((g.nx + 127) / 128, g.ny), 128, 0, st>>>(g, ctl, eps, norm, (__nv_bfloat16*)x);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_corrections(const Grid<T>& g, const Ctl* ctl, T eps, const float* y, const float* norm, T* corr,
+                               size_t plane, double* acc, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(acc, 0, 2 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((g.nx + 127) / 128, g.ny);
+    k_corrections<T><<<grid, 128, 0, st>>>(g, ctl, eps, y, norm, corr, plane, acc, 0);
+    k_corrections<T><<<grid, 128, 0, st>>>(g, ctl, eps, y, norm, corr, plane, acc, 1);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_restrict(const Grid<T>& fine, const Ctl* fctl, const Grid<T>& coarse, Ctl* cctl, cudaStream_t st) {
+    k_restrict<T><<<dim3((coarse.nx + 127) / 128, coarse.ny), 128, 0, st>>>(fine, fctl, coarse, cctl);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_targets(const Grid<T>& pred, const Ctl* pctl, const Grid<T>& ref, const Ctl* rctl, double h,
+                           double eps, const float* norm, float* t, cudaStream_t st) {
+    k_targets<T><<<dim3((pred.nx + 127) / 128, pred.ny), 128, 0, st>>>(pred, pctl, ref, rctl, h, T(eps), norm, t);
+    return cudaGetLastError();
+}
+
+#define SWE_CLOSURE_INSTANTIATE(T)                                                                            \
+    template cudaError_t launch_features<T>(const Grid<T>&, const Ctl*, T, const float*, void*, cudaStream_t);  \
+    template cudaError_t launch_corrections<T>(const Grid<T>&, const Ctl*, T, const float*, const float*, T*,    \
+                                               size_t, double*, cudaStream_t);                                 \
+    template cudaError_t launch_restrict<T>(const Grid<T>&, const Ctl*, const Grid<T>&, Ctl*, cudaStream_t);      \
+    template cudaError_t launch_targets<T>(const Grid<T>&, const Ctl*, const Grid<T>&, const Ctl*, double,        \
+                                           double, const float*, float*, cudaStream_t);
+SWE_CLOSURE_INSTANTIATE(float)
+SWE_CLOSURE_INSTANTIATE(double)
+
+}  // namespace swe
+
+// --------------------------------------------------------------------- C ABI
+
+struct swe_cnn {
+    int n = 0, h = 0, w = 0;
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int nparam = 0;
+    float* p = nullptr;   // master FP32 parameters, flat (w0, b0, w1, b1, ...)
+    float* g = nullptr;   // gradients, same layout
+    float* m = nullptr;   // Adam moments
+    float* v = nullptr;
+    int adam_t = 0;
+    __nv_bfloat16* wk[NLAYER] = {};   // forward weights, kernel layout
+    __nv_bfloat16* wd[NLAYER] = {};   // data-gradient weights
+    __nv_bfloat16* act[NLAYER] = {};  // act[0] unused (input given); act[l] = output of layer l-1 (BF16)
+    float* yout = nullptr;            // last layer output FP32 [n][h][w][3]
+    __nv_bfloat16* gbuf[2] = {};      // gradient ping-pong, BF16 [n][h][w][32]
+    float* part = nullptr;            // weight-gradient partials
+    float* bpart = nullptr;
+    double* lpart = nullptr;
+    double* dloss = nullptr;
+    int off_w[NLAYER], off_b[NLAYER];
+};
+
+namespace {
+
+int layer_fwd(swe_cnn* c, int l, const __nv_bfloat16* x, void* out) {
+    const dim3 grid(c->w / TX, c->h / TY, c->n), blk(32 * TY);
+    const float* bias = c->p + c->off_b[l];
+    switch (l) {
+        case 0: k_conv<16, 32, MODE_RELU_BF16><<<grid, blk, 0, c->st>>>(x, c->wk[0], bias, out, nullptr, c->h, c->w, 32); break;
+        case 1: k_conv<32, 32, MODE_RELU_BF16><<<grid, blk, 0, c->st>>>(x, c->wk[1], bias, out, nullptr, c->h, c->w, 32); break;
+        case 2: k_conv<32, 32, MODE_RELU_BF16><<<grid, blk, 0, c->st>>>(x, c->wk[2], bias, out, nullptr, c->h, c->w, 32); break;
+        default: k_conv<32, 8, MODE_LINEAR_F32><<<grid, blk, 0, c->st>>>(x, c->wk[3], bias, out, nullptr, c->h, c->w, 3); break;
+    }
+    CKC(cudaGetLastError());
+    return SWE_OK;
+}
+
+// Output-gradient channels of layer l as seen by its backward kernels: the
+// last layer's 3 outputs travel as 16 channels (the MMA K step).
+constexpr int cog(int l) { return l == NLAYER - 1 ? 16 : COP[l]; }
+
+int pack_weights(swe_cnn* c) {
+    for (int l = 0; l < NLAYER; ++l) {
+        const int nel = 9 * CIP[l] * COP[l];
+        k_pack_w<<<(nel + 255) / 256, 256, 0, c->st>>>(c->p + c->off_w[l], c->wk[l], CH[l], CH[l + 1], CIP[l], COP[l], 0);
+        const int neld = 9 * CIP[l] * cog(l);
+        k_pack_w<<<(neld + 255) / 256, 256, 0, c->st>>>(c->p + c->off_w[l], c->wd[l], CH[l], CH[l + 1], CIP[l], cog(l), 1);
+    }
+    CKC(cudaGetLastError());
+    return SWE_OK;
+}
+
+int forward_all(swe_cnn* c, const __nv_bfloat16* x) {
+    int rc = layer_fwd(c, 0, x, c->act[1]);
+    if (!rc) rc = layer_fwd(c, 1, c->act[1], c->act[2]);
+    if (!rc) rc = layer_fwd(c, 2, c->act[2], c->act[3]);
+    if (!rc) rc = layer_fwd(c, 3, c->act[3], c->yout);
+    return rc;
+}
+
+// Loss, gradients of all layers into c->g (loss value into c->dloss).
+int backward_all(swe_cnn* c, const __nv_bfloat16* x, const float* target) {
+    const long long npix = (long long)c->n * c->h * c->w;
+    const int nb = (int)((npix + 255) / 256);
+    // gbuf[0] holds the 16-channel gradient of the last layer's output
+    k_mse<<<nb, 256, 0, c->st>>>(c->yout, target, c->gbuf[0], c->lpart, npix, 3, 1.0f / (float)(npix * 3));
+    k_sum<<<1, 1, 0, c->st>>>(c->lpart, nb, c->dloss);
+    const dim3 grid(c->w / TX, c->h / TY, c->n), blk(32 * TY);
+    const int nblk = (int)(grid.x * grid.y * grid.z);
+    const __nv_bfloat16* ins[NLAYER] = {x, c->act[1], c->act[2], c->act[3]};
+    int cur = 0;
+    for (int l = NLAYER - 1; l >= 0; --l) {
+        const __nv_bfloat16* gl = c->gbuf[cur];
+        // weight gradient of layer l: inputs ins[l] (CIP), output gradient gl
+        switch (l) {
+            case 0: k_wgrad<16, 32><<<grid, blk, 0, c->st>>>(ins[0], gl, c->part, c->bpart, c->h, c->w); break;
+            case 3: k_wgrad<32, 16><<<grid, blk, 0, c->st>>>(ins[3], gl, c->part, c->bpart, c->h, c->w); break;
+            default: k_wgrad<32, 32><<<grid, blk, 0, c->st>>>(ins[l], gl, c->part, c->bpart, c->h, c->w); break;
+        }
+        const int nw = 9 * CH[l] * CH[l + 1] + CH[l + 1];
+        k_wgrad_reduce<<<(nw + 255) / 256, 256, 0, c->st>>>(c->part, c->bpart, nblk, CIP[l], cog(l), CH[l], CH[l + 1],
+                                                           c->g + c->off_w[l], c->g + c->off_b[l]);
+        if (l > 0) {
+            // data gradient into layer l's input, masked by that input's ReLU
+            __nv_bfloat16* go = c->gbuf[cur ^ 1];
+            if (l == 3)
+                k_conv<16, 32, MODE_MASK_BF16><<<grid, blk, 0, c->st>>>(gl, c->wd[3], nullptr, go, c->act[3], c->h, c->w, 32);
+            else
+                k_conv<32, 32, MODE_MASK_BF16><<<grid, blk, 0, c->st>>>(gl, c->wd[l], nullptr, go, c->act[l], c->h, c->w, 32);
+            cur ^= 1;
+        }
+    }
+    CKC(cudaGetLastError());
+    return SWE_OK;
+}
+
+}  // namespace
+
+int swe::cnn_forward_on(swe_cnn* c, const void* x, cudaStream_t st) {
+    cudaStream_t keep = c->st;
+    c->st = st;
+    const int rc = forward_all(c, (const __nv_bfloat16*)x);
+    c->st = keep;
+    return rc;
+}
+
+const float* swe::cnn_output(const swe_cnn* c) { return c->yout; }
+
+void swe::cnn_shape(const swe_cnn* c, int* n, int* h, int* w) {
+    *n = c->n;
+    *h = c->h;
+    *w = c->w;
+}
+
+extern "C" {
+
+SWE_API int swe_cnn_create(int32_t n, int32_t h, int32_t w, void* stream, swe_cnn** out) {
+    if (!out || n < 1 || h < TY || w < TX || h % TY || w % TX)
+        return cfail(SWE_ERR_ARG, "batch shape: n >= 1, h a multiple of 8, w a multiple of 16");
+    *out = nullptr;
+    swe_cnn* c = new (std::nothrow) swe_cnn();
+    if (!c) return cfail(SWE_ERR_OOM, "cnn");
+    c->n = n;
+    c->h = h;
+    c->w = w;
+    if (stream) {
+        c->st = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return cfail(SWE_ERR_CUDA, "stream");
+        }
+        c->own_stream = true;
+    }
+    int np = 0;
+    for (int l = 0; l < NLAYER; ++l) {
+        c->off_w[l] = np;
+        np += 9 * CH[l] * CH[l + 1];
+        c->off_b[l] = np;
+        np += CH[l + 1];
+    }
+    c->nparam = np;
+    const size_t npix = (size_t)n * h * w;
+    const dim3 grid(w / TX, h / TY, n);
+    const size_t nblk = (size_t)grid.x * grid.y * grid.z;
+    bool ok = cudaMalloc(&c->p, np * sizeof(float)) == cudaSuccess && cudaMalloc(&c->g, np * sizeof(float)) == cudaSuccess &&
+              cudaMalloc(&c->m, np * sizeof(float)) == cudaSuccess && cudaMalloc(&c->v, np * sizeof(float)) == cudaSuccess;
+    for (int l = 0; l < NLAYER && ok; ++l) {
+        ok = cudaMalloc(&c->wk[l], 9 * CIP[l] * COP[l] * sizeof(__nv_bfloat16)) == cudaSuccess &&
+             cudaMalloc(&c->wd[l], 9 * CIP[l] * cog(l) * sizeof(__nv_bfloat16)) == cudaSuccess;
+        if (ok && l > 0) ok = cudaMalloc(&c->act[l], npix * 32 * sizeof(__nv_bfloat16)) == cudaSuccess;
+    }
+    ok = ok && cudaMalloc(&c->yout, npix * 3 * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&c->gbuf[0], npix * 32 * sizeof(__nv_bfloat16)) == cudaSuccess &&
+         cudaMalloc(&c->gbuf[1], npix * 32 * sizeof(__nv_bfloat16)) == cudaSuccess &&
+         cudaMalloc(&c->part, nblk * 9 * 32 * 32 * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&c->bpart, nblk * 32 * sizeof(float)) == cudaSuccess &&
+         cudaMalloc(&c->lpart, ((npix + 255) / 256) * sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&c->dloss, sizeof(double)) == cudaSuccess;
+    if (!ok) {
+        swe_cnn_destroy(c);
+        return cfail(SWE_ERR_OOM, "cnn buffers");
+    }
+    cudaMemsetAsync(c->p, 0, np * sizeof(float), c->st);
+    cudaMemsetAsync(c->m, 0, np * sizeof(float), c->st);
+    cudaMemsetAsync(c->v, 0, np * sizeof(float), c->st);
+    *out = c;
+    return SWE_OK;
+}
+
+SWE_API int swe_cnn_num_params(const swe_cnn* c) { return c ? c->nparam : 0; }
+
+SWE_API int swe_cnn_set_params(swe_cnn* c, const float* host) {
+    if (!c || !host) return cfail(SWE_ERR_ARG, "null argument");
+    CKC(cudaMemcpyAsync(c->p, host, c->nparam * sizeof(float), cudaMemcpyHostToDevice, c->st));
+    CKC(cudaMemsetAsync(c->m, 0, c->nparam * sizeof(float), c->st));
+    CKC(cudaMemsetAsync(c->v, 0, c->nparam * sizeof(float), c->st));
+    c->adam_t = 0;
+    int rc = pack_weights(c);
+    if (rc) return rc;
+    CKC(cudaStreamSynchronize(c->st));
+    return SWE_OK;
+}
+
+SWE_API int swe_cnn_get_params(swe_cnn* c, float* host) {
+    if (!c || !host) return cfail(SWE_ERR_ARG, "null argument");
+    CKC(cudaMemcpyAsync(host, c->p, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    CKC(cudaStreamSynchronize(c->st));
+    return SWE_OK;
+}
+
+SWE_API int swe_cnn_forward(swe_cnn* c, const void* x, float* y) {
+    if (!c || !x) return cfail(SWE_ERR_ARG, "null argument");
+    int rc = forward_all(c, (const __nv_bfloat16*)x);
+    if (rc) return rc;
+    if (y) CKC(cudaMemcpyAsync(y, c->yout, (size_t)c->n * c->h * c->w * 3 * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+    return SWE_OK;
+}
+
+SWE_API int swe_cnn_gradients(swe_cnn* c, const void* x, const float* target, float* grads_host, double* loss) {
+    if (!c || !x || !target) return cfail(SWE_ERR_ARG, "null argument");
+    int rc = forward_all(c, (const __nv_bfloat16*)x);
+    if (!rc) rc = backward_all(c, (const __nv_bfloat16*)x, target);
+    if (rc) return rc;
+    double l = 0.0;
+    CKC(cudaMemcpyAsync(&l, c->dloss, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    if (grads_host) CKC(cudaMemcpyAsync(grads_host, c->g, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, c->st));
+    CKC(cudaStreamSynchronize(c->st));
+    if (loss) *loss = l / (3.0 * c->n * c->h * c->w);
+    return SWE_OK;
+}
+
+SWE_API int swe_cnn_train_step(swe_cnn* c, const void* x, const float* target, float lr, double* loss) {
+    if (!c || !x || !target || !(lr > 0.f)) return cfail(SWE_ERR_ARG, "bad argument");
+    int rc = forward_all(c, (const __nv_bfloat16*)x);
+    if (!rc) rc = backward_all(c, (const __nv_bfloat16*)x, target);
+    if (rc) return rc;
+    c->adam_t += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - (float)std::pow((double)b1, c->adam_t), c2 = 1.f - (float)std::pow((double)b2, c->adam_t);
+    k_adam<<<(c->nparam + 255) / 256, 256, 0, c->st>>>(c->p, c->g, c->m, c->v, c->nparam, lr, b1, b2, 1e-8f, c1, c2);
+    rc = pack_weights(c);
+    if (rc) return rc;
+    if (loss) {
+        double l = 0.0;
+        CKC(cudaMemcpyAsync(&l, c->dloss, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        CKC(cudaStreamSynchronize(c->st));
+        *loss = l / (3.0 * c->n * c->h * c->w);
+    }
+    return SWE_OK;
+}
+
+SWE_API void swe_cnn_destroy(swe_cnn* c) {
+    if (!c) return;
+    if (c->st) cudaStreamSynchronize(c->st);
+    cudaFree(c->p);
+    cudaFree(c->g);
+    cudaFree(c->m);
+    cudaFree(c->v);
+    for (int l = 0; l < NLAYER; ++l) {
+        cudaFree(c->wk[l]);
+        cudaFree(c->wd[l]);
+        cudaFree(c->act[l]);
+    }
+    cudaFree(c->yout);
+    cudaFree(c->gbuf[0]);
+    cudaFree(c->gbuf[1]);
+    cudaFree(c->part);
+    cudaFree(c->bpart);
+    cudaFree(c->lpart);
+    cudaFree(c->dloss);
+    if (c->own_stream) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+}  // extern "C"

@@ -409,9 +409,16 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
                 const int r = k - LAG6;
                 if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
                     const T(*FX)[WIN] = s.fX[r % DF];
-                    const T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
-                    const T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
-                    const T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
+                    T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
+                    T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
+                    T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
+                    if (a.corr && gx0 + c < a.g.nx + 2 * PAD) {
+                        // learned sub-grid corrections of the net flux sums
+                        const size_t gk = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
+                        fh += a.corr[gk];
+                        fqx += a.corr[a.corr_plane + gk];
+                        fqy += a.corr[2 * a.corr_plane + gk];
+                    }
                     const T(*C)[WIN] = s.cS[r % DC];
                     T hn = C[0][c] + dth * fh;
                     double clip = 0.0;

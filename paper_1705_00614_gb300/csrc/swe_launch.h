@@ -8,6 +8,8 @@
 
 #include "swe_math.cuh"
 
+struct swe_cnn;
+
 namespace swe {
 
 // Ring of wall cells around every grid (>= the 6-cell dependence radius of
@@ -82,6 +84,10 @@ struct FusedArgs {
     const double* hydro;  // [nh][4]
     int nh;
     int ntx, seg_h, nitems;
+    // learned closure: corrections of the net face-flux sums (3 padded
+    // planes F_H, F_Qx, F_Qy), or null
+    const T* corr;
+    size_t corr_plane;
 };
 
 // Control block of a batched launch: the next work-list entry to hand out and
@@ -149,6 +155,32 @@ template <class T>
 cudaError_t launch_fill_bed(T* b, int nx, int ny, int pitch, cudaStream_t st);
 template <class T>
 size_t fused_smem_bytes();
+// Learned-closure kernels (swe_cnn.cu).
+// Standardised coarse features (H, Ux, Uy, b, n) of the state at step
+// parity, BF16 [ny][nx][16]; norm = mu[5], sd[5].
+template <class T>
+cudaError_t launch_features(const Grid<T>& g, const Ctl* ctl, T eps, const float* norm, void* x, cudaStream_t st);
+// CNN output (standardised, FP32 [ny][nx][3]) -> flux-sum corrections in
+// padded planes for wet cells, depth correction centred over wet cells;
+// norm = mu[3], sd[3]; acc: 2 doubles of scratch.
+template <class T>
+cudaError_t launch_corrections(const Grid<T>& g, const Ctl* ctl, T eps, const float* y, const float* norm, T* corr,
+                               size_t plane, double* acc, cudaStream_t st);
+// coarse state (buffer 0) := 4x4 block means of the fine state; coarse
+// control block := fine time, step 0.
+template <class T>
+cudaError_t launch_restrict(const Grid<T>& fine, const Ctl* fctl, const Grid<T>& coarse, Ctl* cctl, cudaStream_t st);
+// standardised training targets: ((ref - pred) h / tau - mu) / sd, FP32
+// [ny][nx][3]; tau = the predicting grid's last step.
+template <class T>
+cudaError_t launch_targets(const Grid<T>& pred, const Ctl* pctl, const Grid<T>& ref, const Ctl* rctl, double h,
+                           double eps, const float* norm, float* t, cudaStream_t st);
+// Forward pass of a closure network on a given stream; output FP32
+// [n][h][w][3] in the network's own buffer.
+int cnn_forward_on(swe_cnn* c, const void* x, cudaStream_t st);
+const float* cnn_output(const swe_cnn* c);
+void cnn_shape(const swe_cnn* c, int* n, int* h, int* w);
+
 // The message swe_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 // Set the device copy of t_end (kernel argument, so it is stream ordered).

@@ -24,7 +24,10 @@ API = ["swe_params_default", "swe_create", "swe_set_terrain", "swe_set_state", "
        "swe_set_solid", "swe_step", "swe_get_state", "swe_get_device_ptrs", "swe_get_stages", "swe_sync",
        "swe_destroy", "swe_status_str", "swe_last_error", "swe_step_f32_noalloc", "swe_autotune",
        "swe_batch_create", "swe_batch_set_gate_events", "swe_batch_step", "swe_batch_autotune",
-       "swe_batch_destroy"]
+       "swe_batch_destroy", "swe_cnn_create", "swe_cnn_num_params", "swe_cnn_set_params", "swe_cnn_get_params",
+       "swe_cnn_forward", "swe_cnn_gradients", "swe_cnn_train_step", "swe_cnn_destroy", "swe_restrict_state",
+       "swe_closure_features", "swe_closure_targets", "swe_closure_attach", "swe_step_closed"]
+CNN_CHANNELS = (5, 32, 32, 32, 3)
 SWE_PAD = 10
 NOALLOC_MAX_ITEMS = 7000
 
@@ -111,6 +114,33 @@ def load(path=None):
     L.swe_batch_autotune.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
     L.swe_batch_destroy.restype = None
     L.swe_batch_destroy.argtypes = [ctypes.c_void_p]
+    _fp = ctypes.POINTER(ctypes.c_float)
+    L.swe_cnn_create.restype = ctypes.c_int
+    L.swe_cnn_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
+                                 ctypes.POINTER(ctypes.c_void_p)]
+    L.swe_cnn_num_params.restype = ctypes.c_int
+    L.swe_cnn_num_params.argtypes = [ctypes.c_void_p]
+    L.swe_cnn_set_params.restype = ctypes.c_int
+    L.swe_cnn_set_params.argtypes = [ctypes.c_void_p, _fp]
+    L.swe_cnn_get_params.restype = ctypes.c_int
+    L.swe_cnn_get_params.argtypes = [ctypes.c_void_p, _fp]
+    L.swe_cnn_forward.restype = ctypes.c_int
+    L.swe_cnn_forward.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    L.swe_cnn_gradients.restype = ctypes.c_int
+    L.swe_cnn_gradients.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, _fp,
+                                    ctypes.POINTER(ctypes.c_double)]
+    L.swe_cnn_train_step.restype = ctypes.c_int
+    L.swe_cnn_train_step.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_float,
+                                     ctypes.POINTER(ctypes.c_double)]
+    L.swe_cnn_destroy.restype = None
+    L.swe_cnn_destroy.argtypes = [ctypes.c_void_p]
+    for name, args in (("swe_restrict_state", [ctypes.c_void_p, ctypes.c_void_p]),
+                       ("swe_closure_features", [ctypes.c_void_p, _fp, ctypes.c_void_p]),
+                       ("swe_closure_targets", [ctypes.c_void_p, ctypes.c_void_p, _fp, ctypes.c_void_p]),
+                       ("swe_closure_attach", [ctypes.c_void_p, ctypes.c_void_p, _fp]),
+                       ("swe_step_closed", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(StepInfo)])):
+        getattr(L, name).restype = ctypes.c_int
+        getattr(L, name).argtypes = args
     L.swe_step_f32_noalloc.restype = ctypes.c_int
     L.swe_step_f32_noalloc.argtypes = [ctypes.POINTER(Params)] + [ctypes.c_void_p] * 8 + [
         ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.POINTER(StepInfo)]
@@ -274,6 +304,28 @@ class Solver:
         _check(self.L, self.L.swe_autotune(self.h, int(trial_steps), ctypes.byref(v)))
         return v.value
 
+    # learned closure (this context is the coarse grid)
+    def restrict_from(self, fine):
+        _check(self.L, self.L.swe_restrict_state(fine.h, self.h))
+
+    def closure_features(self, norm_in, x):
+        a = np.ascontiguousarray(norm_in, dtype=np.float32)
+        _check(self.L, self.L.swe_closure_features(self.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), x))
+
+    def closure_targets(self, ref, norm_out, t):
+        a = np.ascontiguousarray(norm_out, dtype=np.float32)
+        _check(self.L, self.L.swe_closure_targets(self.h, ref.h, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), t))
+
+    def attach_closure(self, cnn, norm):
+        a = np.ascontiguousarray(norm, dtype=np.float32)
+        _check(self.L, self.L.swe_closure_attach(self.h, cnn.h if cnn is not None else None,
+                                                 a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def step_closed(self, nsteps=1, report=True):
+        info = StepInfo()
+        _check(self.L, self.L.swe_step_closed(self.h, int(nsteps), ctypes.byref(info) if report else None))
+        return info.as_dict() if report else None
+
 
 class Batch:
     """A batched ensemble over Solver contexts (swe_batch_*)."""
@@ -309,6 +361,78 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             self.L.swe_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def flatten_cnn_params(params):
+    """[[w (3,3,ci,co), b (co,)], ...] -> flat float32 in the library's order."""
+    return np.concatenate([np.concatenate([np.asarray(w, np.float64).reshape(-1), np.asarray(b, np.float64)])
+                           for w, b in params]).astype(np.float32)
+
+
+def unflatten_cnn_params(flat, channels=CNN_CHANNELS):
+    out, k = [], 0
+    for l in range(len(channels) - 1):
+        ci, co = channels[l], channels[l + 1]
+        w = np.asarray(flat[k:k + 9 * ci * co], dtype=np.float64).reshape(3, 3, ci, co)
+        k += 9 * ci * co
+        b = np.asarray(flat[k:k + co], dtype=np.float64)
+        k += co
+        out.append([w, b])
+    return out
+
+
+class CNN:
+    """The closure network (swe_cnn_*).  Tensors are device pointers (ints):
+    inputs BF16 [n][h][w][16], targets and outputs FP32 [n][h][w][3]."""
+
+    def __init__(self, n, h, w, stream=None):
+        self.L = load()
+        hh = ctypes.c_void_p()
+        _check(self.L, self.L.swe_cnn_create(int(n), int(h), int(w), stream, ctypes.byref(hh)))
+        self.h = hh
+        self.nparam = self.L.swe_cnn_num_params(self.h)
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.nparam
+        _check(self.L, self.L.swe_cnn_set_params(self.h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def get_params(self):
+        out = np.empty(self.nparam, dtype=np.float32)
+        _check(self.L, self.L.swe_cnn_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def forward(self, x, y=None):
+        _check(self.L, self.L.swe_cnn_forward(self.h, x, y))
+
+    def gradients(self, x, t):
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(self.L, self.L.swe_cnn_gradients(self.h, x, t, g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                ctypes.byref(loss)))
+        return g, loss.value
+
+    def train_step(self, x, t, lr, report=True):
+        loss = ctypes.c_double()
+        _check(self.L, self.L.swe_cnn_train_step(self.h, x, t, float(lr), ctypes.byref(loss) if report else None))
+        return loss.value if report else None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.swe_cnn_destroy(self.h)
             self.h = None
 
     def __del__(self):
