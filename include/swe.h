@@ -150,7 +150,11 @@ SWE_API int swe_get_state(swe_ctx* ctx, double* H, double* Qx, double* Qy, doubl
 
 /* Device pointers of the current state (first interior cell of H, Qx, Qy),
  * the row pitch in elements and the element size in bytes.  Valid until
- * the next swe_step or swe_set_state (the state is double buffered). */
+ * the next swe_step or swe_set_state (the state is double buffered).
+ * Read only: the context keeps quantities derived from the state (the next
+ * step's signal speed and, in SWE_FUSED mode, the forces of Eq. 4 per cell),
+ * so a state written through these pointers would be stepped with stale
+ * ones; change the state with swe_set_state. */
 SWE_API int swe_get_device_ptrs(swe_ctx* ctx, void** H, void** Qx, void** Qy, int64_t* pitch_elems,
                         int32_t* elem_bytes);
 

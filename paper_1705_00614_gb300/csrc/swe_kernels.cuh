@@ -140,21 +140,35 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // k = r + LAG_s.  Lags are chosen so that every stage reads only rows that
 // other threads finished in earlier iterations; one CTA barrier per
 // iteration then orders everything.  Two warp groups of 128 threads (one
-// thread per window column each) share the work of an iteration:
-//   group L (Lagrangian, stage I-II):  S0 primitives (row k), S1 forces at
-//     t_n and U* (k-2), S2 particle area and H* (k-4), S3 forces at
-//     t_{n+1/2}, corrector and sources (k-6);
-//   group E (Eulerian, stage III-IV):  S4 MUSCL slopes and face fluxes
-//     (k-8), S6 final update (k-9), S7 signal speed of the new state for the
-//     next step's K3 (k-11).
-// Input rows (H, Qx, Qy, b, n) arrive by TMA in chunks of RB rows; each
-// field has a ring of chunk slots as deep as its oldest reader needs.
+// thread per window column each) share the work of an iteration.
+//
+// Stages: S0 primitives U = Q/H; S1 forces at t_n and predictor U*; S2
+// particle area change and H*; S3 forces at t_{n+1/2}, corrector, sources;
+// S4 MUSCL slopes and face fluxes; S6 final update (K8); S7 signal speed of
+// the new state (the next step's K3).
+//
+// ACC = true (contexts): S7 also stores the new state's accelerations
+// (a_x, a_y, phi) in a second pair of ping-pong planes, and the next step's
+// S1 loads them instead of evaluating the forces again, so S0 and S1 merge.
+// Groups: L = {S0+S1 (lag 0), S3 (4), S7 (9)}, E = {S2 (2), S4 (6),
+// S6 (7)}.
+// ACC = false (caller-owned planes, no acceleration storage): groups
+// L = {S0 (0), S1 (2), S2 (4), S3 (6)}, E = {S4 (8), S6 (9), S7 (11)}.
+// Input rows (H, Qx, Qy, b, n and, with ACC, a_x, a_y, phi) arrive by TMA in
+// chunks of RB rows; each field has a ring of chunk slots as deep as its
+// oldest reader needs.
 
 constexpr int NT = 2 * WIN;
-constexpr int LAG1 = 2, LAG2 = 4, LAG3 = 6, LAG4 = 8, LAG6 = 9, LAG7 = 11;
 constexpr int DP = 7, DA = 6, DB = 4, DC = 4, DF = 2, DN = 4;   // stage ring depths (rows)
-constexpr int SLOT_Q = 2, SLOT_H = 4, SLOT_B = 5, SLOT_N = 5;   // chunk slots per input field
+constexpr int SLOT_Q = 2, SLOT_H = 4, SLOT_B = 5, SLOT_N = 5, SLOT_A = 2;  // chunk slots per input field
 constexpr int NBAR = 5;
+
+template <bool ACC>
+struct Lags {
+    static constexpr int S1 = ACC ? 0 : 2, S2 = ACC ? 2 : 4, S3 = ACC ? 4 : 6, S4 = ACC ? 6 : 8, S6 = ACC ? 7 : 9,
+                         S7 = ACC ? 9 : 11;
+};
+constexpr int MAX_LAG7 = 11;
 
 template <class T>
 struct FSmem {
@@ -163,6 +177,7 @@ struct FSmem {
     T inQy[SLOT_Q][RB][WIN];
     T inB[SLOT_B][RB][WIN];
     T inN[SLOT_N][RB][WIN];
+    T inA[SLOT_A][3][RB][WIN];  // a_x, a_y, phi at t_n (ACC only)
     T pU[DP][2][WIN];      // U at t_n
     T aU[DA][2][WIN];      // predictor U*
     T bH[DB][WIN];         // particle depth H*
@@ -182,25 +197,30 @@ size_t fused_smem_bytes() {
     return sizeof(FSmem<T>) + 128;
 }
 
-template <class T>
+template <class T, bool ACC>
 __device__ __forceinline__ void issue_chunk(FSmem<T>& s, const FusedArgs<T>& a, int buf, int ch,
                                             int gx0, int gy0, unsigned cbase) {
     unsigned long long* bar = &s.bar[(cbase + (unsigned)ch) % NBAR];
-    mbar_expect_tx(bar, 5u * RB * WIN * sizeof(T));
+    mbar_expect_tx(bar, (ACC ? 8u : 5u) * RB * WIN * sizeof(T));
     const int y = gy0 + ch * RB;
     tma_load_2d(&s.inH[ch % SLOT_H][0][0], &a.tmH[buf], gx0, y, bar);
     tma_load_2d(&s.inQx[ch % SLOT_Q][0][0], &a.tmQx[buf], gx0, y, bar);
     tma_load_2d(&s.inQy[ch % SLOT_Q][0][0], &a.tmQy[buf], gx0, y, bar);
     tma_load_2d(&s.inB[ch % SLOT_B][0][0], &a.tmB, gx0, y, bar);
     tma_load_2d(&s.inN[ch % SLOT_N][0][0], &a.tmN, gx0, y, bar);
+    if (ACC) {
+#pragma unroll
+        for (int q = 0; q < 3; ++q) tma_load_2d(&s.inA[ch % SLOT_A][q][0][0], &a.tmA[buf][q], gx0, y, bar);
+    }
 }
 
 // One work item (a window of one grid's segment): the whole step for it.
 // `cbase` counts the TMA chunks this CTA has waited for so far, so the
 // mbarrier phases stay consistent across the items a persistent CTA runs.
 // Returns false when a bounded wait gave up (the CTA must stop).
-template <class T>
+template <class T, bool ACC>
 __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, const int item, unsigned& cbase) {
+    using LG = Lags<ACC>;
     const int tid = threadIdx.x;
     const int c = tid & (WIN - 1);
     const bool groupL = tid < WIN;
@@ -225,7 +245,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
     if (tid < a.nh) s.hq[tid] = hydro_value(a.hydro + 4 * tid, a.ctl->t + 0.5 * (double)tauT);
     if (tid == 0) {
         fence_proxy_async();
-        issue_chunk(s, a, buf, 0, gx0, gy0, cbase);
+        issue_chunk<T, ACC>(s, a, buf, 0, gx0, gy0, cbase);
     }
     __syncthreads();
 
@@ -239,6 +259,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
     auto rQy = [&](int r) -> const T* { return s.inQy[(r / RB) % SLOT_Q][r % RB]; };
     auto rB = [&](int r) -> const T* { return s.inB[(r / RB) % SLOT_B][r % RB]; };
     auto rN = [&](int r) -> const T* { return s.inN[(r / RB) % SLOT_N][r % RB]; };
+    auto rA = [&](int q, int r) -> const T* { return s.inA[(r / RB) % SLOT_A][q][r % RB]; };
 
     int sp = a.src_off[item];
     const int se = a.src_off[item + 1];
@@ -248,13 +269,230 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
     long long acc_wet = 0;
     bool bad = false;
 
-    for (int k = 0; k <= nrows + LAG7 - HALO - 1; ++k) {
+    // S0: primitives at row k (and, with ACC, the predictor velocity from
+    // the stored accelerations of the state at t_n)
+    auto stage0 = [&](int k) {
+        if (k >= nrows) return;
+        const T H = rH(k)[c];
+        const bool wet = is_wet(H, rB(k)[c], eps);
+        const T ux = wet ? rQx(k)[c] / H : T(0);
+        const T uy = wet ? rQy(k)[c] / H : T(0);
+        s.pU[k % DP][0][c] = ux;
+        s.pU[k % DP][1][c] = uy;
+        if (ACC) {
+            T usx = T(0), usy = T(0);
+            if (wet) {
+                const T den = T(1) + th * rA(2, k)[c];
+                usx = (ux + th * rA(0, k)[c]) / den;
+                usy = (uy + th * rA(1, k)[c]) / den;
+            }
+            s.aU[k % DA][0][c] = usx;
+            s.aU[k % DA][1][c] = usy;
+        }
+    };
+    // S1: forces at t_n and predictor velocity U* (without ACC)
+    auto stage1 = [&](int r) {
+        if (!(r >= 1 && r <= nrows - 2 && c >= 1 && c < WIN - 1)) return;
+        const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
+        const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
+        const T(*U0)[WIN] = s.pU[r % DP];
+        const T(*Um)[WIN] = s.pU[(r - 1) % DP];
+        const T(*Up)[WIN] = s.pU[(r + 1) % DP];
+        const T H = H0[c], b = b0[c];
+        T usx = T(0), usy = T(0);
+        if (is_wet(H, b, eps)) {
+            Nb<T> W{H0[c - 1], b0[c - 1], U0[0][c - 1], U0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
+            Nb<T> E{H0[c + 1], b0[c + 1], U0[0][c + 1], U0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
+            Nb<T> S{Hm[c], bm[c], Um[0][c], Um[1][c], is_wet(Hm[c], bm[c], eps)};
+            Nb<T> N{Hp[c], bp[c], Up[0][c], Up[1][c], is_wet(Hp[c], bp[c], eps)};
+            T ax, ay, phi;
+            forces(P, H, b, rN(r)[c], U0[0][c], U0[1][c], W, E, S, N, ax, ay, phi);
+            const T den = T(1) + th * phi;
+            usx = (U0[0][c] + th * ax) / den;
+            usy = (U0[1][c] + th * ay) / den;
+        }
+        s.aU[r % DA][0][c] = usx;
+        s.aU[r % DA][1][c] = usy;
+    };
+    // S2: particle area change and H*
+    auto stage2 = [&](int r) {
+        if (!(r >= 2 && r <= nrows - 3 && c >= 2 && c < WIN - 2)) return;
+        const T H = rH(r)[c];
+        T hs = H;
+        if (is_wet(H, rB(r)[c], eps)) {
+            const T* Ax = s.aU[r % DA][0];
+            const T* Ay = s.aU[r % DA][1];
+            const T u = Ax[c], uW = Ax[c - 1], uE = Ax[c + 1];
+            const T v = Ay[c], vS = s.aU[(r - 1) % DA][1][c], vN = s.aU[(r + 1) % DA][1][c];
+            const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
+            const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
+            const T D = ((fxp - fxm) + (fyp - fym)) / P.h;
+            hs = H / tmax(T(0.5), T(1) + th * D);
+        }
+        s.bH[r % DB][c] = hs;
+    };
+    // S3: forces at t_{n+1/2}, corrector and sources
+    auto stage3 = [&](int r) {
+        if (!(r >= 3 && r <= nrows - 4 && c >= 3 && c < WIN - 3)) return;
+        const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
+        const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
+        const T *B0 = s.bH[r % DB], *Bm = s.bH[(r - 1) % DB], *Bp = s.bH[(r + 1) % DB];
+        const T(*A0)[WIN] = s.aU[r % DA];
+        const T(*Am)[WIN] = s.aU[(r - 1) % DA];
+        const T(*Ap)[WIN] = s.aU[(r + 1) % DA];
+        const T H = H0[c], b = b0[c];
+        const T ux = s.pU[r % DP][0][c], uy = s.pU[r % DP][1][c];
+        T utx = T(0), uty = T(0);
+        if (is_wet(H, b, eps)) {
+            Nb<T> W{B0[c - 1], b0[c - 1], A0[0][c - 1], A0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
+            Nb<T> E{B0[c + 1], b0[c + 1], A0[0][c + 1], A0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
+            Nb<T> S{Bm[c], bm[c], Am[0][c], Am[1][c], is_wet(Hm[c], bm[c], eps)};
+            Nb<T> N{Bp[c], bp[c], Ap[0][c], Ap[1][c], is_wet(Hp[c], bp[c], eps)};
+            T ax, ay, phi;
+            forces(P, B0[c], b, rN(r)[c], A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
+            const T den = T(1) + tauT * phi;
+            utx = (ux + tauT * ax) / den;
+            uty = (uy + tauT * ay) / den;
+        }
+        const T uhx = T(0.5) * (ux + utx), uhy = T(0.5) * (uy + uty);
+        T sig = T(0), vx = T(0), vy = T(0);
+        while (sp < se && a.src[sp].r < r) ++sp;
+        for (int q = sp; q < se && a.src[q].r == r; ++q) {
+            if (a.src[q].c == c) {
+                sig = (T)(a.src[q].w * s.hq[a.src[q].hydro]);
+                vx = (T)a.src[q].vx;
+                vy = (T)a.src[q].vy;
+            }
+        }
+        const T ts = tauT * sig;
+        const T ht = tmax(T(0), H + ts);
+        const T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
+        const T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
+        const bool wt = is_wet(ht, b, eps);
+        T(*C)[WIN] = s.cS[r % DC];
+        C[0][c] = ht;
+        C[1][c] = uhx;
+        C[2][c] = uhy;
+        C[3][c] = wt ? qtx / ht : T(0);
+        C[4][c] = wt ? qty / ht : T(0);
+        C[5][c] = qtx;
+        C[6][c] = qty;
+        if (out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
+    };
+    // S4: MUSCL slopes and face fluxes of row r (and its y face below)
+    auto stage4 = [&](int r) {
+        auto ecell = [&](int rr, int col) {
+            ECell<T> e;
+            const T(*C)[WIN] = s.cS[rr % DC];
+            const T bb = rB(rr)[col];
+            e.w[0] = C[0][col];
+            e.w[1] = C[1][col];
+            e.w[2] = C[2][col];
+            e.w[3] = C[3][col];
+            e.w[4] = C[4][col];
+            e.b = bb;
+            e.wt = is_wet(e.w[0], bb, eps);
+            return e;
+        };
+        if (!(r >= 4 && r <= nrows - 5 && c >= 3 && c < WIN - 3)) return;
+        const ECell<T> em = ecell(r - 1, c), e0 = ecell(r, c), ep = ecell(r + 1, c);
+        T syc[5];
+        slopes(em, e0, ep, syc);
+        if (r >= 5) face_flux(P, em, syPrev, e0, syc, 2, fyCur[0], fyCur[1], fyCur[2]);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
+        if (r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 6) {
+            const ECell<T> xm = ecell(r, c - 1), x1 = ecell(r, c + 1), x2 = ecell(r, c + 2);
+            T sL[5], sR[5];
+            slopes(xm, e0, x1, sL);
+            slopes(e0, x1, x2, sR);
+            T FH, FQx, FQy;
+            face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
+            s.fX[r % DF][0][c] = FH;
+            s.fX[r % DF][1][c] = FQx;
+            s.fX[r % DF][2][c] = FQy;
+        }
+    };
+    // S6: final update of row r (K8)
+    auto stage6 = [&](int r) {
+        if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
+            const T(*FX)[WIN] = s.fX[r % DF];
+            T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
+            T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
+            T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
+            if (a.corr && gx0 + c < a.g.nx + 2 * PAD) {
+                // learned sub-grid corrections of the net flux sums
+                const size_t gk = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
+                fh += a.corr[gk];
+                fqx += a.corr[a.corr_plane + gk];
+                fqy += a.corr[2 * a.corr_plane + gk];
+            }
+            const T(*C)[WIN] = s.cS[r % DC];
+            T hn = C[0][c] + dth * fh;
+            double clip = 0.0;
+            if (hn < T(0)) {
+                clip = -(double)hn;
+                hn = T(0);
+            }
+            T qxn = T(0), qyn = T(0);
+            if (hn > eps) {
+                qxn = C[5][c] + dth * fqx;
+                qyn = C[6][c] + dth * fqy;
+            }
+            const T b = rB(r)[c];
+            const bool wetn = is_wet(hn, b, eps);
+            s.nS[r % DN][0][c] = hn;
+            s.nS[r % DN][1][c] = wetn ? qxn / hn : T(0);
+            s.nS[r % DN][2][c] = wetn ? qyn / hn : T(0);
+            if (out_col && r >= HALO && r < HALO + sh) {
+                const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
+                outH[gi] = hn;
+                outQx[gi] = qxn;
+                outQy[gi] = qyn;
+                acc_mass += (double)hn;
+                acc_clip += clip;
+                acc_wet += wetn ? 1 : 0;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) fyPrev[q] = fyCur[q];
+    };
+    // S7: signal speed of the new state at row r (next step's K3); with ACC
+    // also its accelerations for the next step's predictor
+    auto stage7 = [&](int r) {
+        if (!(r >= HALO && r < HALO + sh && out_col)) return;
+        const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
+        const int i0 = r % DN, im = (r - 1) % DN, ip = (r + 1) % DN;
+        const T H = s.nS[i0][0][c], b = b0[c];
+        T ax = T(0), ay = T(0), phi = T(0);
+        if (is_wet(H, b, eps)) {
+            const T ux = s.nS[i0][1][c], uy = s.nS[i0][2][c];
+            Nb<T> W{s.nS[i0][0][c - 1], b0[c - 1], s.nS[i0][1][c - 1], s.nS[i0][2][c - 1],
+                    is_wet(s.nS[i0][0][c - 1], b0[c - 1], eps)};
+            Nb<T> E{s.nS[i0][0][c + 1], b0[c + 1], s.nS[i0][1][c + 1], s.nS[i0][2][c + 1],
+                    is_wet(s.nS[i0][0][c + 1], b0[c + 1], eps)};
+            Nb<T> S{s.nS[im][0][c], bm[c], s.nS[im][1][c], s.nS[im][2][c], is_wet(s.nS[im][0][c], bm[c], eps)};
+            Nb<T> N{s.nS[ip][0][c], bp[c], s.nS[ip][1][c], s.nS[ip][2][c], is_wet(s.nS[ip][0][c], bp[c], eps)};
+            forces(P, H, b, rN(r)[c], ux, uy, W, E, S, N, ax, ay, phi);
+            const double v = (double)cell_speed(P, H, ux, uy, ax, ay);
+            if (!(v <= DBL_MAX)) bad = true;
+            else if (v > vmax) vmax = v;
+        }
+        if (ACC) {
+            const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
+            a.g.A[buf ^ 1][0][gi] = ax;
+            a.g.A[buf ^ 1][1][gi] = ay;
+            a.g.A[buf ^ 1][2][gi] = phi;
+        }
+    };
+
+    for (int k = 0; k <= nrows + LG::S7 - HALO - 1; ++k) {
         if ((k % RB) == 0) {
             const int ch = k / RB;
             if (ch < nchunks) {
                 if (tid == 0 && ch + 1 < nchunks) {
                     fence_proxy_async();
-                    issue_chunk(s, a, buf, ch + 1, gx0, gy0, cbase);
+                    issue_chunk<T, ACC>(s, a, buf, ch + 1, gx0, gy0, cbase);
                 }
                 const unsigned gch = cbase + (unsigned)ch;
                 const bool ok = mbar_wait_bounded(&s.bar[gch % NBAR], (gch / NBAR) & 1u);
@@ -264,215 +502,26 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
                 }
             }
         }
-        if (groupL) {
-            // S0: primitives at row k
-            if (k < nrows) {
-                const T H = rH(k)[c];
-                const bool wet = is_wet(H, rB(k)[c], eps);
-                s.pU[k % DP][0][c] = wet ? rQx(k)[c] / H : T(0);
-                s.pU[k % DP][1][c] = wet ? rQy(k)[c] / H : T(0);
-            }
-            // S1: forces at t_n and predictor velocity U*
-            {
-                const int r = k - LAG1;
-                if (r >= 1 && r <= nrows - 2 && c >= 1 && c < WIN - 1) {
-                    const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
-                    const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
-                    const T(*U0)[WIN] = s.pU[r % DP];
-                    const T(*Um)[WIN] = s.pU[(r - 1) % DP];
-                    const T(*Up)[WIN] = s.pU[(r + 1) % DP];
-                    const T H = H0[c], b = b0[c];
-                    T usx = T(0), usy = T(0);
-                    if (is_wet(H, b, eps)) {
-                        Nb<T> W{H0[c - 1], b0[c - 1], U0[0][c - 1], U0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
-                        Nb<T> E{H0[c + 1], b0[c + 1], U0[0][c + 1], U0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
-                        Nb<T> S{Hm[c], bm[c], Um[0][c], Um[1][c], is_wet(Hm[c], bm[c], eps)};
-                        Nb<T> N{Hp[c], bp[c], Up[0][c], Up[1][c], is_wet(Hp[c], bp[c], eps)};
-                        T ax, ay, phi;
-                        forces(P, H, b, rN(r)[c], U0[0][c], U0[1][c], W, E, S, N, ax, ay, phi);
-                        const T den = T(1) + th * phi;
-                        usx = (U0[0][c] + th * ax) / den;
-                        usy = (U0[1][c] + th * ay) / den;
-                    }
-                    s.aU[r % DA][0][c] = usx;
-                    s.aU[r % DA][1][c] = usy;
-                }
-            }
-            // S2: particle area change and H*
-            {
-                const int r = k - LAG2;
-                if (r >= 2 && r <= nrows - 3 && c >= 2 && c < WIN - 2) {
-                    const T H = rH(r)[c];
-                    T hs = H;
-                    if (is_wet(H, rB(r)[c], eps)) {
-                        const T* Ax = s.aU[r % DA][0];
-                        const T* Ay = s.aU[r % DA][1];
-                        const T u = Ax[c], uW = Ax[c - 1], uE = Ax[c + 1];
-                        const T v = Ay[c], vS = s.aU[(r - 1) % DA][1][c], vN = s.aU[(r + 1) % DA][1][c];
-                        const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
-                        const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
-                        const T D = ((fxp - fxm) + (fyp - fym)) / P.h;
-                        hs = H / tmax(T(0.5), T(1) + th * D);
-                    }
-                    s.bH[r % DB][c] = hs;
-                }
-            }
-            // S3: forces at t_{n+1/2}, corrector and sources
-            {
-                const int r = k - LAG3;
-                if (r >= 3 && r <= nrows - 4 && c >= 3 && c < WIN - 3) {
-                    const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
-                    const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
-                    const T *B0 = s.bH[r % DB], *Bm = s.bH[(r - 1) % DB], *Bp = s.bH[(r + 1) % DB];
-                    const T(*A0)[WIN] = s.aU[r % DA];
-                    const T(*Am)[WIN] = s.aU[(r - 1) % DA];
-                    const T(*Ap)[WIN] = s.aU[(r + 1) % DA];
-                    const T H = H0[c], b = b0[c];
-                    const T ux = s.pU[r % DP][0][c], uy = s.pU[r % DP][1][c];
-                    T utx = T(0), uty = T(0);
-                    if (is_wet(H, b, eps)) {
-                        Nb<T> W{B0[c - 1], b0[c - 1], A0[0][c - 1], A0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
-                        Nb<T> E{B0[c + 1], b0[c + 1], A0[0][c + 1], A0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
-                        Nb<T> S{Bm[c], bm[c], Am[0][c], Am[1][c], is_wet(Hm[c], bm[c], eps)};
-                        Nb<T> N{Bp[c], bp[c], Ap[0][c], Ap[1][c], is_wet(Hp[c], bp[c], eps)};
-                        T ax, ay, phi;
-                        forces(P, B0[c], b, rN(r)[c], A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
-                        const T den = T(1) + tauT * phi;
-                        utx = (ux + tauT * ax) / den;
-                        uty = (uy + tauT * ay) / den;
-                    }
-                    const T uhx = T(0.5) * (ux + utx), uhy = T(0.5) * (uy + uty);
-                    T sig = T(0), vx = T(0), vy = T(0);
-                    while (sp < se && a.src[sp].r < r) ++sp;
-                    for (int q = sp; q < se && a.src[q].r == r; ++q) {
-                        if (a.src[q].c == c) {
-                            sig = (T)(a.src[q].w * s.hq[a.src[q].hydro]);
-                            vx = (T)a.src[q].vx;
-                            vy = (T)a.src[q].vy;
-                        }
-                    }
-                    const T ts = tauT * sig;
-                    const T ht = tmax(T(0), H + ts);
-                    const T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
-                    const T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
-                    const bool wt = is_wet(ht, b, eps);
-                    T(*C)[WIN] = s.cS[r % DC];
-                    C[0][c] = ht;
-                    C[1][c] = uhx;
-                    C[2][c] = uhy;
-                    C[3][c] = wt ? qtx / ht : T(0);
-                    C[4][c] = wt ? qty / ht : T(0);
-                    C[5][c] = qtx;
-                    C[6][c] = qty;
-                    if (out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
-                }
+        if (ACC) {
+            if (groupL) {
+                stage0(k);
+                stage3(k - LG::S3);
+                stage7(k - LG::S7);
+            } else {
+                stage2(k - LG::S2);
+                stage4(k - LG::S4);
+                stage6(k - LG::S6);
             }
         } else {
-            // S4: MUSCL slopes and face fluxes of row k-8 (and its y face below)
-            {
-                const int r = k - LAG4;
-                auto ecell = [&](int rr, int col) {
-                    ECell<T> e;
-                    const T(*C)[WIN] = s.cS[rr % DC];
-                    const T bb = rB(rr)[col];
-                    e.w[0] = C[0][col];
-                    e.w[1] = C[1][col];
-                    e.w[2] = C[2][col];
-                    e.w[3] = C[3][col];
-                    e.w[4] = C[4][col];
-                    e.b = bb;
-                    e.wt = is_wet(e.w[0], bb, eps);
-                    return e;
-                };
-                if (r >= 4 && r <= nrows - 5 && c >= 3 && c < WIN - 3) {
-                    const ECell<T> em = ecell(r - 1, c), e0 = ecell(r, c), ep = ecell(r + 1, c);
-                    T syc[5];
-                    slopes(em, e0, ep, syc);
-                    if (r >= 5) face_flux(P, em, syPrev, e0, syc, 2, fyCur[0], fyCur[1], fyCur[2]);
-#pragma unroll
-                    for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
-                    if (r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 6) {
-                        const ECell<T> xm = ecell(r, c - 1), x1 = ecell(r, c + 1), x2 = ecell(r, c + 2);
-                        T sL[5], sR[5];
-                        slopes(xm, e0, x1, sL);
-                        slopes(e0, x1, x2, sR);
-                        T FH, FQx, FQy;
-                        face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
-                        s.fX[r % DF][0][c] = FH;
-                        s.fX[r % DF][1][c] = FQx;
-                        s.fX[r % DF][2][c] = FQy;
-                    }
-                }
-            }
-            // S6: final update of row k-9 (K8)
-            {
-                const int r = k - LAG6;
-                if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
-                    const T(*FX)[WIN] = s.fX[r % DF];
-                    T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
-                    T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
-                    T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
-                    if (a.corr && gx0 + c < a.g.nx + 2 * PAD) {
-                        // learned sub-grid corrections of the net flux sums
-                        const size_t gk = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
-                        fh += a.corr[gk];
-                        fqx += a.corr[a.corr_plane + gk];
-                        fqy += a.corr[2 * a.corr_plane + gk];
-                    }
-                    const T(*C)[WIN] = s.cS[r % DC];
-                    T hn = C[0][c] + dth * fh;
-                    double clip = 0.0;
-                    if (hn < T(0)) {
-                        clip = -(double)hn;
-                        hn = T(0);
-                    }
-                    T qxn = T(0), qyn = T(0);
-                    if (hn > eps) {
-                        qxn = C[5][c] + dth * fqx;
-                        qyn = C[6][c] + dth * fqy;
-                    }
-                    const T b = rB(r)[c];
-                    const bool wetn = is_wet(hn, b, eps);
-                    s.nS[r % DN][0][c] = hn;
-                    s.nS[r % DN][1][c] = wetn ? qxn / hn : T(0);
-                    s.nS[r % DN][2][c] = wetn ? qyn / hn : T(0);
-                    if (out_col && r >= HALO && r < HALO + sh) {
-                        const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
-                        outH[gi] = hn;
-                        outQx[gi] = qxn;
-                        outQy[gi] = qyn;
-                        acc_mass += (double)hn;
-                        acc_clip += clip;
-                        acc_wet += wetn ? 1 : 0;
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < 3; ++q) fyPrev[q] = fyCur[q];
-            }
-            // S7: signal speed of the new state at row k-11 (next step's K3)
-            {
-                const int r = k - LAG7;
-                if (r >= HALO && r < HALO + sh && out_col) {
-                    const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
-                    const int i0 = r % DN, im = (r - 1) % DN, ip = (r + 1) % DN;
-                    const T H = s.nS[i0][0][c], b = b0[c];
-                    if (is_wet(H, b, eps)) {
-                        const T ux = s.nS[i0][1][c], uy = s.nS[i0][2][c];
-                        Nb<T> W{s.nS[i0][0][c - 1], b0[c - 1], s.nS[i0][1][c - 1], s.nS[i0][2][c - 1],
-                                is_wet(s.nS[i0][0][c - 1], b0[c - 1], eps)};
-                        Nb<T> E{s.nS[i0][0][c + 1], b0[c + 1], s.nS[i0][1][c + 1], s.nS[i0][2][c + 1],
-                                is_wet(s.nS[i0][0][c + 1], b0[c + 1], eps)};
-                        Nb<T> S{s.nS[im][0][c], bm[c], s.nS[im][1][c], s.nS[im][2][c],
-                                is_wet(s.nS[im][0][c], bm[c], eps)};
-                        Nb<T> N{s.nS[ip][0][c], bp[c], s.nS[ip][1][c], s.nS[ip][2][c],
-                                is_wet(s.nS[ip][0][c], bp[c], eps)};
-                        T ax, ay, phi;
-                        forces(P, H, b, rN(r)[c], ux, uy, W, E, S, N, ax, ay, phi);
-                        const double v = (double)cell_speed(P, H, ux, uy, ax, ay);
-                        if (!(v <= DBL_MAX)) bad = true;
-                        else if (v > vmax) vmax = v;
-                    }
-                }
+            if (groupL) {
+                stage0(k);
+                stage1(k - LG::S1);
+                stage2(k - LG::S2);
+                stage3(k - LG::S3);
+            } else {
+                stage4(k - LG::S4);
+                stage6(k - LG::S6);
+                stage7(k - LG::S7);
             }
         }
         __syncthreads();
@@ -550,17 +599,18 @@ __device__ __forceinline__ void fused_init_barriers(FSmem<T>& s) {
 }
 
 // One grid: CTA b runs work item b.
-template <class T>
+template <class T, bool ACC>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
     FSmem<T>& s = fused_smem<T>();
     fused_init_barriers(s);
     unsigned cbase = 0;
-    fused_item(s, a, blockIdx.x, cbase);
+    fused_item<T, ACC>(s, a, blockIdx.x, cbase);
 }
 
 // Many grids in one persistent launch (batched ensemble): CTAs take
 // (scenario, item) entries from a device work list until it is exhausted;
 // each scenario keeps its own time, time step, sources, walls and report.
+// Every scenario is a context, so accelerations are stored (ACC).
 template <class T>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused_batch(const __grid_constant__ BatchArgs<T> b) {
     FSmem<T>& s = fused_smem<T>();
@@ -573,7 +623,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused_batch(cons
         __syncthreads();
         if (w >= b.nwork) break;
         const int2 e = b.work[w];
-        if (!fused_item(s, b.descs[e.x], e.y, cbase)) break;
+        if (!fused_item<T, true>(s, b.descs[e.x], e.y, cbase)) break;
     }
     if (threadIdx.x == 0) {
         __threadfence();
@@ -589,9 +639,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused_batch(cons
 template <class T>
 cudaError_t prepare_fused(int* ctas_per_sm) {
     const size_t smem = fused_smem_bytes<T>();
-    cudaError_t e = cudaFuncSetAttribute(k_fused<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fused<T>, NT, smem);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fused<T, true>, NT, smem);
 }
 
 template <class T>
@@ -610,7 +662,8 @@ cudaError_t launch_fused_batch(const BatchArgs<T>& b, int grid, cudaStream_t st)
 
 template <class T>
 cudaError_t launch_fused(const FusedArgs<T>& a, cudaStream_t st) {
-    k_fused<T><<<a.nitems, NT, fused_smem_bytes<T>(), st>>>(a);
+    if (a.g.A[0][0]) k_fused<T, true><<<a.nitems, NT, fused_smem_bytes<T>(), st>>>(a);
+    else k_fused<T, false><<<a.nitems, NT, fused_smem_bytes<T>(), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -847,6 +900,7 @@ __global__ void ks_final(const StagedArgs<T> a) {
 
 // Signal speed (and mass) of the state in buffer `which` (0: current,
 // 1: next); atomicMax into the smax slot of that state's step parity.
+// Where the grid stores accelerations, also writes them for that state.
 template <class T>
 __global__ void ks_speed(const StagedArgs<T> a, int which) {
     __shared__ double red[8];
@@ -882,6 +936,15 @@ __global__ void ks_speed(const StagedArgs<T> a, int which) {
                 bad = true;
                 v = 0.0;
             }
+            if (a.g.A[buf][0]) {
+                a.g.A[buf][0][k] = ax;
+                a.g.A[buf][1][k] = ay;
+                a.g.A[buf][2][k] = phi;
+            }
+        } else if (a.g.A[buf][0]) {
+            a.g.A[buf][0][k] = T(0);
+            a.g.A[buf][1][k] = T(0);
+            a.g.A[buf][2][k] = T(0);
         }
         if (!(mass <= DBL_MAX) || !(mass >= 0.0)) bad = true;
     }

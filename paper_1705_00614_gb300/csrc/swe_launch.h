@@ -69,11 +69,14 @@ struct Grid {
     T* Qy[2];
     T* b;
     T* n;
+    // accelerations (a_x, a_y, phi) of the state in each buffer, or null
+    T* A[2][3];
 };
 
 template <class T>
 struct FusedArgs {
     CUtensorMap tmH[2], tmQx[2], tmQy[2], tmB, tmN;
+    CUtensorMap tmA[2][3];
     Grid<T> g;
     Phys<T> P;
     StepP sp;
