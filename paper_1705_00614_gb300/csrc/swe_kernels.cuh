@@ -144,83 +144,107 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 //
 // Stages: S0 primitives U = Q/H; S1 forces at t_n and predictor U*; S2
 // particle area change and H*; S3 forces at t_{n+1/2}, corrector, sources;
-// S4 MUSCL slopes and face fluxes; S6 final update (K8); S7 signal speed of
-// the new state (the next step's K3).
+// S5 MUSCL slopes along x; S4 slopes along y and the face fluxes; S6 final
+// update (K8); S7 signal speed of the new state (the next step's K3).
 //
 // ACC = true (contexts): S7 also stores the new state's accelerations
 // (a_x, a_y, phi) in a second pair of ping-pong planes, and the next step's
 // S1 loads them instead of evaluating the forces again, so S0 and S1 merge.
-// Groups: L = {S0+S1 (lag 0), S3 (4), S7 (9)}, E = {S2 (2), S4 (6),
-// S6 (7)}.
+// Groups: L = {S0+S1 (lag 0), S3 (4), S5 (5), S7 (9)}, E = {S2 (2),
+// S4 (6), S6 (7)}.
 // ACC = false (caller-owned planes, no acceleration storage): groups
-// L = {S0 (0), S1 (2), S2 (4), S3 (6)}, E = {S4 (8), S6 (9), S7 (11)}.
-// Input rows (H, Qx, Qy, b, n and, with ACC, a_x, a_y, phi) arrive by TMA in
-// chunks of RB rows; each field has a ring of chunk slots as deep as its
-// oldest reader needs.
+// L = {S0 (0), S1 (2), S2 (4), S3 (6), S5 (7)}, E = {S4 (8), S6 (9),
+// S7 (11)}.
+// Input rows (H, Qx, Qy, b, n and, with ACC, a_x, a_y, phi) arrive by TMA
+// one row per copy, PREF rows ahead of the row S0 reads, into per-field
+// row rings.  Every ring holds a power of two of rows, so a row's slot is a
+// mask of its index.  The copy of row k + PREF, issued at iteration k,
+// overwrites row k + PREF - R, which must have been read for the last time
+// before iteration k: R >= PREF + 1 + (the field's oldest reading lag).
+// With ACC the rings are sized so that three FP32 CTAs fit on an SM.
 
 constexpr int NT = 2 * WIN;
-constexpr int DP = 7, DA = 6, DB = 4, DC = 4, DF = 2, DN = 4;   // stage ring depths (rows)
-constexpr int SLOT_Q = 2, SLOT_H = 4, SLOT_B = 5, SLOT_N = 5, SLOT_A = 2;  // chunk slots per input field
-constexpr int NBAR = 5;
+constexpr int NBAR = 4;   // > PREF: one mbarrier per row in flight
+constexpr int PREF = 2;
+static_assert(RB == 1, "the fused kernel streams one row per TMA copy");
 
 template <bool ACC>
 struct Lags {
-    static constexpr int S1 = ACC ? 0 : 2, S2 = ACC ? 2 : 4, S3 = ACC ? 4 : 6, S4 = ACC ? 6 : 8, S6 = ACC ? 7 : 9,
-                         S7 = ACC ? 9 : 11;
+    static constexpr int S1 = ACC ? 0 : 2, S2 = ACC ? 2 : 4, S3 = ACC ? 4 : 6, S5 = ACC ? 5 : 7, S4 = ACC ? 6 : 8,
+                         S6 = ACC ? 7 : 9, S7 = ACC ? 9 : 11;
 };
-constexpr int MAX_LAG7 = 11;
 
-template <class T>
+template <class T, bool ACC>
 struct FSmem {
-    T inH[SLOT_H][RB][WIN];
-    T inQx[SLOT_Q][RB][WIN];
-    T inQy[SLOT_Q][RB][WIN];
-    T inB[SLOT_B][RB][WIN];
-    T inN[SLOT_N][RB][WIN];
-    T inA[SLOT_A][3][RB][WIN];  // a_x, a_y, phi at t_n (ACC only)
-    T pU[DP][2][WIN];      // U at t_n
+    // input rings (rows).  Oldest readers, ACC: H and b S3 (row r-1), Q and
+    // n S3 (own row), a S0; without ACC: H and b S3 (r-1), n S3, Q S0.
+    // Later stages take b and n from the Eulerian ring cS.
+    static constexpr int RH = ACC ? 8 : 16, RQ = ACC ? 8 : 4, RB_ = ACC ? 8 : 16, RN = ACC ? 8 : 16,
+                         RA = ACC ? 4 : 1;
+    static_assert(RH >= PREF + 1 + Lags<ACC>::S3 + 1 && RB_ >= PREF + 1 + Lags<ACC>::S3 + 1, "H/b ring");
+    static_assert(RN >= PREF + 1 + Lags<ACC>::S3 && RQ >= PREF + 1 + (ACC ? Lags<ACC>::S3 : 0), "n/Q ring");
+    static_assert(!ACC || RA >= PREF + 1, "a ring");
+    // stage rings (rows); pU (U at t_n, read by S1 and S3) only without ACC:
+    // with ACC, S3 forms U from the Q ring itself
+    static constexpr int DP = ACC ? 1 : 8, DA = 8, DB = 4, DC = 4, DX = 2, DF = 2, DN = 4;
+    T inH[RH][WIN];
+    T inQx[RQ][WIN];
+    T inQy[RQ][WIN];
+    T inB[RB_][WIN];
+    T inN[RN][WIN];
+    T inA[3][RA][WIN];     // a_x, a_y, phi at t_n (ACC only)
+    T pU[DP][2][WIN];      // U at t_n (without ACC)
     T aU[DA][2][WIN];      // predictor U*
     T bH[DB][WIN];         // particle depth H*
-    T cS[DC][7][WIN];      // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y
+    T cS[DC][9][WIN];      // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y, b, n
+    T sX[DX][5][WIN];      // x slopes of H~, U^, U~'
     T fX[DF][3][WIN];      // x-face fluxes F_H, F_Qx, F_Qy
-    T nS[DN][3][WIN];      // new state H, Ux, Uy
+    T nS[DN][4][WIN];      // new state H, Ux, Uy with the cell's b
     unsigned long long bar[NBAR];
     double hq[MAX_HYDRO];
     double red[NT / 32];
     double tau;
     int last;
     int witem;
+    int abort;
 };
 
+template <class T, bool ACC>
+size_t fused_smem_bytes_v() {
+    return sizeof(FSmem<T, ACC>) + 128;
+}
 template <class T>
 size_t fused_smem_bytes() {
-    return sizeof(FSmem<T>) + 128;
+    return fused_smem_bytes_v<T, true>();
 }
 
 template <class T, bool ACC>
-__device__ __forceinline__ void issue_chunk(FSmem<T>& s, const FusedArgs<T>& a, int buf, int ch,
-                                            int gx0, int gy0, unsigned cbase) {
-    unsigned long long* bar = &s.bar[(cbase + (unsigned)ch) % NBAR];
-    mbar_expect_tx(bar, (ACC ? 8u : 5u) * RB * WIN * sizeof(T));
-    const int y = gy0 + ch * RB;
-    tma_load_2d(&s.inH[ch % SLOT_H][0][0], &a.tmH[buf], gx0, y, bar);
-    tma_load_2d(&s.inQx[ch % SLOT_Q][0][0], &a.tmQx[buf], gx0, y, bar);
-    tma_load_2d(&s.inQy[ch % SLOT_Q][0][0], &a.tmQy[buf], gx0, y, bar);
-    tma_load_2d(&s.inB[ch % SLOT_B][0][0], &a.tmB, gx0, y, bar);
-    tma_load_2d(&s.inN[ch % SLOT_N][0][0], &a.tmN, gx0, y, bar);
+__device__ __forceinline__ void issue_row(FSmem<T, ACC>& s, const FusedArgs<T>& a, int buf, int r0,
+                                          int gx0, int gy0, unsigned cbase) {
+    using S = FSmem<T, ACC>;
+    unsigned long long* bar = &s.bar[(cbase + (unsigned)r0) % NBAR];
+    mbar_expect_tx(bar, (ACC ? 8u : 5u) * WIN * sizeof(T));
+    const int y = gy0 + r0;
+    tma_load_2d(&s.inH[r0 & (S::RH - 1)][0], &a.tmH[buf], gx0, y, bar);
+    tma_load_2d(&s.inQx[r0 & (S::RQ - 1)][0], &a.tmQx[buf], gx0, y, bar);
+    tma_load_2d(&s.inQy[r0 & (S::RQ - 1)][0], &a.tmQy[buf], gx0, y, bar);
+    tma_load_2d(&s.inB[r0 & (S::RB_ - 1)][0], &a.tmB, gx0, y, bar);
+    tma_load_2d(&s.inN[r0 & (S::RN - 1)][0], &a.tmN, gx0, y, bar);
     if (ACC) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) tma_load_2d(&s.inA[ch % SLOT_A][q][0][0], &a.tmA[buf][q], gx0, y, bar);
+        for (int q = 0; q < 3; ++q) tma_load_2d(&s.inA[q][r0 & (S::RA - 1)][0], &a.tmA[buf][q], gx0, y, bar);
     }
 }
 
 // One work item (a window of one grid's segment): the whole step for it.
-// `cbase` counts the TMA chunks this CTA has waited for so far, so the
+// `cbase` counts the TMA rows this CTA has waited for so far, so the
 // mbarrier phases stay consistent across the items a persistent CTA runs.
 // Returns false when a bounded wait gave up (the CTA must stop).
 template <class T, bool ACC>
-__device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, const int item, unsigned& cbase) {
+__device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>& a, const int item,
+                                           unsigned& cbase) {
     using LG = Lags<ACC>;
+    using S = FSmem<T, ACC>;
     const int tid = threadIdx.x;
     const int c = tid & (WIN - 1);
     const bool groupL = tid < WIN;
@@ -229,7 +253,6 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
     const int tw = min(TW, a.g.nx - x0), sh = min(a.seg_h, a.g.ny - y0);
     const int gx0 = PAD + x0 - HALO, gy0 = PAD + y0 - HALO;
     const int nrows = sh + 2 * HALO;
-    const int nchunks = (nrows + RB - 1) / RB;
     const long long step = *(volatile const long long*)&a.ctl->step;
     const int buf = (int)(step & 1);
     const Phys<T>& P = a.P;
@@ -245,7 +268,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
     if (tid < a.nh) s.hq[tid] = hydro_value(a.hydro + 4 * tid, a.ctl->t + 0.5 * (double)tauT);
     if (tid == 0) {
         fence_proxy_async();
-        issue_chunk<T, ACC>(s, a, buf, 0, gx0, gy0, cbase);
+        for (int r = 0; r < PREF && r < nrows; ++r) issue_row<T, ACC>(s, a, buf, r, gx0, gy0, cbase);
     }
     __syncthreads();
 
@@ -254,12 +277,20 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
     T* const outQy = a.g.Qy[buf ^ 1];
     const bool out_col = (c >= HALO) && (c < HALO + tw);
 
-    auto rH = [&](int r) -> const T* { return s.inH[(r / RB) % SLOT_H][r % RB]; };
-    auto rQx = [&](int r) -> const T* { return s.inQx[(r / RB) % SLOT_Q][r % RB]; };
-    auto rQy = [&](int r) -> const T* { return s.inQy[(r / RB) % SLOT_Q][r % RB]; };
-    auto rB = [&](int r) -> const T* { return s.inB[(r / RB) % SLOT_B][r % RB]; };
-    auto rN = [&](int r) -> const T* { return s.inN[(r / RB) % SLOT_N][r % RB]; };
-    auto rA = [&](int q, int r) -> const T* { return s.inA[(r / RB) % SLOT_A][q][r % RB]; };
+    // ring rows (stage row indices are non-negative where they are used)
+    auto rH = [&](int r) -> const T* { return s.inH[r & (S::RH - 1)]; };
+    auto rQx = [&](int r) -> const T* { return s.inQx[r & (S::RQ - 1)]; };
+    auto rQy = [&](int r) -> const T* { return s.inQy[r & (S::RQ - 1)]; };
+    auto rB = [&](int r) -> const T* { return s.inB[r & (S::RB_ - 1)]; };
+    auto rN = [&](int r) -> const T* { return s.inN[r & (S::RN - 1)]; };
+    auto rA = [&](int q, int r) -> const T* { return s.inA[q][r & (S::RA - 1)]; };
+    auto pU = [&](int r) { return s.pU[r & (S::DP - 1)]; };
+    auto aU = [&](int r) { return s.aU[r & (S::DA - 1)]; };
+    auto bH = [&](int r) { return s.bH[r & (S::DB - 1)]; };
+    auto cS = [&](int r) { return s.cS[r & (S::DC - 1)]; };
+    auto sX = [&](int r) { return s.sX[r & (S::DX - 1)]; };
+    auto fX = [&](int r) { return s.fX[r & (S::DF - 1)]; };
+    auto nS = [&](int r) { return s.nS[r & (S::DN - 1)]; };
 
     int sp = a.src_off[item];
     const int se = a.src_off[item + 1];
@@ -277,8 +308,11 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
         const bool wet = is_wet(H, rB(k)[c], eps);
         const T ux = wet ? rQx(k)[c] / H : T(0);
         const T uy = wet ? rQy(k)[c] / H : T(0);
-        s.pU[k % DP][0][c] = ux;
-        s.pU[k % DP][1][c] = uy;
+        if (!ACC) {
+            T(*U)[WIN] = pU(k);
+            U[0][c] = ux;
+            U[1][c] = uy;
+        }
         if (ACC) {
             T usx = T(0), usy = T(0);
             if (wet) {
@@ -286,8 +320,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
                 usx = (ux + th * rA(0, k)[c]) / den;
                 usy = (uy + th * rA(1, k)[c]) / den;
             }
-            s.aU[k % DA][0][c] = usx;
-            s.aU[k % DA][1][c] = usy;
+            T(*A)[WIN] = aU(k);
+            A[0][c] = usx;
+            A[1][c] = usy;
         }
     };
     // S1: forces at t_n and predictor velocity U* (without ACC)
@@ -295,9 +330,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
         if (!(r >= 1 && r <= nrows - 2 && c >= 1 && c < WIN - 1)) return;
         const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
         const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
-        const T(*U0)[WIN] = s.pU[r % DP];
-        const T(*Um)[WIN] = s.pU[(r - 1) % DP];
-        const T(*Up)[WIN] = s.pU[(r + 1) % DP];
+        const T(*U0)[WIN] = pU(r);
+        const T(*Um)[WIN] = pU(r - 1);
+        const T(*Up)[WIN] = pU(r + 1);
         const T H = H0[c], b = b0[c];
         T usx = T(0), usy = T(0);
         if (is_wet(H, b, eps)) {
@@ -311,8 +346,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
             usx = (U0[0][c] + th * ax) / den;
             usy = (U0[1][c] + th * ay) / den;
         }
-        s.aU[r % DA][0][c] = usx;
-        s.aU[r % DA][1][c] = usy;
+        T(*A)[WIN] = aU(r);
+        A[0][c] = usx;
+        A[1][c] = usy;
     };
     // S2: particle area change and H*
     auto stage2 = [&](int r) {
@@ -320,36 +356,44 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
         const T H = rH(r)[c];
         T hs = H;
         if (is_wet(H, rB(r)[c], eps)) {
-            const T* Ax = s.aU[r % DA][0];
-            const T* Ay = s.aU[r % DA][1];
-            const T u = Ax[c], uW = Ax[c - 1], uE = Ax[c + 1];
-            const T v = Ay[c], vS = s.aU[(r - 1) % DA][1][c], vN = s.aU[(r + 1) % DA][1][c];
+            const T(*A0)[WIN] = aU(r);
+            const T u = A0[0][c], uW = A0[0][c - 1], uE = A0[0][c + 1];
+            const T v = A0[1][c], vS = aU(r - 1)[1][c], vN = aU(r + 1)[1][c];
             const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
             const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
             const T D = ((fxp - fxm) + (fyp - fym)) / P.h;
             hs = H / tmax(T(0.5), T(1) + th * D);
         }
-        s.bH[r % DB][c] = hs;
+        bH(r)[c] = hs;
     };
     // S3: forces at t_{n+1/2}, corrector and sources
     auto stage3 = [&](int r) {
         if (!(r >= 3 && r <= nrows - 4 && c >= 3 && c < WIN - 3)) return;
         const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
         const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
-        const T *B0 = s.bH[r % DB], *Bm = s.bH[(r - 1) % DB], *Bp = s.bH[(r + 1) % DB];
-        const T(*A0)[WIN] = s.aU[r % DA];
-        const T(*Am)[WIN] = s.aU[(r - 1) % DA];
-        const T(*Ap)[WIN] = s.aU[(r + 1) % DA];
+        const T *B0 = bH(r), *Bm = bH(r - 1), *Bp = bH(r + 1);
+        const T(*A0)[WIN] = aU(r);
+        const T(*Am)[WIN] = aU(r - 1);
+        const T(*Ap)[WIN] = aU(r + 1);
         const T H = H0[c], b = b0[c];
-        const T ux = s.pU[r % DP][0][c], uy = s.pU[r % DP][1][c];
+        const bool wet = is_wet(H, b, eps);
+        T ux, uy;
+        if (ACC) {
+            ux = wet ? rQx(r)[c] / H : T(0);
+            uy = wet ? rQy(r)[c] / H : T(0);
+        } else {
+            ux = pU(r)[0][c];
+            uy = pU(r)[1][c];
+        }
+        const T nm = rN(r)[c];
         T utx = T(0), uty = T(0);
-        if (is_wet(H, b, eps)) {
+        if (wet) {
             Nb<T> W{B0[c - 1], b0[c - 1], A0[0][c - 1], A0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
             Nb<T> E{B0[c + 1], b0[c + 1], A0[0][c + 1], A0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
             Nb<T> S{Bm[c], bm[c], Am[0][c], Am[1][c], is_wet(Hm[c], bm[c], eps)};
             Nb<T> N{Bp[c], bp[c], Ap[0][c], Ap[1][c], is_wet(Hp[c], bp[c], eps)};
             T ax, ay, phi;
-            forces(P, B0[c], b, rN(r)[c], A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
+            forces(P, B0[c], b, nm, A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
             const T den = T(1) + tauT * phi;
             utx = (ux + tauT * ax) / den;
             uty = (uy + tauT * ay) / den;
@@ -369,7 +413,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
         const T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
         const T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
         const bool wt = is_wet(ht, b, eps);
-        T(*C)[WIN] = s.cS[r % DC];
+        T(*C)[WIN] = cS(r);
         C[0][c] = ht;
         C[1][c] = uhx;
         C[2][c] = uhy;
@@ -377,23 +421,36 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
         C[4][c] = wt ? qty / ht : T(0);
         C[5][c] = qtx;
         C[6][c] = qty;
+        C[7][c] = b;
+        C[8][c] = nm;
         if (out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
     };
-    // S4: MUSCL slopes and face fluxes of row r (and its y face below)
+    auto ecell = [&](int rr, int col) {
+        ECell<T> e;
+        const T(*C)[WIN] = cS(rr);
+        const T bb = C[7][col];
+        e.w[0] = C[0][col];
+        e.w[1] = C[1][col];
+        e.w[2] = C[2][col];
+        e.w[3] = C[3][col];
+        e.w[4] = C[4][col];
+        e.b = bb;
+        e.wt = is_wet(e.w[0], bb, eps);
+        return e;
+    };
+    // S5: MUSCL slopes along x of row r (each cell once; the face fluxes
+    // read both sides' slopes)
+    auto stage5 = [&](int r) {
+        if (!(r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 5)) return;
+        T sx[5];
+        slopes(ecell(r, c - 1), ecell(r, c), ecell(r, c + 1), sx);
+        T(*X)[WIN] = sX(r);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) X[q][c] = sx[q];
+    };
+    // S4: MUSCL slopes along y and face fluxes of row r (x faces, and the y
+    // face below the row)
     auto stage4 = [&](int r) {
-        auto ecell = [&](int rr, int col) {
-            ECell<T> e;
-            const T(*C)[WIN] = s.cS[rr % DC];
-            const T bb = rB(rr)[col];
-            e.w[0] = C[0][col];
-            e.w[1] = C[1][col];
-            e.w[2] = C[2][col];
-            e.w[3] = C[3][col];
-            e.w[4] = C[4][col];
-            e.b = bb;
-            e.wt = is_wet(e.w[0], bb, eps);
-            return e;
-        };
         if (!(r >= 4 && r <= nrows - 5 && c >= 3 && c < WIN - 3)) return;
         const ECell<T> em = ecell(r - 1, c), e0 = ecell(r, c), ep = ecell(r + 1, c);
         T syc[5];
@@ -402,21 +459,26 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
 #pragma unroll
         for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
         if (r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 6) {
-            const ECell<T> xm = ecell(r, c - 1), x1 = ecell(r, c + 1), x2 = ecell(r, c + 2);
+            const ECell<T> x1 = ecell(r, c + 1);
+            const T(*X)[WIN] = sX(r);
             T sL[5], sR[5];
-            slopes(xm, e0, x1, sL);
-            slopes(e0, x1, x2, sR);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                sL[q] = X[q][c];
+                sR[q] = X[q][c + 1];
+            }
             T FH, FQx, FQy;
             face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
-            s.fX[r % DF][0][c] = FH;
-            s.fX[r % DF][1][c] = FQx;
-            s.fX[r % DF][2][c] = FQy;
+            T(*F)[WIN] = fX(r);
+            F[0][c] = FH;
+            F[1][c] = FQx;
+            F[2][c] = FQy;
         }
     };
     // S6: final update of row r (K8)
     auto stage6 = [&](int r) {
         if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
-            const T(*FX)[WIN] = s.fX[r % DF];
+            const T(*FX)[WIN] = fX(r);
             T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
             T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
             T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
@@ -427,7 +489,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
                 fqx += a.corr[a.corr_plane + gk];
                 fqy += a.corr[2 * a.corr_plane + gk];
             }
-            const T(*C)[WIN] = s.cS[r % DC];
+            const T(*C)[WIN] = cS(r);
             T hn = C[0][c] + dth * fh;
             double clip = 0.0;
             if (hn < T(0)) {
@@ -439,16 +501,22 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
                 qxn = C[5][c] + dth * fqx;
                 qyn = C[6][c] + dth * fqy;
             }
-            const T b = rB(r)[c];
+            const T b = C[7][c];
             const bool wetn = is_wet(hn, b, eps);
-            s.nS[r % DN][0][c] = hn;
-            s.nS[r % DN][1][c] = wetn ? qxn / hn : T(0);
-            s.nS[r % DN][2][c] = wetn ? qyn / hn : T(0);
+            const T uxn = wetn ? qxn / hn : T(0), uyn = wetn ? qyn / hn : T(0);
+            T(*Nw)[WIN] = nS(r);
+            Nw[0][c] = hn;
+            Nw[1][c] = uxn;
+            Nw[2][c] = uyn;
+            Nw[3][c] = b;
             if (out_col && r >= HALO && r < HALO + sh) {
                 const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
                 outH[gi] = hn;
                 outQx[gi] = qxn;
                 outQy[gi] = qyn;
+                // the friction coefficient of the new state is local to the
+                // cell; the next step's predictor reads it with a_x, a_y
+                if (ACC) a.g.A[buf ^ 1][2][gi] = wetn ? friction(P, hn, C[8][c], uxn, uyn) : T(0);
                 acc_mass += (double)hn;
                 acc_clip += clip;
                 acc_wet += wetn ? 1 : 0;
@@ -458,22 +526,22 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
         for (int q = 0; q < 3; ++q) fyPrev[q] = fyCur[q];
     };
     // S7: signal speed of the new state at row r (next step's K3); with ACC
-    // also its accelerations for the next step's predictor
+    // also its accelerations for the next step's predictor.  The new state
+    // carries b, so no input row older than S3's is needed.
     auto stage7 = [&](int r) {
         if (!(r >= HALO && r < HALO + sh && out_col)) return;
-        const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
-        const int i0 = r % DN, im = (r - 1) % DN, ip = (r + 1) % DN;
-        const T H = s.nS[i0][0][c], b = b0[c];
-        T ax = T(0), ay = T(0), phi = T(0);
+        const T(*N0)[WIN] = nS(r);
+        const T(*Nm)[WIN] = nS(r - 1);
+        const T(*Np)[WIN] = nS(r + 1);
+        const T H = N0[0][c], b = N0[3][c];
+        T ax = T(0), ay = T(0);
         if (is_wet(H, b, eps)) {
-            const T ux = s.nS[i0][1][c], uy = s.nS[i0][2][c];
-            Nb<T> W{s.nS[i0][0][c - 1], b0[c - 1], s.nS[i0][1][c - 1], s.nS[i0][2][c - 1],
-                    is_wet(s.nS[i0][0][c - 1], b0[c - 1], eps)};
-            Nb<T> E{s.nS[i0][0][c + 1], b0[c + 1], s.nS[i0][1][c + 1], s.nS[i0][2][c + 1],
-                    is_wet(s.nS[i0][0][c + 1], b0[c + 1], eps)};
-            Nb<T> S{s.nS[im][0][c], bm[c], s.nS[im][1][c], s.nS[im][2][c], is_wet(s.nS[im][0][c], bm[c], eps)};
-            Nb<T> N{s.nS[ip][0][c], bp[c], s.nS[ip][1][c], s.nS[ip][2][c], is_wet(s.nS[ip][0][c], bp[c], eps)};
-            forces(P, H, b, rN(r)[c], ux, uy, W, E, S, N, ax, ay, phi);
+            const T ux = N0[1][c], uy = N0[2][c];
+            Nb<T> W{N0[0][c - 1], N0[3][c - 1], N0[1][c - 1], N0[2][c - 1], is_wet(N0[0][c - 1], N0[3][c - 1], eps)};
+            Nb<T> E{N0[0][c + 1], N0[3][c + 1], N0[1][c + 1], N0[2][c + 1], is_wet(N0[0][c + 1], N0[3][c + 1], eps)};
+            Nb<T> S{Nm[0][c], Nm[3][c], Nm[1][c], Nm[2][c], is_wet(Nm[0][c], Nm[3][c], eps)};
+            Nb<T> N{Np[0][c], Np[3][c], Np[1][c], Np[2][c], is_wet(Np[0][c], Np[3][c], eps)};
+            accel(P, H, b, ux, uy, W, E, S, N, ax, ay);
             const double v = (double)cell_speed(P, H, ux, uy, ax, ay);
             if (!(v <= DBL_MAX)) bad = true;
             else if (v > vmax) vmax = v;
@@ -482,30 +550,26 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
             const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
             a.g.A[buf ^ 1][0][gi] = ax;
             a.g.A[buf ^ 1][1][gi] = ay;
-            a.g.A[buf ^ 1][2][gi] = phi;
         }
     };
 
     for (int k = 0; k <= nrows + LG::S7 - HALO - 1; ++k) {
-        if ((k % RB) == 0) {
-            const int ch = k / RB;
-            if (ch < nchunks) {
-                if (tid == 0 && ch + 1 < nchunks) {
-                    fence_proxy_async();
-                    issue_chunk<T, ACC>(s, a, buf, ch + 1, gx0, gy0, cbase);
-                }
-                const unsigned gch = cbase + (unsigned)ch;
-                const bool ok = mbar_wait_bounded(&s.bar[gch % NBAR], (gch / NBAR) & 1u);
-                if (__syncthreads_or(!ok)) {
-                    if (tid == 0) atomicOr(&a.ctl->err, (unsigned)ERR_TIMEOUT);
-                    return false;
-                }
+        if (k < nrows) {
+            if (tid == 0 && k + PREF < nrows) {
+                fence_proxy_async();
+                issue_row<T, ACC>(s, a, buf, k + PREF, gx0, gy0, cbase);
             }
+            // every thread observes the copy of row k; a wait that gives up
+            // is reported after the iteration's barrier (the row's values
+            // are then garbage, but every index stays in bounds)
+            const unsigned gr = cbase + (unsigned)k;
+            if (!mbar_wait_bounded(&s.bar[gr % NBAR], (gr / NBAR) & 1u)) s.abort = 1;
         }
         if (ACC) {
             if (groupL) {
                 stage0(k);
                 stage3(k - LG::S3);
+                stage5(k - LG::S5);
                 stage7(k - LG::S7);
             } else {
                 stage2(k - LG::S2);
@@ -518,6 +582,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
                 stage1(k - LG::S1);
                 stage2(k - LG::S2);
                 stage3(k - LG::S3);
+                stage5(k - LG::S5);
             } else {
                 stage4(k - LG::S4);
                 stage6(k - LG::S6);
@@ -525,6 +590,10 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
             }
         }
         __syncthreads();
+        if (s.abort) {
+            if (tid == 0) atomicOr(&a.ctl->err, (unsigned)ERR_TIMEOUT);
+            return false;
+        }
     }
 
     // per-CTA partials, the next step's signal speed, and the step report
@@ -577,22 +646,27 @@ __device__ __forceinline__ bool fused_item(FSmem<T>& s, const FusedArgs<T>& a, c
             __threadfence();
         }
     }
-    cbase += (unsigned)nchunks;
+    cbase += (unsigned)nrows;
     __syncthreads();
     return true;
 }
 
-template <class T>
-__device__ __forceinline__ FSmem<T>& fused_smem() {
+template <class T, bool ACC>
+__device__ __forceinline__ FSmem<T, ACC>& fused_smem() {
+    // Round up to 128 bytes (TMA destinations) by offsetting into the shared
+    // array itself: the compiler then still knows every access is to shared
+    // memory (32-bit LDS/STS addressing instead of generic 64-bit loads).
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    return *reinterpret_cast<FSmem<T>*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    const unsigned off = (128u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u;
+    return *reinterpret_cast<FSmem<T, ACC>*>(smem_raw + off);
 }
 
-template <class T>
-__device__ __forceinline__ void fused_init_barriers(FSmem<T>& s) {
+template <class T, bool ACC>
+__device__ __forceinline__ void fused_init_barriers(FSmem<T, ACC>& s) {
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int i = 0; i < NBAR; ++i) mbar_init(&s.bar[i], 1);
+        s.abort = 0;
         fence_mbar_init();
     }
     __syncthreads();
@@ -600,8 +674,8 @@ __device__ __forceinline__ void fused_init_barriers(FSmem<T>& s) {
 
 // One grid: CTA b runs work item b.
 template <class T, bool ACC>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
-    FSmem<T>& s = fused_smem<T>();
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
+    FSmem<T, ACC>& s = fused_smem<T, ACC>();
     fused_init_barriers(s);
     unsigned cbase = 0;
     fused_item<T, ACC>(s, a, blockIdx.x, cbase);
@@ -612,8 +686,8 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused(const __gr
 // each scenario keeps its own time, time step, sources, walls and report.
 // Every scenario is a context, so accelerations are stored (ACC).
 template <class T>
-__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused_batch(const __grid_constant__ BatchArgs<T> b) {
-    FSmem<T>& s = fused_smem<T>();
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_fused_batch(const __grid_constant__ BatchArgs<T> b) {
+    FSmem<T, true>& s = fused_smem<T, true>();
     fused_init_barriers(s);
     unsigned cbase = 0;
     while (true) {
@@ -638,10 +712,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1) k_fused_batch(cons
 // Opt the fused kernel into its shared-memory size; returns CTAs per SM.
 template <class T>
 cudaError_t prepare_fused(int* ctas_per_sm) {
-    const size_t smem = fused_smem_bytes<T>();
+    const size_t smem = fused_smem_bytes_v<T, true>();
     cudaError_t e = cudaFuncSetAttribute(k_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)fused_smem_bytes_v<T, false>());
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, k_fused<T, true>, NT, smem);
 }
@@ -662,8 +737,8 @@ cudaError_t launch_fused_batch(const BatchArgs<T>& b, int grid, cudaStream_t st)
 
 template <class T>
 cudaError_t launch_fused(const FusedArgs<T>& a, cudaStream_t st) {
-    if (a.g.A[0][0]) k_fused<T, true><<<a.nitems, NT, fused_smem_bytes<T>(), st>>>(a);
-    else k_fused<T, false><<<a.nitems, NT, fused_smem_bytes<T>(), st>>>(a);
+    if (a.g.A[0][0]) k_fused<T, true><<<a.nitems, NT, fused_smem_bytes_v<T, true>(), st>>>(a);
+    else k_fused<T, false><<<a.nitems, NT, fused_smem_bytes_v<T, false>(), st>>>(a);
     return cudaGetLastError();
 }
 

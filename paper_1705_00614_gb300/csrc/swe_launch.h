@@ -21,7 +21,7 @@ constexpr int PAD = 10;
 constexpr int WIN = 128;
 constexpr int HALO = 6;
 constexpr int TW = WIN - 2 * HALO;
-constexpr int RB = 4;      // rows per TMA chunk
+constexpr int RB = 1;      // rows per TMA chunk
 constexpr int NSLOT = 4;   // chunk slots in shared memory
 constexpr int MAX_HYDRO = 32;
 

@@ -76,13 +76,11 @@ struct Nb {
     bool wet;
 };
 
-// Forces of Eqs. 2-4 on a wet cell (stage I, K2; and K5 at t_{n+1/2}):
-// a = a^P + a^V + a^C + a^W and the friction coefficient phi with
-// F^fric = -phi U, phi = g n^2 |U| / H^{4/3}.
+// Accelerations of Eqs. 2-4 on a wet cell without friction (stage I, K2;
+// and K5 at t_{n+1/2}): a = a^P + a^V + a^C + a^W.
 template <class T>
-__device__ __forceinline__ void forces(const Phys<T>& P, T hs, T b, T nm, T ux, T uy,
-                                       const Nb<T>& W, const Nb<T>& E, const Nb<T>& S,
-                                       const Nb<T>& N, T& ax, T& ay, T& phi) {
+__device__ __forceinline__ void accel(const Phys<T>& P, T hs, T b, T ux, T uy, const Nb<T>& W,
+                                      const Nb<T>& E, const Nb<T>& S, const Nb<T>& N, T& ax, T& ay) {
     // pressure -g grad(eta) in the well-balanced face form
     T dxm = face_delta(W.hs, W.b, hs, b);
     T dxp = face_delta(hs, b, E.hs, E.b);
@@ -108,9 +106,24 @@ __device__ __forceinline__ void forces(const Phys<T>& P, T hs, T b, T nm, T ux, 
     T aWx = cw * dwx, aWy = cw * dwy;
     ax = ((aPx + aVx) + aCx) + aWx;
     ay = ((aPy + aVy) + aCy) + aWy;
-    // Manning friction coefficient
+}
+
+// Manning friction coefficient of a wet cell: F^fric = -phi U with
+// phi = g n^2 |U| / H^{4/3} (Eq. 4); it depends on the cell alone.
+template <class T>
+__device__ __forceinline__ T friction(const Phys<T>& P, T hs, T nm, T ux, T uy) {
     T um = sqrt(ux * ux + uy * uy);
-    phi = P.g * nm * nm * um / pow43(hs);
+    return P.g * nm * nm * um / pow43(hs);
+}
+
+// Forces of Eqs. 2-4 on a wet cell: the accelerations and the friction
+// coefficient.
+template <class T>
+__device__ __forceinline__ void forces(const Phys<T>& P, T hs, T b, T nm, T ux, T uy,
+                                       const Nb<T>& W, const Nb<T>& E, const Nb<T>& S,
+                                       const Nb<T>& N, T& ax, T& ay, T& phi) {
+    accel(P, hs, b, ux, uy, W, E, S, N, ax, ay);
+    phi = friction(P, hs, nm, ux, uy);
 }
 
 // Signal speed of a wet cell (Fig. 2): max(U_s, U_p).
