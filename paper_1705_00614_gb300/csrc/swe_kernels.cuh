@@ -150,7 +150,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // ACC = true (contexts): S7 also stores the new state's accelerations
 // (a_x, a_y, phi) in a second pair of ping-pong planes, and the next step's
 // S1 loads them instead of evaluating the forces again, so S0 and S1 merge.
-// Groups: L = {S0+S1 (lag 0), S3 (4), S5 (5), S7 (9)}, E = {S2 (2),
+// Groups: L = {S0+S1 (lag 0), S2 (2), S3 (4), S7 (9)}, E = {S5 (5),
 // S4 (6), S6 (7)}.
 // ACC = false (caller-owned planes, no acceleration storage): groups
 // L = {S0 (0), S1 (2), S2 (4), S3 (6), S5 (7)}, E = {S4 (8), S6 (9),
@@ -568,11 +568,11 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         if (ACC) {
             if (groupL) {
                 stage0(k);
+                stage2(k - LG::S2);
                 stage3(k - LG::S3);
-                stage5(k - LG::S5);
                 stage7(k - LG::S7);
             } else {
-                stage2(k - LG::S2);
+                stage5(k - LG::S5);
                 stage4(k - LG::S4);
                 stage6(k - LG::S6);
             }
