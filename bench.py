@@ -16,7 +16,14 @@ Prints one JSON line:
                state back (swe_get_state), copies inside the timed region
   roofline     the fused kernel against measured HBM copy bandwidth:
                32 algorithmic bytes per cell (read H, Qx, Qy, b, n; write
-               H, Qx, Qy in FP32) over its CUDA-event time per launch
+               H, Qx, Qy in FP32) over its CUDA-event time per launch;
+               traffic = DRAM bytes per launch from the committed ncu
+               summary (the kernel also stores the state's accelerations,
+               56 B/cell in all)
+  alu_roofline the same kernel against the instruction-issue ceiling it is
+               actually bound by: warp instructions per cell (committed ncu
+               summary) x cells / time, over SMs x 4 schedulers x the SM
+               clock sampled during the timed region
   cpu_baseline the FP64 CPU oracle on a bounded crop of the same workload
 ``--impl reference`` times the oracle alone on the host cores.
 """
@@ -182,9 +189,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.samples)}
 
 
-def traffic_from_profile(workload):
-    """DRAM bytes per launch of the fused kernel from the committed ncu
-    summary, if it was taken on the current kernel sources."""
+def alu_roofline(prof, cells, ms_per_step, nsm, clocks):
+    """Instruction-issue roofline: one warp instruction per scheduler per
+    cycle, four schedulers per SM."""
+    mhz = clocks.get("sm_mhz")
+    if prof is None or not mhz:
+        return None
+    achieved = prof["inst"] * cells / (ms_per_step * 1e-3) / 1e9
+    peak = nsm * 4 * mhz * 1e6 / 1e9
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp-instructions/s",
+            "frac": achieved / peak, "inst_per_cell": prof["inst"],
+            "peak_basis": f"{nsm} SMs x 4 schedulers x {mhz:.0f} MHz (median sampled SM clock)"}
+
+
+def profile_per_cell(workload):
+    """DRAM bytes and warp instructions per cell of the fused kernel from
+    the committed ncu summary, if it was taken on the current kernel
+    sources (else None)."""
     path = os.path.join(ROOT, "profiles", "k_fused_f32_dram.txt")
     if not os.path.exists(path):
         return None
@@ -196,10 +217,9 @@ def traffic_from_profile(workload):
     if kv.get("kernel_sources_sha256_16") != kernel_hash():
         return None
     try:
-        per_cell = float(kv["dram_bytes_per_cell"])
+        return {"dram": float(kv["dram_bytes_per_cell"]), "inst": float(kv["warp_inst_per_cell"])}
     except (KeyError, ValueError):
         return None
-    return per_cell
 
 
 def oracle_rate(prob, steps, cells_hint=None):
@@ -352,7 +372,8 @@ def main():
         peak_src = "measured"
     else:
         peak, peak_src = 6800.0, "fallback"
-    tr = traffic_from_profile(args.workload)
+    prof = profile_per_cell(args.workload) if args.precision == "f32" else None
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
     solver.close()
 
     if rank == 0:
@@ -369,13 +390,15 @@ def main():
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": args.workload, "cells": cells, "dx_m": prob.params.dx,
                            "initial_eta_m": round(eta0, 4), "wet_fraction": float((prob.H > prob.params.eps).mean()),
-                           "l2": "inputs larger than L2 (state + statics 5.4 GB per step)",
+                           "l2": f"inputs larger than L2 ({8 * cells * (4 if args.precision == 'f32' else 8) / 1e9:.1f} GB read per step)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "final_t_s": info["t"], "wet_cells_end": info["wet_cells"]},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src,
-                             "traffic": None if tr is None else tr * cells,
-                             "kernel": "k_fused<float>", "algorithmic_bytes_per_cell": bpc},
+                             "traffic": None if prof is None else prof["dram"] * cells,
+                             "kernel": f"k_fused<{'float' if args.precision == 'f32' else 'double'}>",
+                             "algorithmic_bytes_per_cell": bpc},
+                "alu_roofline": alu_roofline(prof, cells, ms_per_step, nsm, clk.summary()),
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
                 "gpu_launches": args.steps,
