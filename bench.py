@@ -61,9 +61,13 @@ def kernel_hash():
 
 def flooded_workload(name):
     """The benchmark problem: a named floodplain, filled to its median
-    terrain height (still water), keeping the inflow strip and physics."""
+    terrain height (still water), keeping the inflow strip and physics.
+    Without the "-flooded" suffix the floodplain starts dry (the inflow
+    strip is the only water), the case dry-tile skipping is for."""
     base = name.replace("-flooded", "")
     p = I.workload(base)
+    if not name.endswith("-flooded"):
+        return p.to_f32_values(), None
     eta0 = float(np.median(p.b))
     H = np.maximum(0.0, eta0 - p.b)
     z = np.zeros_like(H)
@@ -270,6 +274,9 @@ def main():
     ap.add_argument("--ref-crop", type=int, default=768)
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--skip-dry", action="store_true",
+                    help="skip dry work items (the paper's K1 wet-block test); off for the headline")
+    ap.add_argument("--seg-h", type=int, default=0, help="output rows per work item (0 = automatic)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -310,7 +317,8 @@ def main():
     # CUDA events below are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    solver = swe.Solver.from_problem(prob, args.precision, stream=stream.cuda_stream)
+    solver = swe.Solver.from_problem(prob, args.precision, stream=stream.cuda_stream, seg_h=args.seg_h,
+                                     skip_dry=args.skip_dry)
 
     # instantiate the CUDA graph of K steps once, restart, then W untimed
     # single-launch warm-up steps (they leave the cached K-step graph alone)
@@ -389,7 +397,10 @@ def main():
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": args.workload, "cells": cells, "dx_m": prob.params.dx,
-                           "initial_eta_m": round(eta0, 4), "wet_fraction": float((prob.H > prob.params.eps).mean()),
+                           "initial_eta_m": None if eta0 is None else round(eta0, 4),
+                           "wet_fraction": float((prob.H > prob.params.eps).mean()),
+                           "skip_dry": args.skip_dry, "seg_h": args.seg_h or "auto",
+                           "skipped_items_last_step": info["skipped"],
                            "l2": f"inputs larger than L2 ({8 * cells * (4 if args.precision == 'f32' else 8) / 1e9:.1f} GB read per step)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "final_t_s": info["t"], "wet_cells_end": info["wet_cells"]},

@@ -81,6 +81,17 @@ typedef struct {
     void* cuda_stream;     /* cudaStream_t to run on; borrowed, may be NULL */
     int32_t tile_w;        /* fused mode: output columns per CTA (0 = auto) */
     int32_t seg_h;         /* fused mode: output rows per CTA (0 = auto) */
+    int32_t skip_dry;      /* fused mode, 0 or 1: skip dry tiles (the wet-block
+                              test of the paper's kernel K1, Sec. 3).  A work
+                              item whose window (its cells and the 6-cell ring
+                              a step reads) holds no wet cell and no source
+                              cell is not computed: its cells keep H and get
+                              Q = 0, bitwise what the full step computes for
+                              them.  Wetness is kept per 32 x 16-cell block as
+                              the last step at which the block held a wet
+                              cell.  Never applied to swe_step_closed.
+                              Off by default (throughput then does not depend
+                              on the wet fraction). */
 } swe_params;
 
 /* What one call of swe_step reports (all reductions in FP64). */
@@ -94,7 +105,7 @@ typedef struct {
     int64_t wet_cells; /* cells with H > eps_dry after the last step */
     int64_t step;      /* steps taken since swe_set_state */
     int32_t err_word;  /* device error bits (0 = none) */
-    int32_t pad;
+    int32_t skipped;   /* work items of the last step skipped as dry (skip_dry) */
 } swe_step_info;
 
 /* Fill p with defaults: g 9.81, K 0.3, eps 1e-4, dt_max 1, FP32, fused,

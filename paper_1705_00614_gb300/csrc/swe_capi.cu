@@ -117,6 +117,10 @@ struct swe_ctx {
     double* d_acc = nullptr;
     cudaGraphExec_t cexec = nullptr;
     int csteps = 0;
+    // wet-block stamps (skip_dry)
+    long long* d_act = nullptr;
+    int act_nbx = 0, act_nby = 0;
+    unsigned char* d_hist = nullptr;  // per-item skip history (parts_cap bytes)
 };
 
 namespace {
@@ -185,6 +189,10 @@ StagedArgs<T> staged_args(const swe_ctx* c) {
     a.nsrc = c->nsrc;
     a.hydro = c->d_hydro;
     a.nh = c->nh;
+    a.act = c->d_act;
+    a.act_nbx = c->act_nbx;
+    a.hist = c->d_hist;
+    a.nhist = c->d_hist ? c->parts_cap : 0;
     return a;
 }
 
@@ -214,6 +222,10 @@ FusedArgs<T> fused_args(const swe_ctx* c, bool closed = false) {
     a.seg_h = c->seg_h;
     a.nitems = c->nitems;
     a.corr = closed ? (const T*)c->d_corr : nullptr;
+    a.act = c->d_act;
+    a.act_nbx = c->act_nbx;
+    a.skip = (c->d_act && !closed) ? 1 : 0;  // closed steps stamp but never skip
+    a.hist = c->d_hist;
     a.corr_plane = (size_t)c->pitch * (size_t)c->rows;
     return a;
 }
@@ -342,8 +354,6 @@ int launch_one_step(swe_ctx* c) {
     return SWE_OK;
 }
 
-size_t cells_padded(const swe_ctx* c) { return (size_t)c->pitch * (size_t)c->rows; }
-
 // Per-work-item source lists of the fused kernel, in window coordinates and
 // sorted by (row, column).
 int build_source_tables(swe_ctx* c, const int32_t* ix, const int32_t* iy, const double* w, const double* vx,
@@ -428,7 +438,14 @@ int retile(swe_ctx* c, int seg_h) {
         if (cudaMalloc(&c->parts, c->parts_cap * sizeof(Part)) != cudaSuccess ||
             cudaMalloc(&c->parts2, c->parts_cap * sizeof(Part)) != cudaSuccess)
             return fail(SWE_ERR_OOM, "partials");
+        if (c->d_act) {
+            cudaFree(c->d_hist);
+            c->d_hist = nullptr;
+            if (cudaMalloc(&c->d_hist, c->parts_cap) != cudaSuccess) return fail(SWE_ERR_OOM, "skip history");
+        }
     }
+    // the items changed: no item has a skip history
+    if (c->d_hist) CK(cudaMemsetAsync(c->d_hist, 0, c->parts_cap, c->st));
     drop_graph(c);
     c->generation++;
     const int n = c->nsrc;
@@ -467,6 +484,8 @@ int snapshot_restore(swe_ctx* c, Snapshot& sn) {
     }
     *c->ctl_host = sn.ctl;
     CK(cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
+    // the other buffer holds trial steps: no item may rely on it
+    if (c->d_hist) CK(cudaMemsetAsync(c->d_hist, 0, c->parts_cap, c->st));
     CK(cudaStreamSynchronize(c->st));
     return SWE_OK;
 }
@@ -682,6 +701,8 @@ int swe_create(const swe_params* p, swe_ctx** out) {
     if (p->mode != SWE_FUSED && p->mode != SWE_STAGED) return fail(SWE_ERR_ARG, "mode");
     if (p->seg_h < 0 || p->seg_h > 32768 || p->tile_w < 0) return fail(SWE_ERR_ARG, "tiling");
     if (p->tile_w != 0 && p->tile_w != TW) return fail(SWE_ERR_ARG, "tile_w must be 0 or 116");
+    if (p->skip_dry != 0 && p->skip_dry != 1) return fail(SWE_ERR_ARG, "skip_dry must be 0 or 1");
+    if (p->skip_dry && p->mode != SWE_FUSED) return fail(SWE_ERR_ARG, "skip_dry needs SWE_FUSED");
     swe_ctx* c = new (std::nothrow) swe_ctx();
     if (!c) return fail(SWE_ERR_OOM, "context");
     c->p = *p;
@@ -750,6 +771,16 @@ int swe_create(const swe_params* p, swe_ctx** out) {
             std::string m = g_err;
             return bail(rc, m);
         }
+    }
+    if (p->skip_dry) {
+        // stamps start far in the past: no block is known to be wet
+        c->act_nbx = (p->nx + (1 << ACT_LX) - 1) >> ACT_LX;
+        c->act_nby = (p->ny + (1 << ACT_LY) - 1) >> ACT_LY;
+        const size_t nb = (size_t)c->act_nbx * c->act_nby * sizeof(long long);
+        if (cudaMalloc(&c->d_act, nb) != cudaSuccess) return bail(SWE_ERR_OOM, "wet-block stamps");
+        if (cudaMemsetAsync(c->d_act, 0x80, nb, c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "memset");
+        if (cudaMalloc(&c->d_hist, c->parts_cap) != cudaSuccess) return bail(SWE_ERR_OOM, "skip history");
+        if (cudaMemsetAsync(c->d_hist, 0, c->parts_cap, c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "memset");
     }
     c->h_b.assign((size_t)p->nx * p->ny, 0.0);
     c->h_solid.assign((size_t)p->nx * p->ny, 0);
@@ -952,7 +983,7 @@ int swe_step(swe_ctx* c, int32_t nsteps, double t_end, swe_step_info* info) {
         info->wet_cells = h.wet;
         info->step = h.step;
         info->err_word = (int32_t)h.err;
-        info->pad = 0;
+        info->skipped = (int32_t)h.skipped;
         if (h.err & ERR_TIMEOUT) return fail(SWE_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
         if (h.err & ERR_NONFINITE) return fail(SWE_ERR_NONFINITE, "non-finite signal speed or state");
     }
@@ -1210,7 +1241,7 @@ int swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos) {
             info->wet_cells = h.wet;
             info->step = h.step;
             info->err_word = (int32_t)h.err;
-            info->pad = 0;
+            info->skipped = (int32_t)h.skipped;
             if (h.err & ERR_TIMEOUT) rc = fail(SWE_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
             else if ((h.err & ERR_NONFINITE) && !rc) rc = fail(SWE_ERR_NONFINITE, "non-finite signal speed");
         }
@@ -1438,6 +1469,8 @@ void swe_destroy(swe_ctx* c) {
     cudaFree(c->d_feat);
     cudaFree(c->d_corr);
     cudaFree(c->d_acc);
+    cudaFree(c->d_act);
+    cudaFree(c->d_hist);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
 }

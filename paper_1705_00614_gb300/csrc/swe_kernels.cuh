@@ -265,8 +265,29 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     const T tauT = (T)tau;
     const T th = T(0.5) * tauT;
     const T dth = tauT / P.h;
+    // Wet-block test (the paper's K1): with no wet cell and no source in the
+    // window this item reads, the step maps every output cell to itself
+    // with Q = 0 (no force acts, every face flux is +0), so the item is
+    // written directly.  Stamps of other items of this step may be raised
+    // to step + 1 concurrently, which only keeps a block active.
+    bool skip = false;
+    if (a.skip && a.src_off[item] == a.src_off[item + 1]) {
+        const int cx0 = max(0, x0 - HALO), cx1 = min(a.g.nx - 1, x0 + tw - 1 + HALO);
+        const int cy0 = max(0, y0 - HALO), cy1 = min(a.g.ny - 1, y0 + sh - 1 + HALO);
+        const int bx0 = cx0 >> ACT_LX, nbx = (cx1 >> ACT_LX) - bx0 + 1;
+        const int by0 = cy0 >> ACT_LY, nby = (cy1 >> ACT_LY) - by0 + 1;
+        bool active = false;
+        for (int i = tid; i < nbx * nby; i += NT)
+            active |= __ldcg(&a.act[(size_t)(by0 + i / nbx) * a.act_nbx + bx0 + i % nbx]) >= step;
+        skip = !__syncthreads_or(active);
+    }
+    // skipped in this step and the two before: the output buffer was written
+    // two steps ago with what this step would write (H already free of -0,
+    // Q = 0, a = 0), and the item's partial sums of the last step still hold
+    const unsigned hprev = a.hist ? (unsigned)a.hist[item] : 0u;
+    const bool still = skip && hprev == 3u;
     if (tid < a.nh) s.hq[tid] = hydro_value(a.hydro + 4 * tid, a.ctl->t + 0.5 * (double)tauT);
-    if (tid == 0) {
+    if (tid == 0 && !skip) {
         fence_proxy_async();
         for (int r = 0; r < PREF && r < nrows; ++r) issue_row<T, ACC>(s, a, buf, r, gx0, gy0, cbase);
     }
@@ -299,6 +320,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     double acc_mass = 0.0, acc_src = 0.0, acc_clip = 0.0, vmax = 0.0;
     long long acc_wet = 0;
     bool bad = false;
+    bool band_wet = false;  // a wet new cell in this column's current stamp band
 
     // S0: primitives at row k (and, with ACC, the predictor velocity from
     // the stored accelerations of the state at t_n)
@@ -520,6 +542,16 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                 acc_mass += (double)hn;
                 acc_clip += clip;
                 acc_wet += wetn ? 1 : 0;
+                if (a.act) {
+                    // stamp the blocks of the new state that hold a wet cell
+                    band_wet = band_wet || wetn;
+                    const int gy = y0 + r - HALO;
+                    if ((gy & ((1 << ACT_LY) - 1)) == (1 << ACT_LY) - 1 || r == HALO + sh - 1) {
+                        if (band_wet)
+                            a.act[(size_t)(gy >> ACT_LY) * a.act_nbx + ((x0 + c - HALO) >> ACT_LX)] = step + 1;
+                        band_wet = false;
+                    }
+                }
             }
         }
 #pragma unroll
@@ -553,6 +585,33 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         }
     };
 
+    if (skip) {
+        if (out_col && !still) {
+            if (groupL) {
+                for (int r = HALO; r < HALO + sh; ++r) {
+                    const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
+                    outQx[gi] = T(0);
+                    outQy[gi] = T(0);
+                    if (ACC) {
+                        a.g.A[buf ^ 1][0][gi] = T(0);
+                        a.g.A[buf ^ 1][1][gi] = T(0);
+                        a.g.A[buf ^ 1][2][gi] = T(0);
+                    }
+                }
+            } else {
+                // H^{n+1} = max(0, H + tau*0) + (tau/h)*(+0): H, with -0 turned
+                // into +0 (tested on the bits, as fast math may drop the + 0)
+                const T* inH = a.g.H[buf];
+                for (int r = HALO; r < HALO + sh; ++r) {
+                    const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
+                    const T H = inH[gi];
+                    const T hn = is_neg_zero(H) ? T(0) : H;
+                    outH[gi] = hn;
+                    acc_mass += (double)hn;
+                }
+            }
+        }
+    } else {
     for (int k = 0; k <= nrows + LG::S7 - HALO - 1; ++k) {
         if (k < nrows) {
             if (tid == 0 && k + PREF < nrows) {
@@ -595,6 +654,8 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             return false;
         }
     }
+    cbase += (unsigned)nrows;
+    }
 
     // per-CTA partials, the next step's signal speed, and the step report
     const double bmax = block_max<NT>(vmax, s.red);
@@ -608,8 +669,10 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         p.mass = bmass;
         p.src = bsrc;
         p.clip = bclip;
-        p.wet = (long long)bwet;
-        a.parts[item] = p;
+        p.wet = (int)bwet;
+        p.skipped = skip ? 1 : 0;
+        if (!still) a.parts[item] = p;
+        if (a.hist) a.hist[item] = (unsigned char)(((hprev << 1) | (skip ? 1u : 0u)) & 3u);
         if (anybad) atomicOr(&a.ctl->err, (unsigned)ERR_NONFINITE);
         atomicMax(&a.ctl->smax[buf ^ 1], (unsigned long long)__double_as_longlong(bmax));
         __threadfence();
@@ -619,17 +682,19 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     __syncthreads();
     if (s.last) {
         __threadfence();
-        double m = 0.0, sr = 0.0, cl = 0.0, w = 0.0;
+        double m = 0.0, sr = 0.0, cl = 0.0, w = 0.0, sk = 0.0;
         for (int i = tid; i < a.nitems; i += NT) {
             m += __ldcg(&a.parts[i].mass);
             sr += __ldcg(&a.parts[i].src);
             cl += __ldcg(&a.parts[i].clip);
             w += (double)__ldcg(&a.parts[i].wet);
+            sk += (double)__ldcg(&a.parts[i].skipped);
         }
         m = block_sum<NT>(m, s.red);
         sr = block_sum<NT>(sr, s.red);
         cl = block_sum<NT>(cl, s.red);
         w = block_sum<NT>(w, s.red);
+        sk = block_sum<NT>(sk, s.red);
         if (tid == 0) {
             const double h = (double)P.h;
             Ctl* ctl = a.ctl;
@@ -637,6 +702,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             ctl->src_vol = sr * h * h;
             ctl->clip_vol = cl * h * h;
             ctl->wet = (long long)w;
+            ctl->skipped = (long long)sk;
             ctl->tau_last = (double)tauT;
             ctl->t = ctl->t + (double)tauT;
             ctl->max_speed = __longlong_as_double((long long)atomicAdd(&ctl->smax[buf ^ 1], 0ull));
@@ -646,7 +712,6 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             __threadfence();
         }
     }
-    cbase += (unsigned)nrows;
     __syncthreads();
     return true;
 }
@@ -969,7 +1034,7 @@ __global__ void ks_final(const StagedArgs<T> a) {
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         a.parts[bl].mass = m;
         a.parts[bl].clip = c;
-        a.parts[bl].wet = (long long)w;
+        a.parts[bl].wet = (int)w;
     }
 }
 
@@ -1003,6 +1068,9 @@ __global__ void ks_speed(const StagedArgs<T> a, int which) {
         mass = (double)C.hs;
         if (C.wet) {
             wet = 1.0;
+            if (a.act)
+                a.act[(size_t)(j >> ACT_LY) * a.act_nbx + (i >> ACT_LX)] =
+                    *(volatile const long long*)&a.ctl->step + which;
             T ax, ay, phi;
             forces(a.P, C.hs, C.b, a.g.n[k], C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)), nb(at(i, j - 1)),
                    nb(at(i, j + 1)), ax, ay, phi);
@@ -1034,7 +1102,7 @@ __global__ void ks_speed(const StagedArgs<T> a, int which) {
         if (anybad) atomicOr(&a.ctl->err, (unsigned)ERR_NONFINITE);
         if (which == 0) {
             a.parts[bl].mass = bs;
-            a.parts[bl].wet = (long long)bw;
+            a.parts[bl].wet = (int)bw;
         }
     }
 }
@@ -1043,6 +1111,9 @@ __global__ void ks_speed(const StagedArgs<T> a, int which) {
 // block; with init != 0 only report the mass of the current state.
 template <class T>
 __global__ void ks_finish(const StagedArgs<T> a, int nblocks, int init) {
+    // a state set from the host: no work item has a skip history
+    if (init && a.hist)
+        for (int i = threadIdx.x; i < a.nhist; i += 256) a.hist[i] = 0;
     __shared__ double red[8];
     double m = 0.0, sr = 0.0, cl = 0.0, w = 0.0;
     for (int i = threadIdx.x; i < nblocks; i += 256) {
@@ -1062,6 +1133,7 @@ __global__ void ks_finish(const StagedArgs<T> a, int nblocks, int init) {
         const double h = (double)a.P.h;
         ctl->mass = m * h * h;
         ctl->wet = (long long)w;
+        ctl->skipped = 0;
         if (!init) {
             const int buf = (int)(ctl->step & 1);
             const T tauT = (T)step_tau(ctl, a.sp, buf);

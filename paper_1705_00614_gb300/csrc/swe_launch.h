@@ -22,7 +22,7 @@ constexpr int WIN = 128;
 constexpr int HALO = 6;
 constexpr int TW = WIN - 2 * HALO;
 constexpr int RB = 1;      // rows per TMA chunk
-constexpr int NSLOT = 4;   // chunk slots in shared memory
+constexpr int ACT_LX = 5, ACT_LY = 4;  // wet-block stamps: 32 x 16 cells
 constexpr int MAX_HYDRO = 32;
 
 enum ErrBits : unsigned int {
@@ -38,6 +38,7 @@ struct Ctl {
     double mass, src_vol, clip_vol, max_speed;  // report of the last completed step
     long long wet;
     long long step;    // steps since the state was set
+    long long skipped; // work items of the last step skipped as dry
     unsigned long long smax[2];  // max signal speed (FP64 bits) for the step of that parity
     unsigned int done;           // CTAs finished in the running step
     unsigned int err;            // ErrBits
@@ -46,7 +47,8 @@ struct Ctl {
 // Per-CTA partial sums of one step (reduced in a fixed order).
 struct Part {
     double mass, src, clip;
-    long long wet;
+    int wet;      // wet cells (at most 116 x 32768 per work item)
+    int skipped;  // 1 if the item was skipped as dry
 };
 
 // One source cell as seen by one work item (window coordinates).
@@ -77,6 +79,14 @@ template <class T>
 struct FusedArgs {
     CUtensorMap tmH[2], tmQx[2], tmQy[2], tmB, tmN;
     CUtensorMap tmA[2][3];
+    // wet-block stamps (skip_dry) or null: per 32 x 16-cell block of the
+    // interior grid, the last step at which the block held a wet cell
+    long long* act;
+    int act_nbx;
+    int skip;  // nonzero: items whose window is dry and sourceless may skip
+    // per item, bit 0: skipped in the last step, bit 1: in the one before
+    // (both: the output buffer already holds what a skip would write)
+    unsigned char* hist;
     Grid<T> g;
     Phys<T> P;
     StepP sp;
@@ -130,6 +140,10 @@ struct StagedArgs {
     int nsrc;
     const double* hydro;
     int nh;
+    long long* act;  // wet-block stamps to write for the state, or null
+    int act_nbx;
+    unsigned char* hist;  // per-item skip history to clear, or null
+    int nhist;
 };
 
 template <class T>

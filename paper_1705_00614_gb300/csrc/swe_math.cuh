@@ -54,6 +54,11 @@ __device__ __forceinline__ float pow43(float x) { return exp2f(1.33333333f * log
 template <class T>
 __device__ __forceinline__ bool is_wet(T H, T b, T eps) { return H > eps && b < T(WALL_TEST); }
 
+__device__ __forceinline__ bool is_neg_zero(float x) { return __float_as_uint(x) == 0x80000000u; }
+__device__ __forceinline__ bool is_neg_zero(double x) {
+    return (unsigned long long)__double_as_longlong(x) == 0x8000000000000000ull;
+}
+
 // Hydrostatic reconstruction at the face between L and R (Audusse et al.):
 // b* = max(b_L, b_R), h_{L,R} = max(0, eta_{L,R} - b*); returns h_R^2 - h_L^2.
 // eta - b* is evaluated as H + (b - b*): the bed difference is exact or

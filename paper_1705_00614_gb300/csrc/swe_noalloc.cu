@@ -216,7 +216,7 @@ extern "C" SWE_API int swe_step_f32_noalloc(const swe_params* p, const float* H,
         info->wet_cells = h.wet;
         info->step = h.step;
         info->err_word = (int32_t)h.err;
-        info->pad = 0;
+        info->skipped = 0;
         if (h.err & ERR_TIMEOUT) return nfail(SWE_ERR_DEVICE_TIMEOUT, "a bounded device wait ran out");
         if (h.err & ERR_NONFINITE) return nfail(SWE_ERR_NONFINITE, "non-finite signal speed");
         if (h.step != 1) return nfail(SWE_ERR_DT, "time step not positive");

@@ -48,17 +48,18 @@ class Params(ctypes.Structure):
                 ("dt_fixed", ctypes.c_double), ("nu", ctypes.c_double), ("coriolis_f", ctypes.c_double),
                 ("wind_x", ctypes.c_double), ("wind_y", ctypes.c_double), ("c_a", ctypes.c_double),
                 ("rho_air_over_rho", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("tile_w", ctypes.c_int32), ("seg_h", ctypes.c_int32)]
+                ("tile_w", ctypes.c_int32), ("seg_h", ctypes.c_int32),
+                ("skip_dry", ctypes.c_int32)]
 
 
 class StepInfo(ctypes.Structure):
     _fields_ = [("t", ctypes.c_double), ("dt_last", ctypes.c_double), ("mass", ctypes.c_double),
                 ("src_vol", ctypes.c_double), ("clip_vol", ctypes.c_double), ("max_speed", ctypes.c_double),
                 ("wet_cells", ctypes.c_int64), ("step", ctypes.c_int64), ("err_word", ctypes.c_int32),
-                ("pad", ctypes.c_int32)]
+                ("skipped", ctypes.c_int32)]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -165,7 +166,7 @@ def _ptr(a):
     return a.ctypes.data_as(_dp) if a is not None else None
 
 
-def make_params(params, precision="f32", mode="fused", stream=None, seg_h=0):
+def make_params(params, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False):
     """swe_params from an inputs.Params-like object."""
     L = load()
     p = Params()
@@ -178,6 +179,7 @@ def make_params(params, precision="f32", mode="fused", stream=None, seg_h=0):
     p.mode = SWE_STAGED if mode == "staged" else SWE_FUSED
     p.cuda_stream = stream
     p.seg_h = seg_h
+    p.skip_dry = 1 if skip_dry else 0
     return p
 
 
@@ -195,9 +197,9 @@ def step_f32_noalloc(params, H, Qx, Qy, b, n, H_out, Qx_out, Qy_out, pitch, t, m
 class Solver:
     """One grid: a libswe context.  Arrays are [ny, nx] float64 on the host."""
 
-    def __init__(self, params, precision="f32", mode="fused", stream=None, seg_h=0):
+    def __init__(self, params, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False):
         self.L = load()
-        p = make_params(params, precision, mode, stream, seg_h)
+        p = make_params(params, precision, mode, stream, seg_h, skip_dry)
         self.params = params
         self.nx, self.ny = params.nx, params.ny
         h = ctypes.c_void_p()
@@ -205,8 +207,8 @@ class Solver:
         self.h = h
 
     @classmethod
-    def from_problem(cls, prob, precision="f32", mode="fused", stream=None, seg_h=0):
-        s = cls(prob.params, precision, mode, stream, seg_h)
+    def from_problem(cls, prob, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False):
+        s = cls(prob.params, precision, mode, stream, seg_h, skip_dry)
         s.set_terrain(prob.b, prob.n_manning)
         if len(prob.sources):
             s.set_sources(prob.sources)

@@ -48,8 +48,9 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "{HDR}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(swe_params), offsetof(swe_params, dx),
-         offsetof(swe_params, cuda_stream), offsetof(swe_params, seg_h), sizeof(swe_step_info),
+  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(swe_params), offsetof(swe_params, dx),
+         offsetof(swe_params, cuda_stream), offsetof(swe_params, seg_h), offsetof(swe_params, skip_dry),
+         sizeof(swe_step_info),
          offsetof(swe_step_info, wet_cells));
   return 0;
 }}
@@ -58,7 +59,8 @@ int main(void) {{
     subprocess.check_call(["gcc", "-o", str(exe), str(src)])
     vals = list(map(int, subprocess.check_output([str(exe)]).split()))
     assert vals == [ctypes.sizeof(swe.Params), swe.Params.dx.offset, swe.Params.cuda_stream.offset,
-                    swe.Params.seg_h.offset, ctypes.sizeof(swe.StepInfo), swe.StepInfo.wet_cells.offset]
+                    swe.Params.seg_h.offset, swe.Params.skip_dry.offset, ctypes.sizeof(swe.StepInfo),
+                    swe.StepInfo.wet_cells.offset]
 
 
 def test_status_strings_and_defaults(lib):
@@ -74,7 +76,9 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     lib.swe_params_default(ctypes.byref(p))
     h = ctypes.c_void_p()
     for bad in ({"nx": 0, "ny": 4, "dx": 1.0}, {"nx": 4, "ny": 4, "dx": -1.0},
-                {"nx": 4, "ny": 4, "dx": 1.0, "cfl": 1.5}, {"nx": 4, "ny": 4, "dx": 1.0, "precision": 7}):
+                {"nx": 4, "ny": 4, "dx": 1.0, "cfl": 1.5}, {"nx": 4, "ny": 4, "dx": 1.0, "precision": 7},
+                {"nx": 4, "ny": 4, "dx": 1.0, "skip_dry": 2},
+                {"nx": 4, "ny": 4, "dx": 1.0, "skip_dry": 1, "mode": swe.SWE_STAGED}):
         q = swe.Params()
         lib.swe_params_default(ctypes.byref(q))
         for k, v in bad.items():
