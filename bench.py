@@ -133,6 +133,66 @@ def run_ensemble(args, torch, swe, stream, rank, world):
         print(json.dumps(line), flush=True)
 
 
+# algorithmic FLOPs per pixel of the closure network (3x3 convolutions
+# 5 -> 32 -> 32 -> 32 -> 3): forward, weight gradients, and data gradients
+# of layers 1-3 (the input's gradient is not needed)
+_CNN_CH = (5, 32, 32, 32, 3)
+CNN_FWD_FLOP = sum(2 * 9 * a * b for a, b in zip(_CNN_CH[:-1], _CNN_CH[1:]))
+CNN_TRAIN_FLOP = 3 * CNN_FWD_FLOP - 2 * 9 * _CNN_CH[0] * _CNN_CH[1]
+
+
+def run_cnn(args, torch, swe, stream, rank, world):
+    """Closure network on one coarse grid (cnn-<n>sq: n x n pixels): K
+    training steps (forward, backward, Adam) timed with CUDA events."""
+    from paper_1705_00614_gb300 import closure
+    n = int(args.workload.split("-")[1].replace("sq", ""))
+    g = torch.Generator(device="cuda").manual_seed(1234)
+    x = torch.zeros((1, n, n, 16), dtype=torch.bfloat16, device="cuda")
+    x[..., :5] = torch.randn((1, n, n, 5), generator=g, device="cuda").to(torch.bfloat16)
+    t = torch.randn((1, n, n, 3), generator=g, device="cuda")
+    net = swe.CNN(1, n, n, stream=stream.cuda_stream)
+    net.set_params(swe.flatten_cnn_params(closure.he_init(7)))
+    for _ in range(args.warmup):
+        net.train_step(x.data_ptr(), t.data_ptr(), 1e-4, report=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e2 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            net.train_step(x.data_ptr(), t.data_ptr(), 1e-4, report=False)
+        e1.record(stream)
+        for _ in range(args.steps):
+            net.forward(x.data_ptr())
+        e2.record(stream)
+        torch.cuda.synchronize()
+    ms_train = e0.elapsed_time(e1) / args.steps
+    ms_fwd = e1.elapsed_time(e2) / args.steps
+    net.close()
+    px = n * n
+    tflops = CNN_TRAIN_FLOP * px / (ms_train * 1e-3) / 1e12
+    fwd_tflops = CNN_FWD_FLOP * px / (ms_fwd * 1e-3) / 1e12
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, src = (json.load(open(peaks_path))["bf16_tflops"], "measured") if os.path.exists(peaks_path) \
+        else (1900.0, "fallback")
+    if rank == 0:
+        line = {"metric": "closure CNN training throughput", "value": world * px / (ms_train * 1e-3) / 1e9,
+                "unit": "Gpixel-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": ms_train, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "bf16", "data": "synthetic",
+                "config": {"workload": args.workload, "pixels": px, "channels": list(_CNN_CH),
+                           "train_flop_per_pixel": CNN_TRAIN_FLOP, "fwd_flop_per_pixel": CNN_FWD_FLOP,
+                           "forward_ms": ms_fwd, "forward_tflops": fwd_tflops,
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
+                             "frac": tflops / peak, "peak_source": src, "traffic": None,
+                             "kernel": "k_conv / k_wgrad (mma.sync BF16)"},
+                "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def crop(prob, y0, x0, n):
     s = prob.sources
     keep = (s.ix >= x0) & (s.ix < x0 + n) & (s.iy >= y0) & (s.iy < y0 + n)
@@ -302,6 +362,14 @@ def main():
     from paper_1705_00614_gb300 import build as B
     from paper_1705_00614_gb300 import swe
     B.build()
+
+    if args.workload.startswith("cnn-"):
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        run_cnn(args, torch, swe, stream, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     if args.workload.startswith("ensemble-"):
         stream = torch.cuda.Stream()
