@@ -151,96 +151,124 @@ __global__ void __launch_bounds__(32 * TY) k_conv(const __nv_bfloat16* __restric
     }
 }
 
-// Weight gradient partials of one CTA tile:
-// P[blk][tap][c][o] = sum_{pixels of the tile} x[p + off(tap)][c] * g[p][o].
-// GEMM per tap: M = c (16-row blocks), N = o (8-column blocks), K = pixels.
+// Weight gradient partials of one persistent CTA: the CTA takes the tiles
+// blockIdx.x, blockIdx.x + gridDim.x, ... (a fixed set, in a fixed order) and
+// accumulates, in registers, P[cta][tap][c][o] = sum over their pixels p of
+// x[p + off(tap)][c] * g[p][o]; per tap a GEMM with M = c (16-row blocks),
+// N = o (8-column blocks), K = pixels.  Each warp owns up to UPW (tap,
+// c-block) units for the whole launch.
 template <int CI, int CO>
 __global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ g,
-                                                   float* __restrict__ part, float* __restrict__ bpart, int H, int W) {
+                                                   float* __restrict__ part, float* __restrict__ bpart, int H, int W,
+                                                   int ntiles) {
     constexpr int PS = CI + 8, GS = CO + 8;
+    constexpr int UNITS = 9 * (CI / 16);
+    constexpr int UPW = (UNITS + TY - 1) / TY;
     __shared__ __align__(16) __nv_bfloat16 sx[(TY + 2) * (TX + 2) * PS];
     __shared__ __align__(16) __nv_bfloat16 sg[TY * TX * GS];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = blockIdx.z, i0 = blockIdx.y * TY, j0 = blockIdx.x * TX;
-    const int blk = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    for (int e = tid; e < (TY + 2) * (TX + 2) * (CI / 8); e += blockDim.x) {
-        const int p = e / (CI / 8), c8 = e % (CI / 8);
-        const int ti = p / (TX + 2), tj = p % (TX + 2);
-        const int gi = i0 + ti - 1, gj = j0 + tj - 1;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (gi >= 0 && gi < H && gj >= 0 && gj < W)
-            v = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * c8]);
-        *reinterpret_cast<uint4*>(&sx[p * PS + 8 * c8]) = v;
-    }
-    for (int e = tid; e < TY * TX * (CO / 8); e += blockDim.x) {
-        const int p = e / (CO / 8), c8 = e % (CO / 8);
-        const int ti = p / TX, tj = p % TX;
-        const uint4 v = *reinterpret_cast<const uint4*>(&g[(((size_t)n * H + i0 + ti) * W + j0 + tj) * CO + 8 * c8]);
-        *reinterpret_cast<uint4*>(&sg[p * GS + 8 * c8]) = v;
-    }
-    __syncthreads();
+    const int gx = W / TX, gy = H / TY;
     const int r0 = lane >> 2, kc = (lane & 3) * 2;
-    // work units: (tap, c-block); each warp takes every 8th unit, all o-blocks
-    constexpr int UNITS = 9 * (CI / 16);
-    for (int u = warp; u < UNITS; u += TY) {
-        const int tap = u / (CI / 16), cb = (u % (CI / 16)) * 16;
-        const int ky = tap / 3, kx = tap % 3;
-        float acc[CO / 8][4];
+    float acc[UPW][CO / 8][4];
 #pragma unroll
-        for (int f = 0; f < CO / 8; ++f) acc[f][0] = acc[f][1] = acc[f][2] = acc[f][3] = 0.f;
-        // K = 128 pixels of the tile, 16 per MMA (one tile row)
-        for (int ti = 0; ti < TY; ++ti) {
-            const __nv_bfloat16* xr = &sx[((ti + ky) * (TX + 2) + kx) * PS];
-            const __nv_bfloat16* gr = &sg[(ti * TX) * GS];
-            // A[m = c][k = p] = x[p][c]: pairs of consecutive pixels
-            const uint32_t a0 = pack2(xr[kc * PS + cb + r0], xr[(kc + 1) * PS + cb + r0]);
-            const uint32_t a1 = pack2(xr[kc * PS + cb + r0 + 8], xr[(kc + 1) * PS + cb + r0 + 8]);
-            const uint32_t a2 = pack2(xr[(kc + 8) * PS + cb + r0], xr[(kc + 9) * PS + cb + r0]);
-            const uint32_t a3 = pack2(xr[(kc + 8) * PS + cb + r0 + 8], xr[(kc + 9) * PS + cb + r0 + 8]);
+    for (int q = 0; q < UPW; ++q)
 #pragma unroll
-            for (int f = 0; f < CO / 8; ++f) {
-                // B[k = p][n = o] = g[p][o]
-                const int o = 8 * f + r0;
-                const uint32_t b0 = pack2(gr[kc * GS + o], gr[(kc + 1) * GS + o]);
-                const uint32_t b1 = pack2(gr[(kc + 8) * GS + o], gr[(kc + 9) * GS + o]);
-                mma_bf16(acc[f], a0, a1, a2, a3, b0, b1);
+        for (int f = 0; f < CO / 8; ++f) acc[q][f][0] = acc[q][f][1] = acc[q][f][2] = acc[q][f][3] = 0.f;
+    float bsum = 0.f;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int n = t / (gx * gy), i0 = ((t / gx) % gy) * TY, j0 = (t % gx) * TX;
+        __syncthreads();  // the previous tile's shared data is no longer read
+        for (int e = tid; e < (TY + 2) * (TX + 2) * (CI / 8); e += blockDim.x) {
+            const int p = e / (CI / 8), c8 = e % (CI / 8);
+            const int ti = p / (TX + 2), tj = p % (TX + 2);
+            const int gi = i0 + ti - 1, gj = j0 + tj - 1;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (gi >= 0 && gi < H && gj >= 0 && gj < W)
+                v = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * c8]);
+            *reinterpret_cast<uint4*>(&sx[p * PS + 8 * c8]) = v;
+        }
+        for (int e = tid; e < TY * TX * (CO / 8); e += blockDim.x) {
+            const int p = e / (CO / 8), c8 = e % (CO / 8);
+            const int ti = p / TX, tj = p % TX;
+            const uint4 v = *reinterpret_cast<const uint4*>(&g[(((size_t)n * H + i0 + ti) * W + j0 + tj) * CO + 8 * c8]);
+            *reinterpret_cast<uint4*>(&sg[p * GS + 8 * c8]) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < UPW; ++q) {
+            const int u = warp + q * TY;
+            if (u >= UNITS) continue;
+            const int tap = u / (CI / 16), cb = (u % (CI / 16)) * 16;
+            const int ky = tap / 3, kx = tap % 3;
+            // K = 128 pixels of the tile, 16 per MMA (one tile row)
+            for (int ti = 0; ti < TY; ++ti) {
+                const __nv_bfloat16* xr = &sx[((ti + ky) * (TX + 2) + kx) * PS];
+                const __nv_bfloat16* gr = &sg[(ti * TX) * GS];
+                // A[m = c][k = p] = x[p][c]: pairs of consecutive pixels
+                const uint32_t a0 = pack2(xr[kc * PS + cb + r0], xr[(kc + 1) * PS + cb + r0]);
+                const uint32_t a1 = pack2(xr[kc * PS + cb + r0 + 8], xr[(kc + 1) * PS + cb + r0 + 8]);
+                const uint32_t a2 = pack2(xr[(kc + 8) * PS + cb + r0], xr[(kc + 9) * PS + cb + r0]);
+                const uint32_t a3 = pack2(xr[(kc + 8) * PS + cb + r0 + 8], xr[(kc + 9) * PS + cb + r0 + 8]);
+#pragma unroll
+                for (int f = 0; f < CO / 8; ++f) {
+                    // B[k = p][n = o] = g[p][o]
+                    const int o = 8 * f + r0;
+                    const uint32_t b0 = pack2(gr[kc * GS + o], gr[(kc + 1) * GS + o]);
+                    const uint32_t b1 = pack2(gr[(kc + 8) * GS + o], gr[(kc + 9) * GS + o]);
+                    mma_bf16(acc[q][f], a0, a1, a2, a3, b0, b1);
+                }
             }
         }
-        float* P = part + (size_t)blk * 9 * CI * CO + (size_t)tap * CI * CO;
+        // bias gradient: sum of g over the tile, pixels in order
+        if (tid < CO)
+            for (int p = 0; p < TY * TX; ++p) bsum += __bfloat162float(sg[p * GS + tid]);
+    }
+#pragma unroll
+    for (int q = 0; q < UPW; ++q) {
+        const int u = warp + q * TY;
+        if (u >= UNITS) continue;
+        const int tap = u / (CI / 16), cb = (u % (CI / 16)) * 16;
+        float* P = part + (size_t)blockIdx.x * 9 * CI * CO + (size_t)tap * CI * CO;
 #pragma unroll
         for (int f = 0; f < CO / 8; ++f) {
             const int o = 8 * f + kc;
-            P[(cb + r0) * CO + o] = acc[f][0];
-            P[(cb + r0) * CO + o + 1] = acc[f][1];
-            P[(cb + r0 + 8) * CO + o] = acc[f][2];
-            P[(cb + r0 + 8) * CO + o + 1] = acc[f][3];
+            P[(cb + r0) * CO + o] = acc[q][f][0];
+            P[(cb + r0) * CO + o + 1] = acc[q][f][1];
+            P[(cb + r0 + 8) * CO + o] = acc[q][f][2];
+            P[(cb + r0 + 8) * CO + o + 1] = acc[q][f][3];
         }
     }
-    // bias gradient partial: sum of g over the tile
-    for (int o = tid; o < CO; o += blockDim.x) {
-        float sacc = 0.f;
-        for (int p = 0; p < TY * TX; ++p) sacc += __bfloat162float(sg[p * GS + o]);
-        bpart[(size_t)blk * CO + o] = sacc;
-    }
+    if (tid < CO) bpart[(size_t)blockIdx.x * CO + tid] = bsum;
 }
 
 // Fixed-order sum of the per-CTA partials -> FP32 gradients in the master
-// layout [3][3][ci][co] (real channels) and [co].
-__global__ void k_wgrad_reduce(const float* __restrict__ part, const float* __restrict__ bpart, int nblk, int CIp, int COp,
-                               int ci, int co, float* __restrict__ gw, float* __restrict__ gb) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+// layout [3][3][ci][co] (real channels) and [co].  One CTA per 32 outputs
+// (lane = output): warp k sums the partials k, k + 8, k + 16, ... in order,
+// then the 8 warp sums are added in warp order.
+__global__ void __launch_bounds__(256) k_wgrad_reduce(const float* __restrict__ part, const float* __restrict__ bpart,
+                                                      int nblk, int CIp, int COp, int ci, int co,
+                                                      float* __restrict__ gw, float* __restrict__ gb) {
+    __shared__ float red[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + lane;
     const int nw = 9 * ci * co;
+    float s = 0.f;
     if (e < nw) {
         const int tap = e / (ci * co), c = (e / co) % ci, o = e % co;
         const size_t off = (size_t)tap * CIp * COp + (size_t)c * COp + o;
-        float s = 0.f;
-        for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 9 * CIp * COp + off];
-        gw[e] = s;
+        for (int b = warp; b < nblk; b += 8) s += part[(size_t)b * 9 * CIp * COp + off];
     } else if (e < nw + co) {
         const int o = e - nw;
-        float s = 0.f;
-        for (int b = 0; b < nblk; ++b) s += bpart[(size_t)b * COp + o];
-        gb[o] = s;
+        for (int b = warp; b < nblk; b += 8) s += bpart[(size_t)b * COp + o];
+    }
+    red[warp][lane] = s;
+    __syncthreads();
+    if (warp == 0) {
+        float t = 0.f;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t += red[k][lane];
+        if (e < nw) gw[e] = t;
+        else if (e < nw + co) gb[e - nw] = t;
     }
 }
 
@@ -292,10 +320,19 @@ __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, 
     }
 }
 
+// Fixed-order sum of n values by one CTA of 256 threads (strided partial
+// sums, then a fixed tree).
 __global__ void k_sum(const double* __restrict__ part, int n, double* __restrict__ out) {
+    __shared__ double red[256];
     double s = 0.0;
-    for (int i = 0; i < n; ++i) s += part[i];
-    *out = s;
+    for (int i = threadIdx.x; i < n; i += 256) s += part[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0];
 }
 
 // Adam (Kingma & Ba 2015) on all parameters, FP32.
@@ -495,7 +532,8 @@ struct swe_cnn {
     __nv_bfloat16* act[NLAYER] = {};  // act[0] unused (input given); act[l] = output of layer l-1 (BF16)
     float* yout = nullptr;            // last layer output FP32 [n][h][w][3]
     __nv_bfloat16* gbuf[2] = {};      // gradient ping-pong, BF16 [n][h][w][32]
-    float* part = nullptr;            // weight-gradient partials
+    int nwg = 0;                      // persistent weight-gradient CTAs
+    float* part = nullptr;            // weight-gradient partials, one set per such CTA
     float* bpart = nullptr;
     double* lpart = nullptr;
     double* dloss = nullptr;
@@ -546,21 +584,22 @@ int backward_all(swe_cnn* c, const __nv_bfloat16* x, const float* target) {
     const int nb = (int)((npix + 255) / 256);
     // gbuf[0] holds the 16-channel gradient of the last layer's output
     k_mse<<<nb, 256, 0, c->st>>>(c->yout, target, c->gbuf[0], c->lpart, npix, 3, 1.0f / (float)(npix * 3));
-    k_sum<<<1, 1, 0, c->st>>>(c->lpart, nb, c->dloss);
+    k_sum<<<1, 256, 0, c->st>>>(c->lpart, nb, c->dloss);
     const dim3 grid(c->w / TX, c->h / TY, c->n), blk(32 * TY);
-    const int nblk = (int)(grid.x * grid.y * grid.z);
+    const int ntiles = (int)(grid.x * grid.y * grid.z);
+    const int nblk = c->nwg;
     const __nv_bfloat16* ins[NLAYER] = {x, c->act[1], c->act[2], c->act[3]};
     int cur = 0;
     for (int l = NLAYER - 1; l >= 0; --l) {
         const __nv_bfloat16* gl = c->gbuf[cur];
         // weight gradient of layer l: inputs ins[l] (CIP), output gradient gl
         switch (l) {
-            case 0: k_wgrad<16, 32><<<grid, blk, 0, c->st>>>(ins[0], gl, c->part, c->bpart, c->h, c->w); break;
-            case 3: k_wgrad<32, 16><<<grid, blk, 0, c->st>>>(ins[3], gl, c->part, c->bpart, c->h, c->w); break;
-            default: k_wgrad<32, 32><<<grid, blk, 0, c->st>>>(ins[l], gl, c->part, c->bpart, c->h, c->w); break;
+            case 0: k_wgrad<16, 32><<<nblk, blk, 0, c->st>>>(ins[0], gl, c->part, c->bpart, c->h, c->w, ntiles); break;
+            case 3: k_wgrad<32, 16><<<nblk, blk, 0, c->st>>>(ins[3], gl, c->part, c->bpart, c->h, c->w, ntiles); break;
+            default: k_wgrad<32, 32><<<nblk, blk, 0, c->st>>>(ins[l], gl, c->part, c->bpart, c->h, c->w, ntiles); break;
         }
         const int nw = 9 * CH[l] * CH[l + 1] + CH[l + 1];
-        k_wgrad_reduce<<<(nw + 255) / 256, 256, 0, c->st>>>(c->part, c->bpart, nblk, CIP[l], cog(l), CH[l], CH[l + 1],
+        k_wgrad_reduce<<<(nw + 31) / 32, 256, 0, c->st>>>(c->part, c->bpart, nblk, CIP[l], cog(l), CH[l], CH[l + 1],
                                                            c->g + c->off_w[l], c->g + c->off_b[l]);
         if (l > 0) {
             // data gradient into layer l's input, masked by that input's ReLU
@@ -624,7 +663,14 @@ SWE_API int swe_cnn_create(int32_t n, int32_t h, int32_t w, void* stream, swe_cn
     c->nparam = np;
     const size_t npix = (size_t)n * h * w;
     const dim3 grid(w / TX, h / TY, n);
-    const size_t nblk = (size_t)grid.x * grid.y * grid.z;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        swe_cnn_destroy(c);
+        return cfail(SWE_ERR_CUDA, "device attributes");
+    }
+    c->nwg = (int)std::min<size_t>((size_t)grid.x * grid.y * grid.z, (size_t)4 * nsm);
+    const size_t nblk = (size_t)c->nwg;
     bool ok = cudaMalloc(&c->p, np * sizeof(float)) == cudaSuccess && cudaMalloc(&c->g, np * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&c->m, np * sizeof(float)) == cudaSuccess && cudaMalloc(&c->v, np * sizeof(float)) == cudaSuccess;
     for (int l = 0; l < NLAYER && ok; ++l) {
