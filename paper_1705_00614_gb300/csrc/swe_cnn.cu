@@ -4,12 +4,13 @@
 // coarse state (H, Ux, Uy, b, n_M) to corrections of the coarse cells' net
 // face-flux sums (the Fh, Fv that the final update K8 applies).
 //
-// Tensor-core kernels: BF16 operands, FP32 accumulation, mma.sync m16n8k16,
-// NHWC activations.  Forward and data-gradient convolutions are implicit
-// GEMMs over (pixel) x (tap, input channel); the weight gradient is an
-// implicit GEMM over (input channel) x (pixel) per tap, reduced over CTAs
-// in a fixed order.  Channel counts are padded: inputs to multiples of 16
-// (the MMA K step), outputs to multiples of 8 (the MMA N step).
+// Tensor-core kernels: BF16 operands, FP32 accumulation, NHWC activations.
+// Forward and data-gradient convolutions are implicit GEMMs over (pixel) x
+// (tap, input channel) on the fifth-generation tensor cores (tcgen05.mma,
+// accumulator in tensor memory); the weight gradient is an implicit GEMM
+// over (input channel) x (pixel) per tap (mma.sync m16n8k16), reduced over
+// CTAs in a fixed order.  Channel counts are padded: inputs to multiples of
+// 16 (the MMA K step), outputs to 16 or 32 (the MMA N).
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -19,7 +20,9 @@
 #include <vector>
 
 #include "../../include/swe.h"
+#include "swe_conv_tc.cuh"
 #include "swe_launch.h"
+#include "swe_ptx.cuh"
 
 using namespace swe;
 
@@ -41,9 +44,7 @@ constexpr int TY = 8, TX = 16;   // pixels per CTA tile (one warp per row)
 constexpr int NLAYER = 4;
 constexpr int CH[NLAYER + 1] = {5, 32, 32, 32, 3};
 constexpr int CIP[NLAYER] = {16, 32, 32, 32};  // padded input channels
-constexpr int COP[NLAYER] = {32, 32, 32, 8};   // padded output channels
-
-__device__ __forceinline__ uint32_t ld_u32(const __nv_bfloat16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+constexpr int COP[NLAYER] = {32, 32, 32, 16};  // padded output channels
 
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
@@ -66,88 +67,138 @@ enum ConvMode {
 };
 
 // y[n, i, j, o] = sum_{tap, c} x[n, i+dy-1, j+dx-1, c] * W[tap][o][c] (+ bias)
-// x: BF16 [N][H][W][CI]; W: BF16 [9][CO][CI]; H % TY == 0, W % TX == 0.
+// x: BF16 [N][H][W][CI]; W: BF16 [9][CO][CI]; any H, W.
+//
+// Fifth-generation tensor cores: a persistent CTA of 4 warps keeps all nine
+// taps' weights in shared memory and, per tile of 128 pixels of one row,
+// stages the three input rows it needs (130 pixels each, zero outside the
+// image) in the no-swizzle K-major layout of swe_conv_tc.cuh; one thread
+// issues 9 * CI / 16 MMAs (M = 128 pixels, N = CO, K = 16 channels, tap
+// (dy, dx) = the staged rows started dx pixels later) accumulating in
+// tensor memory, commits them to an mbarrier, and each warp reads its 32
+// pixels' accumulators back (tcgen05.ld) for the epilogue.  Waits are
+// bounded; a timeout sets *err and the CTA frees its tensor memory and
+// stops.
 template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(32 * TY) k_conv(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w,
-                                                  const float* __restrict__ bias, void* __restrict__ out,
-                                                  const __nv_bfloat16* __restrict__ mask, int H, int W, int CO_STORE) {
-    constexpr int PS = CI + 8;  // padded pixel stride in shared memory (bank-conflict free fragments)
-    constexpr int WS = CI + 8;
-    __shared__ __align__(16) __nv_bfloat16 sx[(TY + 2) * (TX + 2) * PS];
-    __shared__ __align__(16) __nv_bfloat16 sw[9 * CO * WS];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int n = blockIdx.z, i0 = blockIdx.y * TY, j0 = blockIdx.x * TX;
-    // weights
-    for (int e = tid; e < 9 * CO * (CI / 2); e += blockDim.x) {
-        const int tc = e / (CI / 2), c2 = e % (CI / 2);
-        *reinterpret_cast<uint32_t*>(&sw[tc * WS + 2 * c2]) =
-            *reinterpret_cast<const uint32_t*>(&w[(size_t)tc * CI + 2 * c2]);
+__global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w,
+                                              const float* __restrict__ bias, void* __restrict__ out,
+                                              const __nv_bfloat16* __restrict__ mask, int H, int W, int CO_STORE,
+                                              int ntiles, unsigned* __restrict__ err) {
+    constexpr int NKC = CI / 8;
+    static_assert(CO == 16 || CO == 32, "MMA N");
+    // staged input rows, then the weights (dynamic shared memory of at least
+    // conv_smem_bytes<CI, CO>())
+    extern __shared__ __align__(128) unsigned char csm[];
+    unsigned char* const sA = csm;
+    unsigned char* const sW = csm + conv_a_bytes<CI>();
+    __shared__ __align__(8) unsigned long long bar;
+    __shared__ uint32_t s_taddr;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (warp == 0) {
+        tmem_alloc(&s_taddr, 32);
+        tmem_relinquish();
     }
-    // input tile with a one-pixel halo, zero outside the image
-    for (int e = tid; e < (TY + 2) * (TX + 2) * (CI / 8); e += blockDim.x) {
-        const int p = e / (CI / 8), c8 = e % (CI / 8);
-        const int ti = p / (TX + 2), tj = p % (TX + 2);
-        const int gi = i0 + ti - 1, gj = j0 + tj - 1;
-        uint4 v = make_uint4(0, 0, 0, 0);
-        if (gi >= 0 && gi < H && gj >= 0 && gj < W)
-            v = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * c8]);
-        *reinterpret_cast<uint4*>(&sx[p * PS + 8 * c8]) = v;
+    if (tid == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
     }
+    // weights: global [tap][o][c] -> shared [tap][kc][o][8]
+    for (int e = tid; e < 9 * CO * NKC; e += 128) {
+        const int tap = e / (CO * NKC), o = (e / NKC) % CO, kc = e % NKC;
+        *reinterpret_cast<uint4*>(&sW[conv_w_stage<CI, CO>(tap, kc, o)]) =
+            *reinterpret_cast<const uint4*>(&w[((size_t)tap * CO + o) * CI + 8 * kc]);
+    }
+    fence_proxy_async();
+    tc_fence_before();
     __syncthreads();
-    float acc[CO / 8][4];
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+    const uint32_t tw = taddr + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
+    const uint32_t aBase = smem_u32(sA), wBase = smem_u32(sW);
+    constexpr uint32_t IDESC = idesc_bf16_f32(TCM, CO);
+    const int tpr = (W + TCM - 1) / TCM;  // tiles per image row
+    unsigned phase = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int jt = t % tpr, i = (t / tpr) % H, n = t / (tpr * H);
+        const int j0 = jt * TCM;
+        // the previous tile's MMAs have completed, so its rows may be replaced
+        for (int e = tid; e < 3 * (TCM + 2) * NKC; e += 128) {
+            const int dy = e / ((TCM + 2) * NKC), p = (e / NKC) % (TCM + 2), kc = e % NKC;
+            const int gi = i + dy - 1, gj = j0 - 1 + p;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (gi >= 0 && gi < H && gj >= 0 && gj < W)
+                v = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * kc]);
+            *reinterpret_cast<uint4*>(&sA[conv_a_stage<CI>(dy, kc, p)]) = v;
+        }
+        fence_proxy_async();
+        __syncthreads();  // staged rows visible; the last tile's accumulator reads done
+        if (tid == 0) {
+            tc_fence_after();
 #pragma unroll
-    for (int f = 0; f < CO / 8; ++f) acc[f][0] = acc[f][1] = acc[f][2] = acc[f][3] = 0.f;
-    const int r0 = lane >> 2, kc = (lane & 3) * 2;
+            for (int tap = 0; tap < 9; ++tap) {
 #pragma unroll
-    for (int tap = 0; tap < 9; ++tap) {
-        const int ky = tap / 3, kx = tap % 3;
-        const __nv_bfloat16* rowp = &sx[((warp + ky) * (TX + 2) + kx) * PS];
-#pragma unroll
-        for (int q = 0; q < CI / 16; ++q) {
-            const int cb = 16 * q + kc;
-            const uint32_t a0 = ld_u32(rowp + r0 * PS + cb);
-            const uint32_t a1 = ld_u32(rowp + (r0 + 8) * PS + cb);
-            const uint32_t a2 = ld_u32(rowp + r0 * PS + cb + 8);
-            const uint32_t a3 = ld_u32(rowp + (r0 + 8) * PS + cb + 8);
-#pragma unroll
-            for (int f = 0; f < CO / 8; ++f) {
-                const __nv_bfloat16* wp = &sw[(tap * CO + 8 * f + r0) * WS + cb];
-                mma_bf16(acc[f], a0, a1, a2, a3, ld_u32(wp), ld_u32(wp + 8));
+                for (int s = 0; s < CI / 16; ++s) {
+                    const uint64_t ad = smem_desc(aBase + conv_a_off<CI>(tap / 3, tap % 3, s), TC_A_LBO, TC_SBO);
+                    const uint64_t bd = smem_desc(wBase + conv_b_off<CI, CO>(tap, s), conv_b_lbo<CO>(), TC_SBO);
+                    tc_mma_bf16(taddr, ad, bd, IDESC, (tap | s) != 0 ? 1u : 0u);
+                }
             }
+            tc_commit(&bar);
+        }
+        const bool ok = mbar_wait_bounded(&bar, phase);
+        phase ^= 1u;
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicOr(err, 1u);
+            break;
+        }
+        tc_fence_after();
+        float v[CO];
+        tmem_ld16(tw, v);
+        if constexpr (CO > 16) tmem_ld16(tw + 16, v + 16);
+        tmem_ld_wait();
+        tc_fence_before();
+        const int j = j0 + 32 * warp + lane;
+        if (j >= W) continue;
+        const size_t pix = ((size_t)n * H + i) * W + j;
+        if (MODE == MODE_LINEAR_F32) {
+            float* y = reinterpret_cast<float*>(out);
+            for (int o = 0; o < CO_STORE; ++o) y[pix * CO_STORE + o] = v[o] + bias[o];
+        } else {
+            uint32_t pk[CO / 2];
+            if (MODE == MODE_MASK_BF16) {
+                uint32_t mk[CO / 2];
+#pragma unroll
+                for (int q = 0; q < CO / 8; ++q) {
+                    const uint4 m4 = *reinterpret_cast<const uint4*>(&mask[pix * CO + 8 * q]);
+                    mk[4 * q] = m4.x;
+                    mk[4 * q + 1] = m4.y;
+                    mk[4 * q + 2] = m4.z;
+                    mk[4 * q + 3] = m4.w;
+                }
+#pragma unroll
+                for (int h = 0; h < CO / 2; ++h) {
+                    const float m0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk[h] & 0xFFFFu)));
+                    const float m1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk[h] >> 16)));
+                    pk[h] = pack2(__float2bfloat16(m0 > 0.f ? v[2 * h] : 0.f), __float2bfloat16(m1 > 0.f ? v[2 * h + 1] : 0.f));
+                }
+            } else {
+#pragma unroll
+                for (int h = 0; h < CO / 2; ++h)
+                    pk[h] = pack2(__float2bfloat16(fmaxf(v[2 * h] + bias[2 * h], 0.f)),
+                                  __float2bfloat16(fmaxf(v[2 * h + 1] + bias[2 * h + 1], 0.f)));
+            }
+            __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(out);
+#pragma unroll
+            for (int q = 0; q < CO / 8; ++q)
+                *reinterpret_cast<uint4*>(&y[pix * CO + 8 * q]) =
+                    make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
     }
-    // epilogue: rows r0 and r0 + 8 of the warp's 16 pixels, columns kc, kc+1
-    const int gi = i0 + warp;
-#pragma unroll
-    for (int half = 0; half < 2; ++half) {
-        const int gj = j0 + r0 + 8 * half;
-        const size_t pix = ((size_t)n * H + gi) * W + gj;
-#pragma unroll
-        for (int f = 0; f < CO / 8; ++f) {
-            const int o = 8 * f + kc;
-            float v0 = acc[f][2 * half], v1 = acc[f][2 * half + 1];
-            if (MODE != MODE_MASK_BF16) {
-                v0 += bias[o];
-                v1 += bias[o + 1];
-            }
-            if (MODE == MODE_RELU_BF16) {
-                v0 = fmaxf(v0, 0.f);
-                v1 = fmaxf(v1, 0.f);
-            }
-            if (MODE == MODE_MASK_BF16) {
-                const __nv_bfloat16* mp = &mask[pix * CO + o];
-                if (!(__bfloat162float(mp[0]) > 0.f)) v0 = 0.f;
-                if (!(__bfloat162float(mp[1]) > 0.f)) v1 = 0.f;
-            }
-            if (MODE == MODE_LINEAR_F32) {
-                float* y = reinterpret_cast<float*>(out);
-                if (o < CO_STORE) y[pix * CO_STORE + o] = v0;
-                if (o + 1 < CO_STORE) y[pix * CO_STORE + o + 1] = v1;
-            } else {
-                __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(out);
-                *reinterpret_cast<uint32_t*>(&y[pix * CO + o]) = pack2(__float2bfloat16(v0), __float2bfloat16(v1));
-            }
-        }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(taddr, 32);
     }
 }
 
@@ -537,19 +588,39 @@ struct swe_cnn {
     float* bpart = nullptr;
     double* lpart = nullptr;
     double* dloss = nullptr;
+    unsigned* derr = nullptr;         // device error word (bounded waits that gave up)
     int off_w[NLAYER], off_b[NLAYER];
 };
 
 namespace {
 
+// Synchronise the network's stream and report a device wait that gave up.
+int sync_check(swe_cnn* c) {
+    unsigned e = 0;
+    CKC(cudaMemcpyAsync(&e, c->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, c->st));
+    CKC(cudaStreamSynchronize(c->st));
+    if (e) return cfail(SWE_ERR_DEVICE_TIMEOUT, "a tensor-core wait timed out");
+    return SWE_OK;
+}
+
+template <int CI, int CO>
+constexpr size_t conv_smem_bytes() {
+    return (size_t)conv_a_bytes<CI>() + conv_w_bytes<CI, CO>();
+}
+
+// Tiles of the convolution kernel (128 pixels of one row) and its
+// persistent grid.
+int conv_tiles(const swe_cnn* c) { return c->n * c->h * ((c->w + TCM - 1) / TCM); }
+int conv_grid(const swe_cnn* c) { return std::min(conv_tiles(c), c->nwg); }
+
 int layer_fwd(swe_cnn* c, int l, const __nv_bfloat16* x, void* out) {
-    const dim3 grid(c->w / TX, c->h / TY, c->n), blk(32 * TY);
+    const int nt = conv_tiles(c), g = conv_grid(c);
     const float* bias = c->p + c->off_b[l];
     switch (l) {
-        case 0: k_conv<16, 32, MODE_RELU_BF16><<<grid, blk, 0, c->st>>>(x, c->wk[0], bias, out, nullptr, c->h, c->w, 32); break;
-        case 1: k_conv<32, 32, MODE_RELU_BF16><<<grid, blk, 0, c->st>>>(x, c->wk[1], bias, out, nullptr, c->h, c->w, 32); break;
-        case 2: k_conv<32, 32, MODE_RELU_BF16><<<grid, blk, 0, c->st>>>(x, c->wk[2], bias, out, nullptr, c->h, c->w, 32); break;
-        default: k_conv<32, 8, MODE_LINEAR_F32><<<grid, blk, 0, c->st>>>(x, c->wk[3], bias, out, nullptr, c->h, c->w, 3); break;
+        case 0: k_conv<16, 32, MODE_RELU_BF16><<<g, 128, conv_smem_bytes<16, 32>(), c->st>>>(x, c->wk[0], bias, out, nullptr, c->h, c->w, 32, nt, c->derr); break;
+        case 1: k_conv<32, 32, MODE_RELU_BF16><<<g, 128, conv_smem_bytes<32, 32>(), c->st>>>(x, c->wk[1], bias, out, nullptr, c->h, c->w, 32, nt, c->derr); break;
+        case 2: k_conv<32, 32, MODE_RELU_BF16><<<g, 128, conv_smem_bytes<32, 32>(), c->st>>>(x, c->wk[2], bias, out, nullptr, c->h, c->w, 32, nt, c->derr); break;
+        default: k_conv<32, 16, MODE_LINEAR_F32><<<g, 128, conv_smem_bytes<32, 16>(), c->st>>>(x, c->wk[3], bias, out, nullptr, c->h, c->w, 3, nt, c->derr); break;
     }
     CKC(cudaGetLastError());
     return SWE_OK;
@@ -605,9 +676,11 @@ int backward_all(swe_cnn* c, const __nv_bfloat16* x, const float* target) {
             // data gradient into layer l's input, masked by that input's ReLU
             __nv_bfloat16* go = c->gbuf[cur ^ 1];
             if (l == 3)
-                k_conv<16, 32, MODE_MASK_BF16><<<grid, blk, 0, c->st>>>(gl, c->wd[3], nullptr, go, c->act[3], c->h, c->w, 32);
+                k_conv<16, 32, MODE_MASK_BF16><<<conv_grid(c), 128, conv_smem_bytes<16, 32>(), c->st>>>(gl, c->wd[3], nullptr, go, c->act[3],
+                                                                                c->h, c->w, 32, conv_tiles(c), c->derr);
             else
-                k_conv<32, 32, MODE_MASK_BF16><<<grid, blk, 0, c->st>>>(gl, c->wd[l], nullptr, go, c->act[l], c->h, c->w, 32);
+                k_conv<32, 32, MODE_MASK_BF16><<<conv_grid(c), 128, conv_smem_bytes<32, 32>(), c->st>>>(gl, c->wd[l], nullptr, go, c->act[l],
+                                                                                c->h, c->w, 32, conv_tiles(c), c->derr);
             cur ^= 1;
         }
     }
@@ -684,12 +757,14 @@ SWE_API int swe_cnn_create(int32_t n, int32_t h, int32_t w, void* stream, swe_cn
          cudaMalloc(&c->part, nblk * 9 * 32 * 32 * sizeof(float)) == cudaSuccess &&
          cudaMalloc(&c->bpart, nblk * 32 * sizeof(float)) == cudaSuccess &&
          cudaMalloc(&c->lpart, ((npix + 255) / 256) * sizeof(double)) == cudaSuccess &&
-         cudaMalloc(&c->dloss, sizeof(double)) == cudaSuccess;
+         cudaMalloc(&c->dloss, sizeof(double)) == cudaSuccess &&
+         cudaMalloc(&c->derr, sizeof(unsigned)) == cudaSuccess;
     if (!ok) {
         swe_cnn_destroy(c);
         return cfail(SWE_ERR_OOM, "cnn buffers");
     }
     cudaMemsetAsync(c->p, 0, np * sizeof(float), c->st);
+    cudaMemsetAsync(c->derr, 0, sizeof(unsigned), c->st);
     cudaMemsetAsync(c->m, 0, np * sizeof(float), c->st);
     cudaMemsetAsync(c->v, 0, np * sizeof(float), c->st);
     *out = c;
@@ -706,14 +781,14 @@ SWE_API int swe_cnn_set_params(swe_cnn* c, const float* host) {
     c->adam_t = 0;
     int rc = pack_weights(c);
     if (rc) return rc;
-    CKC(cudaStreamSynchronize(c->st));
+    if (int r_ = sync_check(c)) return r_;
     return SWE_OK;
 }
 
 SWE_API int swe_cnn_get_params(swe_cnn* c, float* host) {
     if (!c || !host) return cfail(SWE_ERR_ARG, "null argument");
     CKC(cudaMemcpyAsync(host, c->p, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, c->st));
-    CKC(cudaStreamSynchronize(c->st));
+    if (int r_ = sync_check(c)) return r_;
     return SWE_OK;
 }
 
@@ -733,7 +808,7 @@ SWE_API int swe_cnn_gradients(swe_cnn* c, const void* x, const float* target, fl
     double l = 0.0;
     CKC(cudaMemcpyAsync(&l, c->dloss, sizeof(double), cudaMemcpyDeviceToHost, c->st));
     if (grads_host) CKC(cudaMemcpyAsync(grads_host, c->g, c->nparam * sizeof(float), cudaMemcpyDeviceToHost, c->st));
-    CKC(cudaStreamSynchronize(c->st));
+    if (int r_ = sync_check(c)) return r_;
     if (loss) *loss = l / (3.0 * c->n * c->h * c->w);
     return SWE_OK;
 }
@@ -752,7 +827,7 @@ SWE_API int swe_cnn_train_step(swe_cnn* c, const void* x, const float* target, f
     if (loss) {
         double l = 0.0;
         CKC(cudaMemcpyAsync(&l, c->dloss, sizeof(double), cudaMemcpyDeviceToHost, c->st));
-        CKC(cudaStreamSynchronize(c->st));
+        if (int r_ = sync_check(c)) return r_;
         *loss = l / (3.0 * c->n * c->h * c->w);
     }
     return SWE_OK;
@@ -777,6 +852,7 @@ SWE_API void swe_cnn_destroy(swe_cnn* c) {
     cudaFree(c->bpart);
     cudaFree(c->lpart);
     cudaFree(c->dloss);
+    cudaFree(c->derr);
     if (c->own_stream) cudaStreamDestroy(c->st);
     delete c;
 }

@@ -4,16 +4,17 @@
 //
 // Two organisations of the same arithmetic (swe_math.cuh):
 //  * k_fused: one launch per step.  A CTA owns a window of WIN = 128 columns
-//    (one thread per column) and streams down the rows of its segment.  Input
-//    rows (H, Qx, Qy, b, n) arrive by TMA in 4-row chunks into a 4-slot ring;
-//    every stage keeps the few rows its consumers need in shared-memory rings,
-//    so one pass over the rows runs the whole step with no intermediate in
-//    HBM.  Per row: primitives -> forces + predictor U* -> particle area H*
-//    -> forces at t_{n+1/2} + corrector + sources -> MUSCL slopes and face
-//    fluxes -> final update -> signal speed of the new state (the next step's
-//    K3, which needs one more row and column of the new state).  The
-//    dependence radius of all that is 6 cells, so a window produces its 116
-//    central columns and rows [6, 6 + seg_h) of its 12 + seg_h rows.
+//    (one thread per column in each of two warp groups) and streams down the
+//    rows of its segment.  Input rows arrive by TMA one row per copy into
+//    per-field shared-memory rings; every stage keeps the few rows its
+//    consumers need in rings of its own, so one pass over the rows runs the
+//    whole step with no intermediate in HBM: primitives and predictor U* ->
+//    particle area H* -> forces at t_{n+1/2} + corrector + sources -> MUSCL
+//    slopes and face fluxes -> final update -> forces and signal speed of
+//    the new state (the next step's K3; its accelerations are stored for
+//    the next step's predictor).  The dependence radius of all that is 6
+//    cells, so a window produces its 116 central columns and rows
+//    [6, 6 + seg_h) of its 12 + seg_h rows.
 //  * staged kernels: one kernel per stage with every intermediate in device
 //    memory (the paper's K2-K8 split); used for stage-by-stage comparison with
 //    the oracle and the per-stage time breakdown.
@@ -22,68 +23,9 @@
 #include <float.h>
 
 #include "swe_launch.h"
+#include "swe_ptx.cuh"
 
 namespace swe {
-
-// ------------------------------------------------------------------ PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void fence_mbar_init() {
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-
-__device__ __forceinline__ void fence_proxy_async() {
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for a phase of an mbarrier, giving up after ~2 s.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer_ns();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer_ns() - t0 > 2000000000ull) return false;
-    }
-}
-
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
-                                            unsigned long long* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
 
 // ------------------------------------------------------------------ time step
 

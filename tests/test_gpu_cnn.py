@@ -53,12 +53,19 @@ def _setup(torch, swe, n=2, h=32, w=48, seed=0):
     return params_r, flat, xd, x64[..., :5], td, t.astype(np.float64)
 
 
-def test_forward_matches_oracle(env):
+# (n, h, w): narrower than one 128-pixel tile of the convolution kernel, and
+# one full plus one partial tile per row
+SHAPES = [(2, 32, 48), (1, 16, 160)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_forward_matches_oracle(env, shape):
     torch, swe = env
-    params, flat, xd, x64, td, t = _setup(torch, swe)
-    with swe.CNN(2, 32, 48) as net:
+    n, h, w = shape
+    params, flat, xd, x64, td, t = _setup(torch, swe, n, h, w)
+    with swe.CNN(n, h, w) as net:
         net.set_params(flat)
-        y = torch.empty((2, 32, 48, 3), dtype=torch.float32, device="cuda")
+        y = torch.empty((n, h, w, 3), dtype=torch.float32, device="cuda")
         net.forward(xd.data_ptr(), y.data_ptr())
         torch.cuda.synchronize()
         yg = y.cpu().numpy().astype(np.float64)
@@ -66,10 +73,12 @@ def test_forward_matches_oracle(env):
     assert _rel(yg, yo) <= 1e-2
 
 
-def test_gradients_match_oracle(env):
+@pytest.mark.parametrize("shape", SHAPES)
+def test_gradients_match_oracle(env, shape):
     torch, swe = env
-    params, flat, xd, x64, td, t = _setup(torch, swe, seed=1)
-    with swe.CNN(2, 32, 48) as net:
+    n, h, w = shape
+    params, flat, xd, x64, td, t = _setup(torch, swe, n, h, w, seed=1)
+    with swe.CNN(n, h, w) as net:
         net.set_params(flat)
         g, loss = net.gradients(xd.data_ptr(), td.data_ptr())
     gg = swe.unflatten_cnn_params(g)
