@@ -188,7 +188,7 @@ def run_cnn(args, torch, swe, stream, rank, world):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                              "frac": tflops / peak, "peak_source": src, "traffic": None,
-                             "kernel": "k_conv / k_wgrad (mma.sync BF16)"},
+                             "kernel": "k_conv (tcgen05) + k_wgrad (mma.sync), BF16"},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 

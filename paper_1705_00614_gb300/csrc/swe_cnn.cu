@@ -67,40 +67,47 @@ enum ConvMode {
 };
 
 // y[n, i, j, o] = sum_{tap, c} x[n, i+dy-1, j+dx-1, c] * W[tap][o][c] (+ bias)
-// x: BF16 [N][H][W][CI]; W: BF16 [9][CO][CI]; any H, W.
+// x: BF16 [N][H][W][CI] (through the TMA map xmap); W: BF16 [9][CO][CI].
 //
-// Fifth-generation tensor cores: a persistent CTA of 4 warps keeps all nine
-// taps' weights in shared memory and, per tile of 128 pixels of one row,
-// stages the three input rows it needs (130 pixels each, zero outside the
-// image) in the no-swizzle K-major layout of swe_conv_tc.cuh; one thread
-// issues 9 * CI / 16 MMAs (M = 128 pixels, N = CO, K = 16 channels, tap
-// (dy, dx) = the staged rows started dx pixels later) accumulating in
-// tensor memory, commits them to an mbarrier, and each warp reads its 32
-// pixels' accumulators back (tcgen05.ld) for the epilogue.  Waits are
-// bounded; a timeout sets *err and the CTA frees its tensor memory and
-// stops.
+// Fifth-generation tensor cores.  A persistent CTA of 4 warps keeps all nine
+// taps' weights in shared memory and takes work items of up to `rc` rows of
+// one 128-pixel column band.  One thread streams the input rows (TMA boxes
+// of 8 channels x 130 pixels, zero outside the image) into a ring of TC_RS
+// row slots, four rows ahead, and issues for each tile (one output row of
+// the band) 9 * CI / 16 MMAs (M = 128 pixels, N = CO, K = 16 channels; tap
+// (dy, dx) reads the slot of input row i + dy - 1 started dx pixels later)
+// into one of two tensor-memory accumulators, committed to that
+// accumulator's mbarrier.  The next tile's MMAs are issued before the warps
+// read the current tile's accumulators back (tcgen05.ld) for the epilogue;
+// a CTA barrier per tile frees the other accumulator and the oldest slot.
+// Waits are bounded: on a timeout *err is set, the CTA waits (bounded) for
+// the copies and MMAs it issued, frees its tensor memory and stops.
 template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ w,
+__global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMap xmap, const __nv_bfloat16* __restrict__ w,
                                               const float* __restrict__ bias, void* __restrict__ out,
-                                              const __nv_bfloat16* __restrict__ mask, int H, int W, int CO_STORE,
-                                              int ntiles, unsigned* __restrict__ err) {
+                                              const __nv_bfloat16* __restrict__ mask, int N, int H, int W,
+                                              int CO_STORE, int rc, int nitems, unsigned* __restrict__ err) {
     constexpr int NKC = CI / 8;
     static_assert(CO == 16 || CO == 32, "MMA N");
-    // staged input rows, then the weights (dynamic shared memory of at least
-    // conv_smem_bytes<CI, CO>())
+    // row ring, then the weights (dynamic shared memory, 128-byte aligned)
     extern __shared__ __align__(128) unsigned char csm[];
-    unsigned char* const sA = csm;
-    unsigned char* const sW = csm + conv_a_bytes<CI>();
-    __shared__ __align__(8) unsigned long long bar;
+    unsigned char* const sA = csm + ((128u - (smem_u32(csm) & 127u)) & 127u);
+    unsigned char* const sW = sA + conv_a_bytes<CI>();
+    __shared__ __align__(8) unsigned long long full[TC_RS];
+    __shared__ __align__(8) unsigned long long mdone[2];
     __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (warp == 0) {
-        tmem_alloc(&s_taddr, 32);
+        tmem_alloc(&s_taddr, 64);
         tmem_relinquish();
     }
     if (tid == 0) {
-        mbar_init(&bar, 1);
+        for (int q = 0; q < TC_RS; ++q) mbar_init(&full[q], 1);
+        mbar_init(&mdone[0], 1);
+        mbar_init(&mdone[1], 1);
         fence_mbar_init();
+        s_abort = 0;
     }
     // weights: global [tap][o][c] -> shared [tap][kc][o][8]
     for (int e = tid; e < 9 * CO * NKC; e += 128) {
@@ -113,92 +120,141 @@ __global__ void __launch_bounds__(128) k_conv(const __nv_bfloat16* __restrict__ 
     __syncthreads();
     tc_fence_after();
     const uint32_t taddr = s_taddr;
-    const uint32_t tw = taddr + ((uint32_t)(32 * warp) << 16);  // this warp's 32 lanes
     const uint32_t aBase = smem_u32(sA), wBase = smem_u32(sW);
     constexpr uint32_t IDESC = idesc_bf16_f32(TCM, CO);
-    const int tpr = (W + TCM - 1) / TCM;  // tiles per image row
-    unsigned phase = 0;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int jt = t % tpr, i = (t / tpr) % H, n = t / (tpr * H);
-        const int j0 = jt * TCM;
-        // the previous tile's MMAs have completed, so its rows may be replaced
-        for (int e = tid; e < 3 * (TCM + 2) * NKC; e += 128) {
-            const int dy = e / ((TCM + 2) * NKC), p = (e / NKC) % (TCM + 2), kc = e % NKC;
-            const int gi = i + dy - 1, gj = j0 - 1 + p;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (gi >= 0 && gi < H && gj >= 0 && gj < W)
-                v = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * kc]);
-            *reinterpret_cast<uint4*>(&sA[conv_a_stage<CI>(dy, kc, p)]) = v;
+    const int tpr = (W + TCM - 1) / TCM, rcn = (H + rc - 1) / rc;
+    // rows copied and tiles issued by this CTA so far (the ring slot and the
+    // mbarrier phase of a row or tile follow from its running index); thread
+    // 0 also tracks how far it has waited, for the shutdown after a timeout
+    uint32_t grow = 0, gtile = 0;
+    uint32_t rows_issued = 0, rows_seen = 0, tiles_issued = 0;
+
+    auto issue_row = [&](uint32_t R, int n, int gi, int j0) {
+        const int slot = (int)(R % TC_RS);
+        unsigned long long* bar = &full[slot];
+        mbar_expect_tx(bar, (unsigned)(NKC * (TCM + 2) * 16));
+#pragma unroll
+        for (int kc = 0; kc < NKC; ++kc) tma_load_4d(sA + conv_a_stage<CI>(slot, kc, 0), &xmap, 8 * kc, j0 - 1, gi, n, bar);
+        rows_issued = R + 1;
+    };
+    auto wait_row = [&](uint32_t R) {
+        if (R < rows_seen) return true;
+        const bool ok = mbar_wait_bounded(&full[R % TC_RS], (R / TC_RS) & 1u);
+        if (ok) rows_seen = R + 1;
+        return ok;
+    };
+    // tile G (accumulator G & 1) from the input rows R .. R + 2
+    auto issue_mma = [&](uint32_t G, uint32_t R) {
+        const uint32_t tacc = taddr + 32u * (G & 1u);
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int slot = (int)((R + tap / 3) % TC_RS);
+#pragma unroll
+            for (int s = 0; s < CI / 16; ++s) {
+                const uint64_t ad = smem_desc(aBase + conv_a_off<CI>(slot, tap % 3, s), TC_A_LBO, TC_SBO);
+                const uint64_t bd = smem_desc(wBase + conv_b_off<CI, CO>(tap, s), conv_b_lbo<CO>(), TC_SBO);
+                tc_mma_bf16(tacc, ad, bd, IDESC, (tap | s) != 0 ? 1u : 0u);
+            }
         }
-        fence_proxy_async();
-        __syncthreads();  // staged rows visible; the last tile's accumulator reads done
+        tc_commit(&mdone[G & 1u]);
+        tiles_issued = G + 1;
+    };
+
+    bool stop = false;
+    for (int item = blockIdx.x; item < nitems && !stop; item += gridDim.x) {
+        const int jt = item % tpr, rci = (item / tpr) % rcn, n = item / (tpr * rcn);
+        const int r0 = rci * rc, nt = min(rc, H - r0), nr = nt + 2, j0 = jt * TCM;
         if (tid == 0) {
-            tc_fence_after();
-#pragma unroll
-            for (int tap = 0; tap < 9; ++tap) {
-#pragma unroll
-                for (int s = 0; s < CI / 16; ++s) {
-                    const uint64_t ad = smem_desc(aBase + conv_a_off<CI>(tap / 3, tap % 3, s), TC_A_LBO, TC_SBO);
-                    const uint64_t bd = smem_desc(wBase + conv_b_off<CI, CO>(tap, s), conv_b_lbo<CO>(), TC_SBO);
-                    tc_mma_bf16(taddr, ad, bd, IDESC, (tap | s) != 0 ? 1u : 0u);
-                }
-            }
-            tc_commit(&bar);
-        }
-        const bool ok = mbar_wait_bounded(&bar, phase);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicOr(err, 1u);
-            break;
-        }
-        tc_fence_after();
-        float v[CO];
-        tmem_ld16(tw, v);
-        if constexpr (CO > 16) tmem_ld16(tw + 16, v + 16);
-        tmem_ld_wait();
-        tc_fence_before();
-        const int j = j0 + 32 * warp + lane;
-        if (j >= W) continue;
-        const size_t pix = ((size_t)n * H + i) * W + j;
-        if (MODE == MODE_LINEAR_F32) {
-            float* y = reinterpret_cast<float*>(out);
-            for (int o = 0; o < CO_STORE; ++o) y[pix * CO_STORE + o] = v[o] + bias[o];
-        } else {
-            uint32_t pk[CO / 2];
-            if (MODE == MODE_MASK_BF16) {
-                uint32_t mk[CO / 2];
-#pragma unroll
-                for (int q = 0; q < CO / 8; ++q) {
-                    const uint4 m4 = *reinterpret_cast<const uint4*>(&mask[pix * CO + 8 * q]);
-                    mk[4 * q] = m4.x;
-                    mk[4 * q + 1] = m4.y;
-                    mk[4 * q + 2] = m4.z;
-                    mk[4 * q + 3] = m4.w;
-                }
-#pragma unroll
-                for (int h = 0; h < CO / 2; ++h) {
-                    const float m0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk[h] & 0xFFFFu)));
-                    const float m1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk[h] >> 16)));
-                    pk[h] = pack2(__float2bfloat16(m0 > 0.f ? v[2 * h] : 0.f), __float2bfloat16(m1 > 0.f ? v[2 * h + 1] : 0.f));
-                }
+            fence_proxy_async();  // earlier generic accesses to the ring precede the copies
+            for (int q = 0; q < 4 && q < nr; ++q) issue_row(grow + q, n, r0 - 1 + q, j0);
+            if (wait_row(grow) && wait_row(grow + 1) && wait_row(grow + 2)) {
+                tc_fence_after();
+                issue_mma(gtile, grow);
             } else {
-#pragma unroll
-                for (int h = 0; h < CO / 2; ++h)
-                    pk[h] = pack2(__float2bfloat16(fmaxf(v[2 * h] + bias[2 * h], 0.f)),
-                                  __float2bfloat16(fmaxf(v[2 * h + 1] + bias[2 * h + 1], 0.f)));
+                s_abort = 1;
             }
-            __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(out);
-#pragma unroll
-            for (int q = 0; q < CO / 8; ++q)
-                *reinterpret_cast<uint4*>(&y[pix * CO + 8 * q]) =
-                    make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
         }
+        for (int k = 0; k < nt; ++k) {
+            if (tid == 0 && !s_abort) {
+                // row k + 4 replaces the row of tile k - 2, whose MMAs ended
+                // before the last barrier; tile k + 1 needs rows k + 1 .. k + 3
+                if (k + 4 < nr) issue_row(grow + k + 4, n, r0 + k + 3, j0);
+                if (k + 1 < nt) {
+                    if (wait_row(grow + k + 3)) {
+                        tc_fence_after();
+                        issue_mma(gtile + k + 1, grow + k + 1);
+                    } else {
+                        s_abort = 1;
+                    }
+                }
+            }
+            const uint32_t G = gtile + k;
+            if (!mbar_wait_bounded(&mdone[G & 1u], (G >> 1) & 1u)) s_abort = 1;
+            tc_fence_after();
+            float v[CO];
+            const uint32_t tl = taddr + 32u * (G & 1u) + ((uint32_t)(32 * warp) << 16);
+            tmem_ld16(tl, v);
+            if constexpr (CO > 16) tmem_ld16(tl + 16, v + 16);
+            tmem_ld_wait();
+            tc_fence_before();
+            const int i = r0 + k, j = j0 + 32 * warp + lane;
+            if (j < W) {
+                const size_t pix = ((size_t)n * H + i) * W + j;
+                if (MODE == MODE_LINEAR_F32) {
+                    float* y = reinterpret_cast<float*>(out);
+                    for (int o = 0; o < CO_STORE; ++o) y[pix * CO_STORE + o] = v[o] + bias[o];
+                } else {
+                    uint32_t pk[CO / 2];
+                    if (MODE == MODE_MASK_BF16) {
+                        uint32_t mk[CO / 2];
+#pragma unroll
+                        for (int q = 0; q < CO / 8; ++q) {
+                            const uint4 m4 = *reinterpret_cast<const uint4*>(&mask[pix * CO + 8 * q]);
+                            mk[4 * q] = m4.x;
+                            mk[4 * q + 1] = m4.y;
+                            mk[4 * q + 2] = m4.z;
+                            mk[4 * q + 3] = m4.w;
+                        }
+#pragma unroll
+                        for (int h = 0; h < CO / 2; ++h) {
+                            const float m0 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk[h] & 0xFFFFu)));
+                            const float m1 = __bfloat162float(__ushort_as_bfloat16((unsigned short)(mk[h] >> 16)));
+                            pk[h] = pack2(__float2bfloat16(m0 > 0.f ? v[2 * h] : 0.f),
+                                          __float2bfloat16(m1 > 0.f ? v[2 * h + 1] : 0.f));
+                        }
+                    } else {
+#pragma unroll
+                        for (int h = 0; h < CO / 2; ++h)
+                            pk[h] = pack2(__float2bfloat16(fmaxf(v[2 * h] + bias[2 * h], 0.f)),
+                                          __float2bfloat16(fmaxf(v[2 * h + 1] + bias[2 * h + 1], 0.f)));
+                    }
+                    __nv_bfloat16* y = reinterpret_cast<__nv_bfloat16*>(out);
+#pragma unroll
+                    for (int q = 0; q < CO / 8; ++q)
+                        *reinterpret_cast<uint4*>(&y[pix * CO + 8 * q]) =
+                            make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                }
+            }
+            if (__syncthreads_or(s_abort)) {
+                stop = true;
+                break;
+            }
+        }
+        grow += (uint32_t)nr;
+        gtile += (uint32_t)nt;
+    }
+    if (stop && tid == 0) {
+        atomicOr(err, 1u);
+        // let the copies and MMAs this CTA issued finish before it leaves
+        for (uint32_t R = rows_seen; R < rows_issued; ++R) mbar_wait_bounded(&full[R % TC_RS], (R / TC_RS) & 1u);
+        for (uint32_t G = (tiles_issued >= 2 ? tiles_issued - 2 : 0); G < tiles_issued; ++G)
+            mbar_wait_bounded(&mdone[G & 1u], (G >> 1) & 1u);
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(taddr, 32);
+        tmem_dealloc(taddr, 64);
     }
 }
 
@@ -584,6 +640,7 @@ struct swe_cnn {
     float* yout = nullptr;            // last layer output FP32 [n][h][w][3]
     __nv_bfloat16* gbuf[2] = {};      // gradient ping-pong, BF16 [n][h][w][32]
     int nwg = 0;                      // persistent weight-gradient CTAs
+    int ntc = 0;                      // persistent convolution CTAs
     float* part = nullptr;            // weight-gradient partials, one set per such CTA
     float* bpart = nullptr;
     double* lpart = nullptr;
@@ -605,25 +662,86 @@ int sync_check(swe_cnn* c) {
 
 template <int CI, int CO>
 constexpr size_t conv_smem_bytes() {
-    return (size_t)conv_a_bytes<CI>() + conv_w_bytes<CI, CO>();
+    return (size_t)conv_a_bytes<CI>() + conv_w_bytes<CI, CO>() + 128;  // + alignment slack
 }
 
-// Tiles of the convolution kernel (128 pixels of one row) and its
-// persistent grid.
-int conv_tiles(const swe_cnn* c) { return c->n * c->h * ((c->w + TCM - 1) / TCM); }
-int conv_grid(const swe_cnn* c) { return std::min(conv_tiles(c), c->nwg); }
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int layer_fwd(swe_cnn* c, int l, const __nv_bfloat16* x, void* out) {
-    const int nt = conv_tiles(c), g = conv_grid(c);
-    const float* bias = c->p + c->off_b[l];
-    switch (l) {
-        case 0: k_conv<16, 32, MODE_RELU_BF16><<<g, 128, conv_smem_bytes<16, 32>(), c->st>>>(x, c->wk[0], bias, out, nullptr, c->h, c->w, 32, nt, c->derr); break;
-        case 1: k_conv<32, 32, MODE_RELU_BF16><<<g, 128, conv_smem_bytes<32, 32>(), c->st>>>(x, c->wk[1], bias, out, nullptr, c->h, c->w, 32, nt, c->derr); break;
-        case 2: k_conv<32, 32, MODE_RELU_BF16><<<g, 128, conv_smem_bytes<32, 32>(), c->st>>>(x, c->wk[2], bias, out, nullptr, c->h, c->w, 32, nt, c->derr); break;
-        default: k_conv<32, 16, MODE_LINEAR_F32><<<g, 128, conv_smem_bytes<32, 16>(), c->st>>>(x, c->wk[3], bias, out, nullptr, c->h, c->w, 3, nt, c->derr); break;
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
     }
+    return fn;
+}
+
+// TMA map of a BF16 NHWC image batch [n][h][w][ci]: boxes of 8 channels x
+// (TCM + 2) pixels of one row; reads outside the image return zeros.
+int x_map(CUtensorMap* m, const void* x, int n, int h, int w, int ci) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return cfail(SWE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[4] = {(cuuint64_t)ci, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
+    const cuuint64_t strides[3] = {(cuuint64_t)ci * 2, (cuuint64_t)w * ci * 2, (cuuint64_t)h * w * ci * 2};
+    const cuuint32_t box[4] = {8, (cuuint32_t)(TCM + 2), 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return cfail(SWE_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    return SWE_OK;
+}
+
+// Work split of the convolution kernel: items of rc rows of one 128-pixel
+// column band, about one item per persistent CTA.
+struct ConvPlan {
+    int grid, rc, nitems;
+};
+ConvPlan conv_plan(const swe_cnn* c) {
+    const int tpr = (c->w + TCM - 1) / TCM;
+    const long long tiles = (long long)c->n * c->h * tpr;
+    int rc = (int)std::max<long long>(4, (tiles + c->ntc - 1) / c->ntc);
+    rc = std::min(rc, c->h);
+    ConvPlan p;
+    p.rc = rc;
+    p.nitems = c->n * tpr * ((c->h + rc - 1) / rc);
+    p.grid = std::min(p.nitems, c->ntc);
+    return p;
+}
+
+template <int CI, int CO, int MODE>
+int conv(swe_cnn* c, const void* x, const __nv_bfloat16* w, const float* bias, void* out, const __nv_bfloat16* mask,
+         int co_store) {
+    CUtensorMap m;
+    int rc = x_map(&m, x, c->n, c->h, c->w, CI);
+    if (rc) return rc;
+    const ConvPlan p = conv_plan(c);
+    k_conv<CI, CO, MODE><<<p.grid, 128, conv_smem_bytes<CI, CO>(), c->st>>>(m, w, bias, out, mask, c->n, c->h, c->w,
+                                                                           co_store, p.rc, p.nitems, c->derr);
     CKC(cudaGetLastError());
     return SWE_OK;
+}
+
+template <int CI, int CO, int MODE>
+cudaError_t conv_attr() {
+    return cudaFuncSetAttribute(k_conv<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)conv_smem_bytes<CI, CO>());
+}
+
+int layer_fwd(swe_cnn* c, int l, const __nv_bfloat16* x, void* out) {
+    const float* bias = c->p + c->off_b[l];
+    switch (l) {
+        case 0: return conv<16, 32, MODE_RELU_BF16>(c, x, c->wk[0], bias, out, nullptr, 32);
+        case 1: return conv<32, 32, MODE_RELU_BF16>(c, x, c->wk[1], bias, out, nullptr, 32);
+        case 2: return conv<32, 32, MODE_RELU_BF16>(c, x, c->wk[2], bias, out, nullptr, 32);
+        default: return conv<32, 16, MODE_LINEAR_F32>(c, x, c->wk[3], bias, out, nullptr, 3);
+    }
 }
 
 // Output-gradient channels of layer l as seen by its backward kernels: the
@@ -675,12 +793,9 @@ int backward_all(swe_cnn* c, const __nv_bfloat16* x, const float* target) {
         if (l > 0) {
             // data gradient into layer l's input, masked by that input's ReLU
             __nv_bfloat16* go = c->gbuf[cur ^ 1];
-            if (l == 3)
-                k_conv<16, 32, MODE_MASK_BF16><<<conv_grid(c), 128, conv_smem_bytes<16, 32>(), c->st>>>(gl, c->wd[3], nullptr, go, c->act[3],
-                                                                                c->h, c->w, 32, conv_tiles(c), c->derr);
-            else
-                k_conv<32, 32, MODE_MASK_BF16><<<conv_grid(c), 128, conv_smem_bytes<32, 32>(), c->st>>>(gl, c->wd[l], nullptr, go, c->act[l],
-                                                                                c->h, c->w, 32, conv_tiles(c), c->derr);
+            const int rc = l == 3 ? conv<16, 32, MODE_MASK_BF16>(c, gl, c->wd[3], nullptr, go, c->act[3], 32)
+                                  : conv<32, 32, MODE_MASK_BF16>(c, gl, c->wd[l], nullptr, go, c->act[l], 32);
+            if (rc) return rc;
             cur ^= 1;
         }
     }
@@ -743,6 +858,13 @@ SWE_API int swe_cnn_create(int32_t n, int32_t h, int32_t w, void* stream, swe_cn
         return cfail(SWE_ERR_CUDA, "device attributes");
     }
     c->nwg = (int)std::min<size_t>((size_t)grid.x * grid.y * grid.z, (size_t)4 * nsm);
+    c->ntc = 3 * nsm;  // three 71 KB CTAs fit an SM
+    if (conv_attr<16, 32, MODE_RELU_BF16>() != cudaSuccess || conv_attr<32, 32, MODE_RELU_BF16>() != cudaSuccess ||
+        conv_attr<32, 16, MODE_LINEAR_F32>() != cudaSuccess || conv_attr<16, 32, MODE_MASK_BF16>() != cudaSuccess ||
+        conv_attr<32, 32, MODE_MASK_BF16>() != cudaSuccess) {
+        swe_cnn_destroy(c);
+        return cfail(SWE_ERR_CUDA, "convolution kernel shared-memory size");
+    }
     const size_t nblk = (size_t)c->nwg;
     bool ok = cudaMalloc(&c->p, np * sizeof(float)) == cudaSuccess && cudaMalloc(&c->g, np * sizeof(float)) == cudaSuccess &&
               cudaMalloc(&c->m, np * sizeof(float)) == cudaSuccess && cudaMalloc(&c->v, np * sizeof(float)) == cudaSuccess;

@@ -40,20 +40,27 @@ template <int CI, int CO>
 static void check() {
     const uint32_t A0 = 0x400, W0 = A0 + conv_a_bytes<CI>() + 128;
     for (int tap = 0; tap < 9; ++tap) {
-        const int dy = tap / 3, dx = tap % 3;
+        const int dx = tap % 3;
+        for (int s = 0; s < CI / 16; ++s)
+            for (int slot = 0; slot < TC_RS; ++slot) {
+                const Desc a = decode(smem_desc(A0 + conv_a_off<CI>(slot, dx, s), TC_A_LBO, TC_SBO));
+                for (int k = 0; k < 16; ++k) {
+                    const int c = 16 * s + k;
+                    for (int m = 0; m < TCM; ++m) {
+                        // output pixel m of the tile reads staged pixel m + dx of the slot's row
+                        const uint32_t want = A0 + conv_a_stage<CI>(slot, c / 8, m + dx) + (uint32_t)(c % 8) * 2;
+                        const uint32_t got = addr(a, m, k);
+                        if (got != want || got < A0 || got + 2 > A0 + conv_a_bytes<CI>()) {
+                            if (fails++ < 5)
+                                std::printf("A CI=%d slot=%d dx=%d s=%d m=%d k=%d: %u vs %u\n", CI, slot, dx, s, m, k, got, want);
+                        }
+                    }
+                }
+            }
         for (int s = 0; s < CI / 16; ++s) {
-            const Desc a = decode(smem_desc(A0 + conv_a_off<CI>(dy, dx, s), TC_A_LBO, TC_SBO));
             const Desc b = decode(smem_desc(W0 + conv_b_off<CI, CO>(tap, s), conv_b_lbo<CO>(), TC_SBO));
             for (int k = 0; k < 16; ++k) {
                 const int c = 16 * s + k;  // input channel of this K element
-                for (int m = 0; m < TCM; ++m) {
-                    // output pixel m of the tile reads staged pixel m + dx of input row dy
-                    const uint32_t want = A0 + conv_a_stage<CI>(dy, c / 8, m + dx) + (uint32_t)(c % 8) * 2;
-                    const uint32_t got = addr(a, m, k);
-                    if (got != want || got < A0 || got + 2 > A0 + conv_a_bytes<CI>()) {
-                        if (fails++ < 5) std::printf("A CI=%d tap=%d s=%d m=%d k=%d: %u vs %u\n", CI, tap, s, m, k, got, want);
-                    }
-                }
                 for (int o = 0; o < CO; ++o) {
                     const uint32_t want = W0 + conv_w_stage<CI, CO>(tap, c / 8, o) + (uint32_t)(c % 8) * 2;
                     const uint32_t got = addr(b, o, k);
