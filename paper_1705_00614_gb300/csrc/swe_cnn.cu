@@ -46,6 +46,14 @@ constexpr int CH[NLAYER + 1] = {5, 32, 32, 32, 3};
 constexpr int CIP[NLAYER] = {16, 32, 32, 32};  // padded input channels
 constexpr int COP[NLAYER] = {32, 32, 32, 16};  // padded output channels
 
+// Four 8 x 8 BF16 matrices from shared memory, transposed (lanes 8q .. 8q+7
+// give the 16-byte rows of matrix q).
+__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(smem_u32(p)));
+}
+
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
@@ -273,9 +281,11 @@ __global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restri
     constexpr int UPW = (UNITS + TY - 1) / TY;
     __shared__ __align__(16) __nv_bfloat16 sx[(TY + 2) * (TX + 2) * PS];
     __shared__ __align__(16) __nv_bfloat16 sg[TY * TX * GS];
+    static_assert(CO % 16 == 0, "B fragments are loaded in pairs");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int gx = W / TX, gy = H / TY;
     const int r0 = lane >> 2, kc = (lane & 3) * 2;
+    const int lq = lane >> 3, lr = lane & 7;  // ldmatrix: matrix and row this lane addresses
     float acc[UPW][CO / 8][4];
 #pragma unroll
     for (int q = 0; q < UPW; ++q)
@@ -311,18 +321,18 @@ __global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restri
             for (int ti = 0; ti < TY; ++ti) {
                 const __nv_bfloat16* xr = &sx[((ti + ky) * (TX + 2) + kx) * PS];
                 const __nv_bfloat16* gr = &sg[(ti * TX) * GS];
-                // A[m = c][k = p] = x[p][c]: pairs of consecutive pixels
-                const uint32_t a0 = pack2(xr[kc * PS + cb + r0], xr[(kc + 1) * PS + cb + r0]);
-                const uint32_t a1 = pack2(xr[kc * PS + cb + r0 + 8], xr[(kc + 1) * PS + cb + r0 + 8]);
-                const uint32_t a2 = pack2(xr[(kc + 8) * PS + cb + r0], xr[(kc + 9) * PS + cb + r0]);
-                const uint32_t a3 = pack2(xr[(kc + 8) * PS + cb + r0 + 8], xr[(kc + 9) * PS + cb + r0 + 8]);
+                // A[m = c][k = p] = x[p][c]: the transposes of the 8 x 8 blocks
+                // (pixels 0-7 | 8-15) x (channels cb + 0-7 | 8-15)
+                uint32_t a0, a1, a2, a3;
+                ldsm_x4_t(a0, a1, a2, a3, xr + ((lq & 2) ? 8 : 0) * PS + lr * PS + cb + ((lq & 1) ? 8 : 0));
 #pragma unroll
-                for (int f = 0; f < CO / 8; ++f) {
-                    // B[k = p][n = o] = g[p][o]
-                    const int o = 8 * f + r0;
-                    const uint32_t b0 = pack2(gr[kc * GS + o], gr[(kc + 1) * GS + o]);
-                    const uint32_t b1 = pack2(gr[(kc + 8) * GS + o], gr[(kc + 9) * GS + o]);
+                for (int f = 0; f < CO / 8; f += 2) {
+                    // B[k = p][n = o] = g[p][o]: transposed blocks (pixels 0-7 |
+                    // 8-15) x (outputs 8f + 0-7 | 8f + 8-15)
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4_t(b0, b1, b2, b3, gr + ((lq & 1) ? 8 : 0) * GS + lr * GS + 8 * f + ((lq & 2) ? 8 : 0));
                     mma_bf16(acc[q][f], a0, a1, a2, a3, b0, b1);
+                    mma_bf16(acc[q][f + 1], a0, a1, a2, a3, b2, b3);
                 }
             }
         }
@@ -407,6 +417,7 @@ __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, 
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     double l = 0.0;
     if (p < npix) {
+        __nv_bfloat16 gv[16];
         for (int o = 0; o < 16; ++o) {
             float g = 0.f;
             if (o < co) {
@@ -414,8 +425,11 @@ __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, 
                 l += (double)d * d;
                 g = 2.f * d * scale;
             }
-            gy[p * 16 + o] = __float2bfloat16(g);
+            gv[o] = __float2bfloat16(g);
         }
+        uint4* dst = reinterpret_cast<uint4*>(&gy[p * 16]);
+        dst[0] = *reinterpret_cast<const uint4*>(&gv[0]);
+        dst[1] = *reinterpret_cast<const uint4*>(&gv[8]);
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
