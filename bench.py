@@ -193,6 +193,99 @@ def run_cnn(args, torch, swe, stream, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_closure(args, torch, swe, stream, rank, world):
+    """Learned closure of the 4x coarser grid (closure-<n>sq: fine n^2 at
+    dx = 5 m, coarse (n/4)^2 at 20 m).  Trains the network on fine runs of
+    the training seeds, then runs held-out seeds fine, coarse plain and
+    coarse closed side by side and reports the relative L2 error in H of
+    both coarse runs against the restricted fine solution at several
+    horizons, and the wall-clock speed-up of the closed coarse solve over
+    the fine solve (same simulated time)."""
+    from paper_1705_00614_gb300 import closure as CL
+    n = int(args.workload.split("-")[1].replace("sq", ""))
+    tau_c = 0.2
+    train_seeds = list(range(20000, 20000 + args.closure_train))
+    test_seeds = list(range(20064, 20064 + args.closure_test))
+    horizons = [h for h in (10, 100, 1000, 5000) if h <= args.closure_steps]
+
+    def scenario(seed):
+        return CL.dam_release(I.floodplain(n, 5.0, seed, seed + 1, nsrc=20,
+                                           hydro=I.Hydrograph(0, 2.0, 40.0, 20.0)))
+
+    rng = np.random.default_rng(0)
+    t0 = time.perf_counter()
+    norm = CL.estimate_norm(torch, [scenario(train_seeds[0])], 10, tau_c, rng, 128)
+    X, T = [], []
+    for sd in train_seeds:
+        x, t = CL.collect(torch, scenario(sd), args.closure_collect, tau_c, norm.inp(), norm.out(), 8, 128, rng,
+                          stream=stream.cuda_stream)
+        X.append(x)
+        T.append(t)
+    X = torch.cat(X)
+    T = torch.cat(T)
+    params, hist = CL.train(torch, X, T, args.closure_iters, 16, 1e-3, 1, stream=stream.cuda_stream, log_every=500)
+    del X, T
+    t_train = time.perf_counter() - t0
+
+    errs = {"plain": {h: [] for h in horizons}, "closed": {h: [] for h in horizons}}
+    ms_fine, ms_closed = [], []
+    for sd in test_seeds:
+        fp = scenario(sd)
+        cp = CL.coarse_problem(fp)
+        fine = swe.Solver.from_problem(CL.with_dt(fp, tau_c / 4.0), "f32", stream=stream.cuda_stream)
+        plain = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
+        closed = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
+        ref = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
+        net = swe.CNN(1, cp.params.ny, cp.params.nx, stream.cuda_stream)
+        try:
+            net.set_params(params)
+            plain.restrict_from(fine)
+            closed.restrict_from(fine)
+            closed.attach_closure(net, norm.all())
+            done = 0
+            for h in horizons:
+                k = h - done
+                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                e[0].record(stream)
+                fine.step(4 * k, report=False)
+                e[1].record(stream)
+                closed.step_closed(k, report=False)
+                e[2].record(stream)
+                plain.step(k, report=False)
+                torch.cuda.synchronize()
+                ms_fine.append(e[0].elapsed_time(e[1]) / k)
+                ms_closed.append(e[1].elapsed_time(e[2]) / k)
+                done = h
+                ref.restrict_from(fine)
+                Hr = ref.get_state()[0]
+                den = max(np.linalg.norm(Hr), 1e-30)
+                errs["plain"][h].append(float(np.linalg.norm(plain.get_state()[0] - Hr) / den))
+                errs["closed"][h].append(float(np.linalg.norm(closed.get_state()[0] - Hr) / den))
+        finally:
+            closed.attach_closure(None, norm.all())
+            for x in (fine, plain, closed, ref, net):
+                x.close()
+    mean = {k: {h: float(np.mean(v)) for h, v in d.items()} for k, d in errs.items()}
+    last = horizons[-1]
+    speedup = float(np.median(ms_fine)) / float(np.median(ms_closed))
+    if rank == 0:
+        line = {"metric": "CNN-closure vs fine solve: relative L2 error in H", "value": mean["closed"][last],
+                "unit": "fraction", "n_gpus": world, "steps": last, "warmup": 0,
+                "ms_per_step": float(np.median(ms_closed)), "higher_is_better": False, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
+                "config": {"workload": args.workload, "fine": f"{n}^2 dx 5 m", "coarse": f"{n // 4}^2 dx 20 m",
+                           "scenario": "fractal floodplain, flood release (+2 m over the first quarter) and inflow",
+                           "tau_coarse_s": tau_c, "train_seeds": len(train_seeds), "test_seeds": len(test_seeds),
+                           "collect_steps_per_seed": args.closure_collect, "train_iters": args.closure_iters,
+                           "final_train_loss": hist[-1][1], "train_wall_s": t_train,
+                           "rel_l2_closed": mean["closed"], "rel_l2_plain": mean["plain"],
+                           "target": 0.01, "speedup_closed_coarse_vs_fine": speedup,
+                           "ms_per_fine_step": float(np.median(ms_fine)),
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None}
+        print(json.dumps(line), flush=True)
+
+
 def crop(prob, y0, x0, n):
     s = prob.sources
     keep = (s.ix >= x0) & (s.ix < x0 + n) & (s.iy >= y0) & (s.iy < y0 + n)
@@ -337,6 +430,11 @@ def main():
     ap.add_argument("--skip-dry", action="store_true",
                     help="skip dry work items (the paper's K1 wet-block test); off for the headline")
     ap.add_argument("--seg-h", type=int, default=0, help="output rows per work item (0 = automatic)")
+    ap.add_argument("--closure-train", type=int, default=8, help="closure workload: training seeds")
+    ap.add_argument("--closure-test", type=int, default=4, help="closure workload: held-out seeds")
+    ap.add_argument("--closure-collect", type=int, default=100, help="closure workload: coarse steps per seed")
+    ap.add_argument("--closure-iters", type=int, default=3000, help="closure workload: Adam steps")
+    ap.add_argument("--closure-steps", type=int, default=5000, help="closure workload: longest horizon")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -362,6 +460,14 @@ def main():
     from paper_1705_00614_gb300 import build as B
     from paper_1705_00614_gb300 import swe
     B.build()
+
+    if args.workload.startswith("closure-"):
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        run_closure(args, torch, swe, stream, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     if args.workload.startswith("cnn-"):
         stream = torch.cuda.Stream()
