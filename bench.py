@@ -224,24 +224,39 @@ def run_closure(args, torch, swe, stream, rank, world):
     X = torch.cat(X)
     T = torch.cat(T)
     params, hist = CL.train(torch, X, T, args.closure_iters, 16, 1e-3, 1, stream=stream.cuda_stream, log_every=500)
+    # optional rounds of pairs from the closed model's own trajectory
+    for r in range(args.closure_dagger):
+        for sd in train_seeds:
+            x, t = CL.collect_closed(torch, scenario(sd), args.closure_collect, tau_c, params, norm, 8, 128, rng,
+                                     stream=stream.cuda_stream)
+            if x is not None:
+                X = torch.cat([X, x])
+                T = torch.cat([T, t])
+        params, h2 = CL.train(torch, X, T, args.closure_iters // 2, 16, 5e-4, 2 + r, stream=stream.cuda_stream,
+                              log_every=500, init=params)
+        hist += h2
     del X, T
     t_train = time.perf_counter() - t0
 
-    errs = {"plain": {h: [] for h in horizons}, "closed": {h: [] for h in horizons}}
+    alphas = [float(a) for a in args.closure_alpha.split(",")]
+    names = ["plain"] + [f"closed_a{a:g}" for a in alphas]
+    errs = {k: {h: [] for h in horizons} for k in names}
     ms_fine, ms_closed = [], []
     for sd in test_seeds:
         fp = scenario(sd)
         cp = CL.coarse_problem(fp)
         fine = swe.Solver.from_problem(CL.with_dt(fp, tau_c / 4.0), "f32", stream=stream.cuda_stream)
         plain = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
-        closed = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
+        closed = [swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream) for _ in alphas]
         ref = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
-        net = swe.CNN(1, cp.params.ny, cp.params.nx, stream.cuda_stream)
+        nets = [swe.CNN(1, cp.params.ny, cp.params.nx, stream.cuda_stream) for _ in alphas]
+        alive = [True] * len(alphas)
         try:
-            net.set_params(params)
             plain.restrict_from(fine)
-            closed.restrict_from(fine)
-            closed.attach_closure(net, norm.all())
+            for c, net, a in zip(closed, nets, alphas):
+                net.set_params(params)
+                c.restrict_from(fine)
+                c.attach_closure(net, CL.shrink(norm, a).all())
             done = 0
             for h in horizons:
                 k = h - done
@@ -249,27 +264,40 @@ def run_closure(args, torch, swe, stream, rank, world):
                 e[0].record(stream)
                 fine.step(4 * k, report=False)
                 e[1].record(stream)
-                closed.step_closed(k, report=False)
+                if alive[0]:
+                    closed[0].step_closed(k, report=False)
                 e[2].record(stream)
+                for q in range(1, len(alphas)):
+                    if alive[q]:
+                        closed[q].step_closed(k, report=False)
                 plain.step(k, report=False)
                 torch.cuda.synchronize()
                 ms_fine.append(e[0].elapsed_time(e[1]) / k)
-                ms_closed.append(e[1].elapsed_time(e[2]) / k)
+                if alive[0]:
+                    ms_closed.append(e[1].elapsed_time(e[2]) / k)
                 done = h
                 ref.restrict_from(fine)
                 Hr = ref.get_state()[0]
                 den = max(np.linalg.norm(Hr), 1e-30)
                 errs["plain"][h].append(float(np.linalg.norm(plain.get_state()[0] - Hr) / den))
-                errs["closed"][h].append(float(np.linalg.norm(closed.get_state()[0] - Hr) / den))
+                for q, (c, a) in enumerate(zip(closed, alphas)):
+                    Hc = c.get_state()[0] if alive[q] else None
+                    if Hc is None or not np.isfinite(Hc).all():
+                        alive[q] = False  # diverged: reported as NaN from here on
+                        errs[names[1 + q]][h].append(float("nan"))
+                    else:
+                        errs[names[1 + q]][h].append(float(np.linalg.norm(Hc - Hr) / den))
         finally:
-            closed.attach_closure(None, norm.all())
-            for x in (fine, plain, closed, ref, net):
+            for c in closed:
+                c.attach_closure(None, norm.all())
+            for x in [fine, plain, ref] + closed + nets:
                 x.close()
     mean = {k: {h: float(np.mean(v)) for h, v in d.items()} for k, d in errs.items()}
     last = horizons[-1]
+    best = min(names[1:], key=lambda k: (np.nan_to_num(mean[k][last], nan=np.inf)))
     speedup = float(np.median(ms_fine)) / float(np.median(ms_closed))
     if rank == 0:
-        line = {"metric": "CNN-closure vs fine solve: relative L2 error in H", "value": mean["closed"][last],
+        line = {"metric": "CNN-closure vs fine solve: relative L2 error in H", "value": mean[best][last],
                 "unit": "fraction", "n_gpus": world, "steps": last, "warmup": 0,
                 "ms_per_step": float(np.median(ms_closed)), "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
@@ -277,8 +305,9 @@ def run_closure(args, torch, swe, stream, rank, world):
                            "scenario": "fractal floodplain, flood release (+2 m over the first quarter) and inflow",
                            "tau_coarse_s": tau_c, "train_seeds": len(train_seeds), "test_seeds": len(test_seeds),
                            "collect_steps_per_seed": args.closure_collect, "train_iters": args.closure_iters,
+                           "dagger_rounds": args.closure_dagger,
                            "final_train_loss": hist[-1][1], "train_wall_s": t_train,
-                           "rel_l2_closed": mean["closed"], "rel_l2_plain": mean["plain"],
+                           "rel_l2": mean, "reported": best,
                            "target": 0.01, "speedup_closed_coarse_vs_fine": speedup,
                            "ms_per_fine_step": float(np.median(ms_fine)),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -435,6 +464,10 @@ def main():
     ap.add_argument("--closure-collect", type=int, default=100, help="closure workload: coarse steps per seed")
     ap.add_argument("--closure-iters", type=int, default=3000, help="closure workload: Adam steps")
     ap.add_argument("--closure-steps", type=int, default=5000, help="closure workload: longest horizon")
+    ap.add_argument("--closure-alpha", default="1",
+                    help="closure workload: comma-separated correction scales to evaluate side by side")
+    ap.add_argument("--closure-dagger", type=int, default=0,
+                    help="closure workload: rounds of training pairs from the closed model's own trajectory")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

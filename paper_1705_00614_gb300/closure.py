@@ -132,6 +132,57 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
     return torch.stack(xs), torch.stack(ts)
 
 
+def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step, crop, rng, stream=None):
+    """Training pairs along the closed model's own coarse trajectory: the
+    closed grid runs beside the fine grid; at every coarse step the plain
+    coarse step is taken from the closed grid's state and the target is the
+    correction that would have put it on the restricted fine state.  A
+    network trained on them also learns to undo its own drift (pairs from
+    the states it visits, not only from restricted fine states)."""
+    cp = coarse_problem(fine_prob)
+    nyc, nxc = cp.params.ny, cp.params.nx
+    fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
+    C = S.Solver.from_problem(with_dt(cp, tau_c), "f32", stream=stream)
+    A = S.Solver.from_problem(with_dt(cp, tau_c), "f32", stream=stream)
+    B = S.Solver.from_problem(with_dt(cp, tau_c), "f32", stream=stream)
+    net = S.CNN(1, nyc, nxc, stream)
+    xs, ts = [], []
+    xfull = torch.empty((nyc, nxc, 16), dtype=torch.bfloat16, device="cuda")
+    tfull = torch.empty((nyc, nxc, 3), dtype=torch.float32, device="cuda")
+    try:
+        net.set_params(params)
+        C.restrict_from(fine)
+        C.attach_closure(net, norm.all())
+        for _ in range(steps):
+            H, Qx, Qy, t = C.get_state()
+            if not (np.isfinite(H).all() and np.isfinite(Qx).all() and np.isfinite(Qy).all()):
+                break  # the closed run left the physical range: keep the pairs so far
+            try:
+                A.set_state(H, Qx, Qy, t)
+                A.closure_features(norm.inp(), xfull.data_ptr())
+                A.step(1)
+                fine.step(4)
+                B.restrict_from(fine)
+                A.closure_targets(B, norm.out(), tfull.data_ptr())
+                C.step_closed(1, report=False)
+                torch.cuda.synchronize()
+            except S.SweError:
+                break  # the closed state no longer gives a finite step
+            for _ in range(crops_per_step):
+                y0 = int(rng.integers(0, nyc - crop + 1))
+                x0 = int(rng.integers(0, nxc - crop + 1))
+                xs.append(xfull[y0:y0 + crop, x0:x0 + crop].clone())
+                ts.append(tfull[y0:y0 + crop, x0:x0 + crop].clone())
+    finally:
+        C.attach_closure(None, norm.all())
+        for x in (fine, C, A, B, net):
+            x.close()
+    if not xs:
+        return None, None
+    # standardised targets are clipped like the network's outputs
+    return torch.stack(xs), torch.stack(ts).clamp_(-10.0, 10.0)
+
+
 def estimate_norm(torch, probs, steps, tau_c, rng, crop):
     """Per-channel mean and standard deviation of inputs and targets from a
     short pilot collection with identity normalisation."""
@@ -163,14 +214,15 @@ def he_init(seed, channels=S.CNN_CHANNELS):
     return out
 
 
-def train(torch, X, T, iters, batch, lr, seed, stream=None, log_every=0):
-    """Adam on the mean-squared error of standardised targets; returns the
-    flat parameters and the loss history."""
+def train(torch, X, T, iters, batch, lr, seed, stream=None, log_every=0, init=None):
+    """Adam on the mean-squared error of standardised targets, from He
+    initialisation or from the flat parameters `init`; returns the flat
+    parameters and the loss history."""
     nS, h, w = X.shape[0], X.shape[1], X.shape[2]
     rng = np.random.default_rng(seed)
     hist = []
     with S.CNN(batch, h, w, stream) as net:
-        net.set_params(S.flatten_cnn_params(he_init(seed)))
+        net.set_params(S.flatten_cnn_params(he_init(seed)) if init is None else init)
         for it in range(iters):
             i = int(rng.integers(0, nS - batch + 1))
             rep = (log_every and it % log_every == 0) or it == iters - 1
