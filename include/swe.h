@@ -92,6 +92,15 @@ typedef struct {
                               cell.  Never applied to swe_step_closed.
                               Off by default (throughput then does not depend
                               on the wet fraction). */
+    int32_t ghost_ring;    /* fused mode, 0 or 1: 0 = the SWE_PAD cells around the
+                              grid are reflective walls; 1 = they are ghost cells
+                              whose terrain the caller sets with
+                              swe_set_terrain_ext and whose state a nest
+                              (swe_nest_*) fills from a coarser grid before
+                              every step (a ghost cell that is never filled is
+                              dry ground, through which water can leave).  Such
+                              a context evaluates the forces of every step in
+                              the kernel instead of storing them. */
 } swe_params;
 
 /* What one call of swe_step reports (all reductions in FP64). */
@@ -122,6 +131,12 @@ SWE_API int swe_create(const swe_params* p, swe_ctx** out_ctx);
  * host FP64.  manning_n may be NULL (0 everywhere).  Finite values only
  * (SWE_ERR_NONFINITE otherwise); |b| < 1e20. */
 SWE_API int swe_set_terrain(swe_ctx* ctx, const double* b, const double* manning_n);
+
+/* For a ghost_ring context: bed and Manning n over the whole padded extent,
+ * host FP64 [ny + 2 SWE_PAD][nx + 2 SWE_PAD] row-major (the interior starts
+ * at row and column SWE_PAD); manning_n may be NULL (0).  A ring cell whose
+ * bed is at least 1e29 stays a wall. */
+SWE_API int swe_set_terrain_ext(swe_ctx* ctx, const double* b_ext, const double* manning_n_ext);
 
 /* State at time t: depth H >= 0 and momentum Qx = H Ux, Qy = H Uy (the
  * paper's H and HV), nx*ny host FP64 each.  Resets the step counter, the
@@ -228,6 +243,37 @@ SWE_API int swe_batch_step(swe_batch* b, int32_t nsteps, swe_step_info* infos);
 SWE_API int swe_batch_autotune(swe_batch* b, int32_t trial_steps, int32_t* seg_h_out);
 
 SWE_API void swe_batch_destroy(swe_batch* b);
+
+/* ------------------------------------------------------------------------
+ * Two-level nesting (the paper's hierarchical grid system with feedback,
+ * Sec. 2.2, Fig. 1): a fine patch, 4x finer than its coarse parent, runs
+ * four sub-steps per coarse step.  Per coarse step: (1) the coarse grid
+ * steps from t to t + tau_c; (2) before each fine sub-step s = 0..3 the
+ * patch's ghost ring is filled from the coarse grid at time t + s tau_c / 4
+ * (the coarse cell containing each ghost cell; coarse state linear in time;
+ * ghost depth = coarse free surface minus the fine bed, ghost velocity = the
+ * coarse one; dry or wall coarse cells give dry ghosts) and the patch steps;
+ * (3) every coarse cell under the patch takes the 4 x 4 means of the fine
+ * H, Qx, Qy (feedback), and the coarse time-step speed is recomputed.  Face
+ * fluxes across the patch boundary are not re-matched between the levels.
+ * ------------------------------------------------------------------------ */
+typedef struct swe_nest swe_nest; /* opaque */
+
+/* Nest `fine` into `coarse` with fine interior cell (0, 0) in coarse cell
+ * (ix0, iy0).  Requirements (SWE_ERR_ARG otherwise): both SWE_FUSED, one
+ * precision, states set at the same time; fine->ghost_ring = 1 and coarse's
+ * 0; fine nx, ny multiples of 4 and fine dx = coarse dx / 4; fixed steps with
+ * fine dt_fixed = coarse dt_fixed / 4; the patch and the 3 coarse cells
+ * around it inside the coarse grid.  The nest borrows both contexts (destroy
+ * it before them). */
+SWE_API int swe_nest_create(swe_ctx* coarse, swe_ctx* fine, int32_t ix0, int32_t iy0, swe_nest** out);
+
+/* Advance ncoarse coarse steps (4 fine sub-steps each).  With info_coarse /
+ * info_fine != NULL the streams are synchronised and the reports of both
+ * grids copied out. */
+SWE_API int swe_nest_step(swe_nest* n, int32_t ncoarse, swe_step_info* info_coarse, swe_step_info* info_fine);
+
+SWE_API void swe_nest_destroy(swe_nest* n);
 
 /* ------------------------------------------------------------------------
  * Learned closure for a 4x coarser grid level.  The paper simulates on

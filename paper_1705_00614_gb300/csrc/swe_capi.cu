@@ -703,6 +703,10 @@ int swe_create(const swe_params* p, swe_ctx** out) {
     if (p->tile_w != 0 && p->tile_w != TW) return fail(SWE_ERR_ARG, "tile_w must be 0 or 116");
     if (p->skip_dry != 0 && p->skip_dry != 1) return fail(SWE_ERR_ARG, "skip_dry must be 0 or 1");
     if (p->skip_dry && p->mode != SWE_FUSED) return fail(SWE_ERR_ARG, "skip_dry needs SWE_FUSED");
+    if (p->ghost_ring != 0 && p->ghost_ring != 1) return fail(SWE_ERR_ARG, "ghost_ring must be 0 or 1");
+    if (p->ghost_ring && p->mode != SWE_FUSED) return fail(SWE_ERR_ARG, "ghost_ring needs SWE_FUSED");
+    if (p->ghost_ring && p->skip_dry)
+        return fail(SWE_ERR_ARG, "skip_dry needs wall boundaries (ghost cells are not stamped)");
     swe_ctx* c = new (std::nothrow) swe_ctx();
     if (!c) return fail(SWE_ERR_OOM, "context");
     c->p = *p;
@@ -725,7 +729,9 @@ int swe_create(const swe_params* p, swe_ctx** out) {
             return bail(SWE_ERR_CUDA, "stream creation");
         c->own_stream = true;
     }
-    const int nplanes = p->mode == SWE_FUSED ? 14 : 8;
+    // stored accelerations: fused contexts with wall rings (a ghost ring's
+    // forces change with every fill, so those contexts evaluate them in the kernel)
+    const int nplanes = (p->mode == SWE_FUSED && !p->ghost_ring) ? 14 : 8;
     for (int k = 0; k < nplanes; ++k) {
         if (cudaMalloc(&c->f[k], c->plane) != cudaSuccess) return bail(SWE_ERR_OOM, "state allocation");
         if (cudaMemsetAsync(c->f[k], 0, c->plane, c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "memset");
@@ -765,7 +771,7 @@ int swe_create(const swe_params* p, swe_ctx** out) {
         }
         if (!rc) rc = encode_map(c, &c->tmB, c->f[6]);
         if (!rc) rc = encode_map(c, &c->tmN, c->f[7]);
-        for (int b = 0; b < 2 && !rc; ++b)
+        for (int b = 0; b < 2 && !rc && c->f[8]; ++b)
             for (int q = 0; q < 3 && !rc; ++q) rc = encode_map(c, &c->tmA[b][q], c->f[8 + 3 * b + q]);
         if (rc) {
             std::string m = g_err;
@@ -812,6 +818,45 @@ int swe_set_terrain(swe_ctx* c, const double* b, const double* n) {
     std::memcpy(c->h_b.data(), b, N * sizeof(double));
     std::vector<int> closed;
     for (size_t k = 0; k < N; ++k)
+        if (c->h_solid[k]) closed.push_back((int)k);
+    rc = apply_beds(c, closed);
+    if (rc) return rc;
+    if (c->has_state) return state_speed(c);
+    return SWE_OK;
+}
+
+int swe_set_terrain_ext(swe_ctx* c, const double* b, const double* n) {
+    if (!c || !b) return fail(SWE_ERR_ARG, "null argument");
+    if (!c->p.ghost_ring) return fail(SWE_ERR_STATE, "swe_set_terrain_ext needs a ghost_ring context");
+    const int nxe = c->p.nx + 2 * PAD, nye = c->p.ny + 2 * PAD;
+    const size_t N = (size_t)nxe * nye;
+    if (!finite_all(b, N) || (n && !finite_all(n, N))) return fail(SWE_ERR_NONFINITE, "terrain not finite");
+    for (int j = 0; j < nye; ++j)
+        for (int i = 0; i < nxe; ++i) {
+            const bool inner = i >= PAD && i < PAD + c->p.nx && j >= PAD && j < PAD + c->p.ny;
+            const double v = b[(size_t)j * nxe + i];
+            if (inner ? std::fabs(v) >= 1e20 : (std::fabs(v) >= 1e20 && v < 1e29))
+                return fail(SWE_ERR_ARG, "|b| must stay below 1e20 (ring cells may be walls, b >= 1e29)");
+        }
+    CK(cudaSetDevice(c->dev));
+    int rc = ensure_staging(c, N * sizeof(double));
+    if (rc) return rc;
+    for (int q = 0; q < 2; ++q) {
+        const double* src = q == 0 ? b : n;
+        void* dst = c->f[6 + q];
+        if (!src) {
+            CK(cudaMemsetAsync(dst, 0, c->plane, c->st));
+            continue;
+        }
+        CK(cudaMemcpyAsync(c->staging, src, N * sizeof(double), cudaMemcpyHostToDevice, c->st));
+        CK(is64(c) ? launch_pack_full<double>(c->staging, (double*)dst, nxe, nye, c->pitch, c->st)
+                   : launch_pack_full<float>(c->staging, (float*)dst, nxe, nye, c->pitch, c->st));
+    }
+    CK(cudaStreamSynchronize(c->st));
+    for (int j = 0; j < c->p.ny; ++j)
+        std::memcpy(&c->h_b[(size_t)j * c->p.nx], &b[(size_t)(j + PAD) * nxe + PAD], c->p.nx * sizeof(double));
+    std::vector<int> closed;
+    for (size_t k = 0; k < c->h_solid.size(); ++k)
         if (c->h_solid[k]) closed.push_back((int)k);
     rc = apply_beds(c, closed);
     if (rc) return rc;
@@ -1473,6 +1518,96 @@ void swe_destroy(swe_ctx* c) {
     cudaFree(c->d_hist);
     if (c->own_stream && c->st) cudaStreamDestroy(c->st);
     delete c;
+}
+
+// ------------------------------------------------------------------ nesting
+
+struct swe_nest {
+    swe_ctx* c = nullptr;  // coarse parent
+    swe_ctx* f = nullptr;  // fine patch (ghost ring)
+    int ix0 = 0, iy0 = 0;
+    cudaEvent_t ev_c = nullptr, ev_f = nullptr;
+};
+
+void swe_nest_destroy(swe_nest* n) {
+    if (!n) return;
+    if (n->c) cudaStreamSynchronize(n->c->st);
+    if (n->f) cudaStreamSynchronize(n->f->st);
+    if (n->ev_c) cudaEventDestroy(n->ev_c);
+    if (n->ev_f) cudaEventDestroy(n->ev_f);
+    delete n;
+}
+
+int swe_nest_create(swe_ctx* c, swe_ctx* f, int32_t ix0, int32_t iy0, swe_nest** out) {
+    if (!c || !f || !out || c == f) return fail(SWE_ERR_ARG, "two distinct contexts and an output pointer needed");
+    *out = nullptr;
+    if (c->p.mode != SWE_FUSED || f->p.mode != SWE_FUSED) return fail(SWE_ERR_ARG, "nested contexts must be SWE_FUSED");
+    if (c->p.precision != f->p.precision) return fail(SWE_ERR_ARG, "nested contexts must share the precision");
+    if (!f->p.ghost_ring || c->p.ghost_ring) return fail(SWE_ERR_ARG, "the fine context needs ghost_ring = 1, the coarse 0");
+    if (f->p.nx % 4 || f->p.ny % 4) return fail(SWE_ERR_ARG, "fine nx and ny must be multiples of 4");
+    if (std::fabs(c->p.dx - 4.0 * f->p.dx) > 1e-12 * c->p.dx) return fail(SWE_ERR_ARG, "fine dx must be coarse dx / 4");
+    if (!(c->p.dt_fixed > 0.0) || std::fabs(f->p.dt_fixed - 0.25 * c->p.dt_fixed) > 1e-12 * c->p.dt_fixed)
+        return fail(SWE_ERR_ARG, "fixed steps needed: fine dt_fixed = coarse dt_fixed / 4");
+    if (ix0 < 3 || iy0 < 3 || ix0 + f->p.nx / 4 + 3 > c->p.nx || iy0 + f->p.ny / 4 + 3 > c->p.ny)
+        return fail(SWE_ERR_ARG, "the patch and 3 coarse cells around it must lie inside the coarse grid");
+    if (c->dev != f->dev) return fail(SWE_ERR_ARG, "nested contexts must be on one device");
+    if (!c->has_state || !f->has_state) return fail(SWE_ERR_STATE, "both contexts need a state");
+    CK(cudaSetDevice(c->dev));
+    int rc = read_ctl(c);
+    if (!rc) rc = read_ctl(f);
+    if (rc) return rc;
+    const double tc = c->ctl_host->t, tf = f->ctl_host->t;
+    if (std::fabs(tc - tf) > 1e-9 * std::max(1.0, std::fabs(tc))) return fail(SWE_ERR_STATE, "the two states are at different times");
+    swe_nest* n = new (std::nothrow) swe_nest();
+    if (!n) return fail(SWE_ERR_OOM, "nest");
+    n->c = c;
+    n->f = f;
+    n->ix0 = ix0;
+    n->iy0 = iy0;
+    if (cudaEventCreateWithFlags(&n->ev_c, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&n->ev_f, cudaEventDisableTiming) != cudaSuccess) {
+        swe_nest_destroy(n);
+        return fail(SWE_ERR_CUDA, "events");
+    }
+    *out = n;
+    return SWE_OK;
+}
+
+int swe_nest_step(swe_nest* n, int32_t ncoarse, swe_step_info* info_c, swe_step_info* info_f) {
+    if (!n || ncoarse < 0) return fail(SWE_ERR_ARG, "null nest or ncoarse < 0");
+    swe_ctx *c = n->c, *f = n->f;
+    CK(cudaSetDevice(c->dev));
+    const bool d = is64(c);
+    for (int k = 0; k < ncoarse; ++k) {
+        int rc = swe_step(c, 1, 0.0, nullptr);
+        if (rc) return rc;
+        CK(cudaEventRecord(n->ev_c, c->st));
+        CK(cudaStreamWaitEvent(f->st, n->ev_c, 0));
+        for (int s = 0; s < 4; ++s) {
+            const double w = 0.25 * s;
+            CK(d ? launch_nest_ring<double>(grid_of<double>(f), f->ctl, grid_of<double>(c), c->ctl, n->ix0, n->iy0, w,
+                                            f->p.eps_dry, f->st)
+                 : launch_nest_ring<float>(grid_of<float>(f), f->ctl, grid_of<float>(c), c->ctl, n->ix0, n->iy0, w,
+                                           (double)(float)f->p.eps_dry, f->st));
+            rc = swe_step(f, 1, 0.0, nullptr);
+            if (rc) return rc;
+        }
+        CK(cudaEventRecord(n->ev_f, f->st));
+        CK(cudaStreamWaitEvent(c->st, n->ev_f, 0));
+        CK(d ? launch_nest_restrict<double>(grid_of<double>(f), f->ctl, grid_of<double>(c), c->ctl, n->ix0, n->iy0, c->st)
+             : launch_nest_restrict<float>(grid_of<float>(f), f->ctl, grid_of<float>(c), c->ctl, n->ix0, n->iy0, c->st));
+        rc = state_speed(c);
+        if (rc) return rc;
+    }
+    int rc = SWE_OK;
+    if (info_c) rc = swe_step(c, 0, 0.0, info_c);
+    if (!rc && info_f) rc = swe_step(f, 0, 0.0, info_f);
+    if (!rc && !info_c && !info_f) {
+        // the next call may change either context from the host
+        CK(cudaEventRecord(n->ev_c, c->st));
+        CK(cudaStreamWaitEvent(f->st, n->ev_c, 0));
+    }
+    return rc;
 }
 
 }  // extern "C"

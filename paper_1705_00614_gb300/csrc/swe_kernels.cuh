@@ -1151,6 +1151,102 @@ __global__ void k_pack(const double* __restrict__ src, T* __restrict__ dst, int 
     }
 }
 
+// FP64 host layout of the whole padded extent (ring included) -> padded
+// field.
+template <class T>
+__global__ void k_pack_full(const double* __restrict__ src, T* __restrict__ dst, int nxe, int pitch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i < nxe) dst[(size_t)j * pitch + i] = (T)src[(size_t)j * nxe + i];
+}
+
+__device__ __forceinline__ int floor_div4(int i) { return i >= 0 ? i / 4 : -((3 - i) / 4); }
+
+// Two-level grid system (Sec. 2.2, Fig. 1): the ghost ring of a fine patch
+// (4x finer, its interior cell (0, 0) in coarse cell (ix0, iy0)) from the
+// coarse grid, at the fraction w of the coarse step just taken (0: its
+// start, the other coarse buffer; 1: its end, the current one).  Each ring
+// cell takes the coarse cell containing its centre: the coarse state is
+// interpolated linearly in time, the fine depth is the coarse free surface
+// above the fine bed (so still water stays still) and the velocity is the
+// coarse one.  Dry coarse cells and walls give dry ghosts.
+template <class T>
+__global__ void k_nest_ring(const Grid<T> f, const Ctl* __restrict__ fctl, const Grid<T> c, const Ctl* __restrict__ cctl,
+                            int ix0, int iy0, double w, double eps) {
+    const int nxe = f.nx + 2 * PAD, nye = f.ny + 2 * PAD;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)nxe * nye) return;
+    const int ip = (int)(e % nxe), jp = (int)(e / nxe);
+    const int i = ip - PAD, j = jp - PAD;
+    if (i >= 0 && i < f.nx && j >= 0 && j < f.ny) return;  // interior
+    const int xc = ix0 + floor_div4(i), yc = iy0 + floor_div4(j);
+    const int cnew = (int)(*(volatile const long long*)&cctl->step & 1), cold = cnew ^ 1;
+    const int fb = (int)(*(volatile const long long*)&fctl->step & 1);
+    const size_t kc = (size_t)(yc + PAD) * c.pitch + (size_t)(xc + PAD);
+    const size_t kf = (size_t)jp * f.pitch + (size_t)ip;
+    const double Hc = (1.0 - w) * (double)c.H[cold][kc] + w * (double)c.H[cnew][kc];
+    const double Qxc = (1.0 - w) * (double)c.Qx[cold][kc] + w * (double)c.Qx[cnew][kc];
+    const double Qyc = (1.0 - w) * (double)c.Qy[cold][kc] + w * (double)c.Qy[cnew][kc];
+    const double bc = (double)c.b[kc], bf = (double)f.b[kf];
+    double hg = 0.0, qx = 0.0, qy = 0.0;
+    if (Hc > eps && bc < WALL_TEST && bf < WALL_TEST) {
+        const double eta = Hc + bc;
+        hg = eta - bf > 0.0 ? eta - bf : 0.0;
+        qx = hg * (Qxc / Hc);
+        qy = hg * (Qyc / Hc);
+    }
+    f.H[fb][kf] = (T)hg;
+    f.Qx[fb][kf] = (T)qx;
+    f.Qy[fb][kf] = (T)qy;
+}
+
+// Feedback of a fine patch: each coarse cell it covers takes the means of
+// its 4 x 4 fine cells' H, Qx, Qy (summed row by row in FP64), which keeps
+// the patch's water volume and momentum.
+template <class T>
+__global__ void k_nest_restrict(const Grid<T> f, const Ctl* __restrict__ fctl, const Grid<T> c,
+                                const Ctl* __restrict__ cctl, int ix0, int iy0) {
+    const int ncx = f.nx / 4, ncy = f.ny / 4;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ncx * ncy) return;
+    const int u = e % ncx, v = e / ncx;
+    const int fb = (int)(*(volatile const long long*)&fctl->step & 1);
+    const int cb = (int)(*(volatile const long long*)&cctl->step & 1);
+    double sh = 0.0, sx = 0.0, sy = 0.0;
+    for (int dy = 0; dy < 4; ++dy)
+        for (int dx = 0; dx < 4; ++dx) {
+            const size_t k = (size_t)(4 * v + dy + PAD) * f.pitch + (size_t)(4 * u + dx + PAD);
+            sh += (double)f.H[fb][k];
+            sx += (double)f.Qx[fb][k];
+            sy += (double)f.Qy[fb][k];
+        }
+    const size_t kc = (size_t)(iy0 + v + PAD) * c.pitch + (size_t)(ix0 + u + PAD);
+    c.H[cb][kc] = (T)(sh / 16.0);
+    c.Qx[cb][kc] = (T)(sx / 16.0);
+    c.Qy[cb][kc] = (T)(sy / 16.0);
+}
+
+template <class T>
+cudaError_t launch_pack_full(const double* src, T* dst, int nxe, int nye, int pitch, cudaStream_t st) {
+    k_pack_full<T><<<dim3((nxe + 255) / 256, nye), 256, 0, st>>>(src, dst, nxe, pitch);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_nest_ring(const Grid<T>& f, const Ctl* fctl, const Grid<T>& c, const Ctl* cctl, int ix0, int iy0,
+                             double w, double eps, cudaStream_t st) {
+    const long long n = (long long)(f.nx + 2 * PAD) * (f.ny + 2 * PAD);
+    k_nest_ring<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, fctl, c, cctl, ix0, iy0, w, eps);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_nest_restrict(const Grid<T>& f, const Ctl* fctl, const Grid<T>& c, const Ctl* cctl, int ix0, int iy0,
+                                 cudaStream_t st) {
+    const int n = (f.nx / 4) * (f.ny / 4);
+    k_nest_restrict<T><<<(n + 255) / 256, 256, 0, st>>>(f, fctl, c, cctl, ix0, iy0);
+    return cudaGetLastError();
+}
+
 template <class T>
 __global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, int nx, int ny, int pitch) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
@@ -1209,6 +1305,11 @@ cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cud
     template cudaError_t launch_unpack<T>(const T*, double*, int, int, int, cudaStream_t);           \
     template cudaError_t launch_scatter<T>(T*, const int*, const double*, int, cudaStream_t);        \
     template cudaError_t launch_fill_bed<T>(T*, int, int, int, cudaStream_t);                        \
+    template cudaError_t launch_pack_full<T>(const double*, T*, int, int, int, cudaStream_t);       \
+    template cudaError_t launch_nest_ring<T>(const Grid<T>&, const Ctl*, const Grid<T>&, const Ctl*, int, int, \
+                                             double, double, cudaStream_t);                         \
+    template cudaError_t launch_nest_restrict<T>(const Grid<T>&, const Ctl*, const Grid<T>&, const Ctl*, int, \
+                                                 int, cudaStream_t);                                \
     template size_t fused_smem_bytes<T>();
 
 }  // namespace swe

@@ -170,6 +170,18 @@ template <class T>
 cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cudaStream_t st);
 template <class T>
 cudaError_t launch_fill_bed(T* b, int nx, int ny, int pitch, cudaStream_t st);
+// FP64 row-major [ny + 2 PAD][nx + 2 PAD] -> the whole padded field.
+template <class T>
+cudaError_t launch_pack_full(const double* src, T* dst, int nxe, int nye, int pitch, cudaStream_t st);
+// Two-level nesting: ghost ring of the fine patch from the coarse grid at
+// the fraction w of the last coarse step; 4x4 restriction of the patch onto
+// the coarse cells it covers.
+template <class T>
+cudaError_t launch_nest_ring(const Grid<T>& f, const Ctl* fctl, const Grid<T>& c, const Ctl* cctl, int ix0, int iy0,
+                             double w, double eps, cudaStream_t st);
+template <class T>
+cudaError_t launch_nest_restrict(const Grid<T>& f, const Ctl* fctl, const Grid<T>& c, const Ctl* cctl, int ix0, int iy0,
+                                 cudaStream_t st);
 template <class T>
 size_t fused_smem_bytes();
 // Learned-closure kernels (swe_cnn.cu).

@@ -26,7 +26,8 @@ API = ["swe_params_default", "swe_create", "swe_set_terrain", "swe_set_state", "
        "swe_batch_create", "swe_batch_set_gate_events", "swe_batch_step", "swe_batch_autotune",
        "swe_batch_destroy", "swe_cnn_create", "swe_cnn_num_params", "swe_cnn_set_params", "swe_cnn_get_params",
        "swe_cnn_forward", "swe_cnn_gradients", "swe_cnn_train_step", "swe_cnn_destroy", "swe_restrict_state",
-       "swe_closure_features", "swe_closure_targets", "swe_closure_attach", "swe_step_closed"]
+       "swe_closure_features", "swe_closure_targets", "swe_closure_attach", "swe_step_closed",
+       "swe_set_terrain_ext", "swe_nest_create", "swe_nest_step", "swe_nest_destroy"]
 CNN_CHANNELS = (5, 32, 32, 32, 3)
 SWE_PAD = 10
 NOALLOC_MAX_ITEMS = 7000
@@ -49,7 +50,7 @@ class Params(ctypes.Structure):
                 ("wind_x", ctypes.c_double), ("wind_y", ctypes.c_double), ("c_a", ctypes.c_double),
                 ("rho_air_over_rho", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("tile_w", ctypes.c_int32), ("seg_h", ctypes.c_int32),
-                ("skip_dry", ctypes.c_int32)]
+                ("skip_dry", ctypes.c_int32), ("ghost_ring", ctypes.c_int32)]
 
 
 class StepInfo(ctypes.Structure):
@@ -139,9 +140,16 @@ def load(path=None):
                        ("swe_closure_features", [ctypes.c_void_p, _fp, ctypes.c_void_p]),
                        ("swe_closure_targets", [ctypes.c_void_p, ctypes.c_void_p, _fp, ctypes.c_void_p]),
                        ("swe_closure_attach", [ctypes.c_void_p, ctypes.c_void_p, _fp]),
-                       ("swe_step_closed", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(StepInfo)])):
+                       ("swe_step_closed", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(StepInfo)]),
+                       ("swe_set_terrain_ext", [ctypes.c_void_p, _dp, _dp]),
+                       ("swe_nest_create", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.POINTER(ctypes.c_void_p)]),
+                       ("swe_nest_step", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(StepInfo),
+                                          ctypes.POINTER(StepInfo)])):
         getattr(L, name).restype = ctypes.c_int
         getattr(L, name).argtypes = args
+    L.swe_nest_destroy.restype = None
+    L.swe_nest_destroy.argtypes = [ctypes.c_void_p]
     L.swe_step_f32_noalloc.restype = ctypes.c_int
     L.swe_step_f32_noalloc.argtypes = [ctypes.POINTER(Params)] + [ctypes.c_void_p] * 8 + [
         ctypes.c_int64, ctypes.c_double, ctypes.c_double, ctypes.POINTER(StepInfo)]
@@ -166,7 +174,7 @@ def _ptr(a):
     return a.ctypes.data_as(_dp) if a is not None else None
 
 
-def make_params(params, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False):
+def make_params(params, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False, ghost_ring=False):
     """swe_params from an inputs.Params-like object."""
     L = load()
     p = Params()
@@ -180,6 +188,7 @@ def make_params(params, precision="f32", mode="fused", stream=None, seg_h=0, ski
     p.cuda_stream = stream
     p.seg_h = seg_h
     p.skip_dry = 1 if skip_dry else 0
+    p.ghost_ring = 1 if ghost_ring else 0
     return p
 
 
@@ -197,9 +206,10 @@ def step_f32_noalloc(params, H, Qx, Qy, b, n, H_out, Qx_out, Qy_out, pitch, t, m
 class Solver:
     """One grid: a libswe context.  Arrays are [ny, nx] float64 on the host."""
 
-    def __init__(self, params, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False):
+    def __init__(self, params, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False,
+                 ghost_ring=False):
         self.L = load()
-        p = make_params(params, precision, mode, stream, seg_h, skip_dry)
+        p = make_params(params, precision, mode, stream, seg_h, skip_dry, ghost_ring)
         self.params = params
         self.nx, self.ny = params.nx, params.ny
         h = ctypes.c_void_p()
@@ -207,8 +217,9 @@ class Solver:
         self.h = h
 
     @classmethod
-    def from_problem(cls, prob, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False):
-        s = cls(prob.params, precision, mode, stream, seg_h, skip_dry)
+    def from_problem(cls, prob, precision="f32", mode="fused", stream=None, seg_h=0, skip_dry=False,
+                     ghost_ring=False):
+        s = cls(prob.params, precision, mode, stream, seg_h, skip_dry, ghost_ring)
         s.set_terrain(prob.b, prob.n_manning)
         if len(prob.sources):
             s.set_sources(prob.sources)
@@ -239,6 +250,13 @@ class Solver:
         b = _f64(b)
         n = None if n is None else _f64(n)
         _check(self.L, self.L.swe_set_terrain(self.h, _ptr(b), _ptr(n)))
+
+    def set_terrain_ext(self, b_ext, n_ext=None):
+        """Bed and Manning n over the padded extent [ny + 2 PAD][nx + 2 PAD]
+        (ghost_ring contexts)."""
+        b_ext = _f64(b_ext)
+        n_ext = _f64(n_ext) if n_ext is not None else None
+        _check(self.L, self.L.swe_set_terrain_ext(self.h, _ptr(b_ext), _ptr(n_ext)))
 
     def set_state(self, H, Qx, Qy, t=0.0):
         H, Qx, Qy = _f64(H), _f64(Qx), _f64(Qy)
@@ -327,6 +345,41 @@ class Solver:
         info = StepInfo()
         _check(self.L, self.L.swe_step_closed(self.h, int(nsteps), ctypes.byref(info) if report else None))
         return info.as_dict() if report else None
+
+
+class Nest:
+    """A fine patch (ghost_ring Solver) nested 4:1 in a coarse Solver with
+    its interior cell (0, 0) in coarse cell (ix0, iy0) (swe_nest_*)."""
+
+    def __init__(self, coarse, fine, ix0, iy0):
+        self.L = load()
+        self.coarse, self.fine = coarse, fine
+        h = ctypes.c_void_p()
+        _check(self.L, self.L.swe_nest_create(coarse.h, fine.h, int(ix0), int(iy0), ctypes.byref(h)))
+        self.h = h
+
+    def step(self, ncoarse=1, report=True):
+        ic, jf = StepInfo(), StepInfo()
+        _check(self.L, self.L.swe_nest_step(self.h, int(ncoarse), ctypes.byref(ic) if report else None,
+                                            ctypes.byref(jf) if report else None))
+        return (ic.as_dict(), jf.as_dict()) if report else None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.swe_nest_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 class Batch:

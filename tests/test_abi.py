@@ -48,8 +48,9 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "{HDR}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu\\n", sizeof(swe_params), offsetof(swe_params, dx),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(swe_params), offsetof(swe_params, dx),
          offsetof(swe_params, cuda_stream), offsetof(swe_params, seg_h), offsetof(swe_params, skip_dry),
+         offsetof(swe_params, ghost_ring),
          sizeof(swe_step_info),
          offsetof(swe_step_info, wet_cells));
   return 0;
@@ -59,7 +60,8 @@ int main(void) {{
     subprocess.check_call(["gcc", "-o", str(exe), str(src)])
     vals = list(map(int, subprocess.check_output([str(exe)]).split()))
     assert vals == [ctypes.sizeof(swe.Params), swe.Params.dx.offset, swe.Params.cuda_stream.offset,
-                    swe.Params.seg_h.offset, swe.Params.skip_dry.offset, ctypes.sizeof(swe.StepInfo),
+                    swe.Params.seg_h.offset, swe.Params.skip_dry.offset, swe.Params.ghost_ring.offset,
+                    ctypes.sizeof(swe.StepInfo),
                     swe.StepInfo.wet_cells.offset]
 
 
@@ -78,7 +80,9 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
     for bad in ({"nx": 0, "ny": 4, "dx": 1.0}, {"nx": 4, "ny": 4, "dx": -1.0},
                 {"nx": 4, "ny": 4, "dx": 1.0, "cfl": 1.5}, {"nx": 4, "ny": 4, "dx": 1.0, "precision": 7},
                 {"nx": 4, "ny": 4, "dx": 1.0, "skip_dry": 2},
-                {"nx": 4, "ny": 4, "dx": 1.0, "skip_dry": 1, "mode": swe.SWE_STAGED}):
+                {"nx": 4, "ny": 4, "dx": 1.0, "skip_dry": 1, "mode": swe.SWE_STAGED},
+                {"nx": 4, "ny": 4, "dx": 1.0, "ghost_ring": 1, "mode": swe.SWE_STAGED},
+                {"nx": 4, "ny": 4, "dx": 1.0, "ghost_ring": 1, "skip_dry": 1}):
         q = swe.Params()
         lib.swe_params_default(ctypes.byref(q))
         for k, v in bad.items():
