@@ -315,6 +315,71 @@ def run_closure(args, torch, swe, stream, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_nest(args, torch, swe, stream, rank, world):
+    """Two-level nesting (nest-<n>sq): a flooded n^2 floodplain at dx = 20 m
+    with an n^2 patch at 5 m over its central (n/4)^2 coarse cells; K nested
+    coarse steps (each: one coarse step, four fine sub-steps with ghost
+    fills, feedback) timed with CUDA events.  value counts every cell update
+    of both levels."""
+    from paper_1705_00614_gb300 import closure as CL
+    n = int(args.workload.split("-")[1].replace("sq", ""))
+    # one fine terrain under both levels: the coarse bed is its 4 x 4 means
+    # over the patch and the coarse generator's elsewhere
+    base = I.floodplain(n, 20.0, 2031, 2032, nsrc=1)
+    eta0 = float(np.median(base.b))
+    ix0 = iy0 = 3 * n // 8
+    fine_full = I.floodplain(n + 2 * 10, 5.0, 2033, 2034, nsrc=1)
+    bf_ext = fine_full.b - np.median(fine_full.b) + eta0  # fine relief around the same water level
+    nf_ext = fine_full.n_manning
+    bf = bf_ext[10:10 + n, 10:10 + n]
+    bc = base.b.copy()
+    bc[iy0:iy0 + n // 4, ix0:ix0 + n // 4] = bf.reshape(n // 4, 4, n // 4, 4).mean(axis=(1, 3))
+    Hc = np.maximum(0.0, eta0 - bc)
+    z = np.zeros_like(Hc)
+    pc = I.Params(**{**base.params.__dict__, "dt_fixed": 0.2})
+    coarse = I.Problem("nest-coarse", pc, bc, base.n_manning, Hc, z, z.copy(), I.Sources.empty()).to_f32_values()
+    Hf = np.maximum(0.0, eta0 - bf)
+    zf = np.zeros_like(Hf)
+    pf = I.Params(**{**fine_full.params.__dict__, "nx": n, "ny": n, "dt_fixed": 0.05})
+    fine = I.Problem("nest-fine", pf, bf, nf_ext[10:10 + n, 10:10 + n], Hf, zf, zf.copy(),
+                     I.Sources.empty()).to_f32_values()
+    c = swe.Solver.from_problem(coarse, args.precision, stream=stream.cuda_stream)
+    f = swe.Solver.from_problem(fine, args.precision, stream=stream.cuda_stream, ghost_ring=True)
+    f.set_terrain_ext(np.asarray(bf_ext, np.float32).astype(np.float64),
+                      np.asarray(nf_ext, np.float32).astype(np.float64))
+    f.set_state(fine.H, fine.Qx, fine.Qy, 0.0)
+    nest = swe.Nest(c, f, ix0, iy0)
+    for _ in range(args.warmup):
+        nest.step(1, report=False)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        nest.step(args.steps, report=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ic, jf = nest.step(0)
+    nest.close()
+    c.close()
+    f.close()
+    updates = n * n + 4 * n * n
+    if rank == 0:
+        line = {"metric": "nested Gcell-updates/s (coarse + 4 fine sub-steps)",
+                "value": world * updates / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
+                "config": {"workload": args.workload, "coarse": f"{n}^2 dx 20 m", "patch": f"{n}^2 dx 5 m",
+                           "patch_origin_coarse": [ix0, iy0], "cell_updates_per_step": updates,
+                           "coarse_wet_end": ic["wet_cells"], "fine_wet_end": jf["wet_cells"],
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": None, "cpu_baseline": None, "e2e": None, "gpu_launches": None,
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+
+
 def crop(prob, y0, x0, n):
     s = prob.sources
     keep = (s.ix >= x0) & (s.ix < x0 + n) & (s.iy >= y0) & (s.iy < y0 + n)
@@ -493,6 +558,14 @@ def main():
     from paper_1705_00614_gb300 import build as B
     from paper_1705_00614_gb300 import swe
     B.build()
+
+    if args.workload.startswith("nest-"):
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        run_nest(args, torch, swe, stream, rank, world)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
 
     if args.workload.startswith("closure-"):
         stream = torch.cuda.Stream()
