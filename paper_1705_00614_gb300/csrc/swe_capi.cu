@@ -1596,11 +1596,16 @@ int swe_nest_step(swe_nest* n, int32_t ncoarse, swe_step_info* info_c, swe_step_
         CK(cudaStreamWaitEvent(c->st, n->ev_f, 0));
         CK(d ? launch_nest_restrict<double>(grid_of<double>(f), f->ctl, grid_of<double>(c), c->ctl, n->ix0, n->iy0, c->st)
              : launch_nest_restrict<float>(grid_of<float>(f), f->ctl, grid_of<float>(c), c->ctl, n->ix0, n->iy0, c->st));
-        rc = state_speed(c);
-        if (rc) return rc;
+        // the coarse state changed under the patch: speed and stored
+        // accelerations of those cells and their neighbours
+        const int i0 = n->ix0 - 1, j0 = n->iy0 - 1, ni = f->p.nx / 4 + 2, nj = f->p.ny / 4 + 2;
+        CK(d ? launch_state_speed_region<double>(staged_args<double>(c), i0, j0, ni, nj, c->st)
+             : launch_state_speed_region<float>(staged_args<float>(c), i0, j0, ni, nj, c->st));
     }
     int rc = SWE_OK;
-    if (info_c) rc = swe_step(c, 0, 0.0, info_c);
+    // exact mass, wet cells and speed of the coarse state for the report
+    if (info_c && ncoarse > 0) rc = state_speed(c);
+    if (!rc && info_c) rc = swe_step(c, 0, 0.0, info_c);
     if (!rc && info_f) rc = swe_step(f, 0, 0.0, info_f);
     if (!rc && !info_c && !info_f) {
         // the next call may change either context from the host

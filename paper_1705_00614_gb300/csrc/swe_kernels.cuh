@@ -983,10 +983,12 @@ __global__ void ks_final(const StagedArgs<T> a) {
 // Signal speed (and mass) of the state in buffer `which` (0: current,
 // 1: next); atomicMax into the smax slot of that state's step parity.
 // Where the grid stores accelerations, also writes them for that state.
+// (i0, j0): origin of the cells the launch covers (a region of the grid);
+// parts = 0 leaves the per-block partial sums alone.
 template <class T>
-__global__ void ks_speed(const StagedArgs<T> a, int which) {
+__global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 0, int parts = 1) {
     __shared__ double red[8];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x, j = j0 + blockIdx.y * blockDim.y + threadIdx.y;
     const int buf = ctl_buf(a.ctl) ^ which;
     double v = 0.0, mass = 0.0, wet = 0.0;
     bool bad = false;
@@ -1042,7 +1044,7 @@ __global__ void ks_speed(const StagedArgs<T> a, int which) {
         const int slot = (int)((*(volatile const long long*)&a.ctl->step + which) & 1);
         atomicMax(&a.ctl->smax[slot], (unsigned long long)__double_as_longlong(bm));
         if (anybad) atomicOr(&a.ctl->err, (unsigned)ERR_NONFINITE);
-        if (which == 0) {
+        if (which == 0 && parts) {
             a.parts[bl].mass = bs;
             a.parts[bl].wet = (int)bw;
         }
@@ -1120,6 +1122,17 @@ cudaError_t launch_staged(const StagedArgs<T>& a, cudaStream_t st) {
 
 static __global__ void k_zero_cur_slot(Ctl* ctl) { ctl->smax[ctl->step & 1] = 0ull; }
 
+// Signal speed and stored accelerations of the current state over the cells
+// [i0, i0 + ni) x [j0, j0 + nj) only (after a change confined to them): the
+// step's speed slot takes the max with it, which can only over-estimate.
+template <class T>
+cudaError_t launch_state_speed_region(const StagedArgs<T>& a, int i0, int j0, int ni, int nj, cudaStream_t st) {
+    const dim3 blk(32, 8);
+    const dim3 grd((ni + 31) / 32, (nj + 7) / 8);
+    ks_speed<T><<<grd, blk, 0, st>>>(a, 0, i0, j0, 0);
+    return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st) {
     const dim3 blk(32, 8);
@@ -1172,12 +1185,24 @@ __device__ __forceinline__ int floor_div4(int i) { return i >= 0 ? i / 4 : -((3 
 template <class T>
 __global__ void k_nest_ring(const Grid<T> f, const Ctl* __restrict__ fctl, const Grid<T> c, const Ctl* __restrict__ cctl,
                             int ix0, int iy0, double w, double eps) {
-    const int nxe = f.nx + 2 * PAD, nye = f.ny + 2 * PAD;
+    // ring cells only: PAD full rows above and below, PAD columns left and
+    // right of the interior rows
+    const int nxe = f.nx + 2 * PAD;
     const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= (long long)nxe * nye) return;
-    const int ip = (int)(e % nxe), jp = (int)(e / nxe);
+    const long long nband = (long long)PAD * nxe, nside = (long long)f.ny * PAD;
+    if (e >= 2 * nband + 2 * nside) return;
+    int ip, jp;
+    if (e < 2 * nband) {
+        const int r = (int)(e / nxe);
+        ip = (int)(e % nxe);
+        jp = r < PAD ? r : f.ny + r;  // rows 0..PAD-1 and ny+PAD..ny+2PAD-1
+    } else {
+        const long long q = e - 2 * nband;
+        const int r = (int)(q / (2 * PAD)), k = (int)(q % (2 * PAD));
+        jp = PAD + r;
+        ip = k < PAD ? k : f.nx + k;  // columns 0..PAD-1 and nx+PAD..nx+2PAD-1
+    }
     const int i = ip - PAD, j = jp - PAD;
-    if (i >= 0 && i < f.nx && j >= 0 && j < f.ny) return;  // interior
     const int xc = ix0 + floor_div4(i), yc = iy0 + floor_div4(j);
     const int cnew = (int)(*(volatile const long long*)&cctl->step & 1), cold = cnew ^ 1;
     const int fb = (int)(*(volatile const long long*)&fctl->step & 1);
@@ -1200,8 +1225,8 @@ __global__ void k_nest_ring(const Grid<T> f, const Ctl* __restrict__ fctl, const
 }
 
 // Feedback of a fine patch: each coarse cell it covers takes the means of
-// its 4 x 4 fine cells' H, Qx, Qy (summed row by row in FP64), which keeps
-// the patch's water volume and momentum.
+// its 4 x 4 fine cells' H, Qx, Qy (summed row by row in the state
+// precision), which keeps the patch's water volume and momentum.
 template <class T>
 __global__ void k_nest_restrict(const Grid<T> f, const Ctl* __restrict__ fctl, const Grid<T> c,
                                 const Ctl* __restrict__ cctl, int ix0, int iy0) {
@@ -1211,18 +1236,18 @@ __global__ void k_nest_restrict(const Grid<T> f, const Ctl* __restrict__ fctl, c
     const int u = e % ncx, v = e / ncx;
     const int fb = (int)(*(volatile const long long*)&fctl->step & 1);
     const int cb = (int)(*(volatile const long long*)&cctl->step & 1);
-    double sh = 0.0, sx = 0.0, sy = 0.0;
+    T sh = T(0), sx = T(0), sy = T(0);
     for (int dy = 0; dy < 4; ++dy)
         for (int dx = 0; dx < 4; ++dx) {
             const size_t k = (size_t)(4 * v + dy + PAD) * f.pitch + (size_t)(4 * u + dx + PAD);
-            sh += (double)f.H[fb][k];
-            sx += (double)f.Qx[fb][k];
-            sy += (double)f.Qy[fb][k];
+            sh += f.H[fb][k];
+            sx += f.Qx[fb][k];
+            sy += f.Qy[fb][k];
         }
     const size_t kc = (size_t)(iy0 + v + PAD) * c.pitch + (size_t)(ix0 + u + PAD);
-    c.H[cb][kc] = (T)(sh / 16.0);
-    c.Qx[cb][kc] = (T)(sx / 16.0);
-    c.Qy[cb][kc] = (T)(sy / 16.0);
+    c.H[cb][kc] = sh * T(0.0625);
+    c.Qx[cb][kc] = sx * T(0.0625);
+    c.Qy[cb][kc] = sy * T(0.0625);
 }
 
 template <class T>
@@ -1234,7 +1259,7 @@ cudaError_t launch_pack_full(const double* src, T* dst, int nxe, int nye, int pi
 template <class T>
 cudaError_t launch_nest_ring(const Grid<T>& f, const Ctl* fctl, const Grid<T>& c, const Ctl* cctl, int ix0, int iy0,
                              double w, double eps, cudaStream_t st) {
-    const long long n = (long long)(f.nx + 2 * PAD) * (f.ny + 2 * PAD);
+    const long long n = 2LL * PAD * (f.nx + 2 * PAD) + 2LL * PAD * f.ny;
     k_nest_ring<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, fctl, c, cctl, ix0, iy0, w, eps);
     return cudaGetLastError();
 }
@@ -1301,6 +1326,7 @@ cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cud
     template cudaError_t launch_fused_batch<T>(const BatchArgs<T>&, int, cudaStream_t);              \
     template cudaError_t launch_staged<T>(const StagedArgs<T>&, cudaStream_t);                       \
     template cudaError_t launch_state_speed<T>(const StagedArgs<T>&, cudaStream_t);                  \
+    template cudaError_t launch_state_speed_region<T>(const StagedArgs<T>&, int, int, int, int, cudaStream_t); \
     template cudaError_t launch_pack<T>(const double*, T*, int, int, int, cudaStream_t, unsigned*, int); \
     template cudaError_t launch_unpack<T>(const T*, double*, int, int, int, cudaStream_t);           \
     template cudaError_t launch_scatter<T>(T*, const int*, const double*, int, cudaStream_t);        \

@@ -159,6 +159,10 @@ cudaError_t launch_staged(const StagedArgs<T>& a, cudaStream_t st);
 // Signal speed and mass of the current state (the first step's K3).
 template <class T>
 cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st);
+// The same over a region of the grid, without the mass report: the speed
+// slot takes the max with the region's (an over-estimate at most).
+template <class T>
+cudaError_t launch_state_speed_region(const StagedArgs<T>& a, int i0, int j0, int ni, int nj, cudaStream_t st);
 // FP64 row-major [ny][nx] staging -> padded field of type T, and back.
 template <class T>
 cudaError_t launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cudaStream_t st,
