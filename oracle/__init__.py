@@ -45,7 +45,8 @@ class _Params(ctypes.Structure):
                 ("dt_max", ctypes.c_double), ("dt_fixed", ctypes.c_double),
                 ("t_end", ctypes.c_double), ("nu", ctypes.c_double), ("f", ctypes.c_double),
                 ("wx", ctypes.c_double), ("wy", ctypes.c_double), ("ca", ctypes.c_double),
-                ("ra", ctypes.c_double)]
+                ("ra", ctypes.c_double), ("rain", ctypes.c_double), ("evap", ctypes.c_double),
+                ("infil", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -109,7 +110,8 @@ def _params(p, t_end=0.0):
     return _Params(int(p.nx), int(p.ny), float(p.dx), float(p.g), float(p.cfl), float(p.eps),
                    float(p.dt_max), float(p.dt_fixed), float(t_end), float(p.nu),
                    float(p.coriolis_f), float(p.wind_x), float(p.wind_y), float(p.c_a),
-                   float(p.rho_air_over_rho))
+                   float(p.rho_air_over_rho), float(getattr(p, "rain_rate", 0.0)),
+                   float(getattr(p, "evap_rate", 0.0)), float(getattr(p, "infil_rate", 0.0)))
 
 
 class _Bound:

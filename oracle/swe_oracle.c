@@ -50,6 +50,9 @@ typedef struct {
     double wx, wy;  /* wind velocity W (Eq. 4) */
     double ca;      /* C_a (Eq. 4) */
     double ra;      /* rho_a / rho (Eq. 4) */
+    double rain;    /* distributed sources of Eq. 1 (m/s, every non-wall */
+    double evap;    /*   cell): rainfall adds water without momentum; */
+    double infil;   /*   evaporation and infiltration take water with its velocity */
 } orc_params;
 
 typedef struct {
@@ -327,9 +330,16 @@ int orc_step(const orc_params* p, const double* b, const double* nm, const unsig
         /* particle mass plus source; inflow carries V, a drain takes U~ */
         double ts = tau * sig[k];
         ht[k] = dmax(0.0, H[k] + ts);
-        src_sum += ht[k] - H[k];
         qtx[k] = H[k] * utx[k] + (sig[k] > 0.0 ? ts * vxc[k] : ts * utx[k]);
         qty[k] = H[k] * uty[k] + (sig[k] > 0.0 ? ts * vyc[k] : ts * uty[k]);
+        /* rain, evaporation and infiltration (Eq. 1 sigma) on every non-wall cell */
+        if (!solid[k] && (p->rain != 0.0 || p->evap != 0.0 || p->infil != 0.0)) {
+            double loss = p->evap + p->infil;
+            ht[k] = dmax(0.0, (H[k] + ts) + tau * (p->rain - loss));
+            qtx[k] = qtx[k] - tau * loss * utx[k];
+            qty[k] = qty[k] - tau * loss * uty[k];
+        }
+        src_sum += ht[k] - H[k];
         wt[k] = (!solid[k] && ht[k] > eps);
         upx[k] = wt[k] ? qtx[k] / ht[k] : 0.0;
         upy[k] = wt[k] ? qty[k] / ht[k] : 0.0;

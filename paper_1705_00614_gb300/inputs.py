@@ -169,6 +169,11 @@ class Params:
     wind_y: float = 0.0
     c_a: float = 0.0
     rho_air_over_rho: float = 1.225e-3
+    # distributed sources of Eq. 1 (m/s, uniform over the grid): rainfall,
+    # evaporation, infiltration
+    rain_rate: float = 0.0
+    evap_rate: float = 0.0
+    infil_rate: float = 0.0
 
 
 @dataclasses.dataclass

@@ -2,7 +2,8 @@
 
 Each case plants one slip in a copy of the oracle source (a flipped sign, a
 wrong factor, a swapped index, a dropped term), builds it with gcc on the
-CPU, and checks that at least one pin of test_oracle_pins.py fails against
+CPU, and checks that at least one pin of test_oracle_pins.py or
+test_oracle_rain.py fails against
 the mutated build.  Mistakes are planted only in the oracle, never in the
 CUDA path.
 """
@@ -13,6 +14,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as P
+from tests import test_oracle_rain as R
 
 _SRC = os.path.join(os.path.dirname(oracle.__file__), "swe_oracle.c")
 
@@ -58,6 +60,13 @@ MUTANTS = [
      ["test_source_volume_matches_hydrograph_integral"]),
     ("drain volume unclamped", "ht[k] = dmax(0.0, H[k] + ts);", "ht[k] = H[k] + ts;",
      ["test_drain_on_dry_ground_removes_nothing"]),
+    ("evaporation adds water", "ht[k] = dmax(0.0, (H[k] + ts) + tau * (p->rain - loss));",
+     "ht[k] = dmax(0.0, (H[k] + ts) + tau * (p->rain + loss));",
+     ["test_evaporation_and_infiltration_drain_still_water_until_dry"]),
+    ("losses leave the momentum", "qtx[k] = qtx[k] - tau * loss * utx[k];", "qtx[k] = qtx[k];",
+     ["test_losses_keep_the_velocity_and_rain_slows_the_flow"]),
+    ("rain on gates", "if (!solid[k] && (p->rain != 0.0", "if ((p->rain != 0.0",
+     ["test_rain_volume_budget_over_terrain_with_gates"]),
 ]
 
 
@@ -79,7 +88,7 @@ def test_pins_catch_mutant(name, old, new, pins, tmpdir_mod, monkeypatch):
     caught = []
     for pin in pins:
         try:
-            getattr(P, pin)(*([1] if pin == "test_thacker_bowl" else []))
+            (getattr(P, pin, None) or getattr(R, pin))(*([1] if pin == "test_thacker_bowl" else []))
         except (AssertionError, RuntimeError, FloatingPointError, ValueError, ZeroDivisionError):
             caught.append(pin)
             break
