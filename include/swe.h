@@ -92,15 +92,25 @@ typedef struct {
                               cell.  Never applied to swe_step_closed.
                               Off by default (throughput then does not depend
                               on the wet fraction). */
-    int32_t ghost_ring;    /* fused mode, 0 or 1: 0 = the SWE_PAD cells around the
-                              grid are reflective walls; 1 = they are ghost cells
-                              whose terrain the caller sets with
+    int32_t ghost_ring;    /* fused mode, 0, 1 or 2: 0 = the SWE_PAD cells around
+                              the grid are reflective walls; 1 = they are ghost
+                              cells whose terrain the caller sets with
                               swe_set_terrain_ext and whose state a nest
                               (swe_nest_*) fills from a coarser grid before
                               every step (a ghost cell that is never filled is
-                              dry ground, through which water can leave).  Such
-                              a context evaluates the forces of every step in
-                              the kernel instead of storing them. */
+                              dry ground, through which water can leave);
+                              2 = open boundary: before every step each ghost
+                              cell whose bed is below 1e29 takes the state of
+                              the nearest interior cell (zero gradient), so
+                              flow and waves leave the grid; ghosts with a bed
+                              of 1e29 or more stay walls (set the ring terrain,
+                              e.g. edge-extended, with swe_set_terrain_ext).
+                              Contexts with 1 or 2 evaluate the forces of every
+                              step in the kernel instead of storing them. */
+    /* Distributed sources of Eq. 1 on every non-wall cell, m/s, >= 0: rain
+     * adds water at rest; evaporation and infiltration remove water (down
+     * to a dry cell) with its velocity.  Nonzero rates switch skip_dry off. */
+    double rain_rate, evap_rate, infil_rate;
 } swe_params;
 
 /* What one call of swe_step reports (all reductions in FP64). */

@@ -155,6 +155,9 @@ Phys<T> phys_of(const swe_params& p) {
     P.wy = (T)p.wind_y;
     P.ca = (T)p.c_a;
     P.ra = (T)p.rho_air_over_rho;
+    P.rain = (T)p.rain_rate;
+    P.loss = (T)(p.evap_rate + p.infil_rate);
+    P.dist = (p.rain_rate != 0.0 || p.evap_rate != 0.0 || p.infil_rate != 0.0) ? 1 : 0;
     return P;
 }
 
@@ -224,7 +227,9 @@ FusedArgs<T> fused_args(const swe_ctx* c, bool closed = false) {
     a.corr = closed ? (const T*)c->d_corr : nullptr;
     a.act = c->d_act;
     a.act_nbx = c->act_nbx;
-    a.skip = (c->d_act && !closed) ? 1 : 0;  // closed steps stamp but never skip
+    // closed steps stamp but never skip; rain wets dry tiles and the losses
+    // change thin films, so distributed sources switch skipping off
+    a.skip = (c->d_act && !closed && !a.P.dist) ? 1 : 0;
     a.hist = c->d_hist;
     a.corr_plane = (size_t)c->pitch * (size_t)c->rows;
     return a;
@@ -348,6 +353,10 @@ int launch_one_step(swe_ctx* c) {
         if (is64(c)) CK(launch_staged<double>(staged_args<double>(c), c->st));
         else CK(launch_staged<float>(staged_args<float>(c), c->st));
     } else {
+        if (c->p.ghost_ring == 2) {  // open boundary: extend the state into the ring
+            if (is64(c)) CK(launch_ring_outflow<double>(grid_of<double>(c), c->ctl, c->st));
+            else CK(launch_ring_outflow<float>(grid_of<float>(c), c->ctl, c->st));
+        }
         if (is64(c)) CK(launch_fused<double>(fused_args<double>(c), c->st));
         else CK(launch_fused<float>(fused_args<float>(c), c->st));
     }
@@ -703,7 +712,10 @@ int swe_create(const swe_params* p, swe_ctx** out) {
     if (p->tile_w != 0 && p->tile_w != TW) return fail(SWE_ERR_ARG, "tile_w must be 0 or 116");
     if (p->skip_dry != 0 && p->skip_dry != 1) return fail(SWE_ERR_ARG, "skip_dry must be 0 or 1");
     if (p->skip_dry && p->mode != SWE_FUSED) return fail(SWE_ERR_ARG, "skip_dry needs SWE_FUSED");
-    if (p->ghost_ring != 0 && p->ghost_ring != 1) return fail(SWE_ERR_ARG, "ghost_ring must be 0 or 1");
+    if (p->ghost_ring < 0 || p->ghost_ring > 2) return fail(SWE_ERR_ARG, "ghost_ring must be 0, 1 or 2");
+    if (!(p->rain_rate >= 0.0 && p->rain_rate < 1.0) || !(p->evap_rate >= 0.0 && p->evap_rate < 1.0) ||
+        !(p->infil_rate >= 0.0 && p->infil_rate < 1.0))
+        return fail(SWE_ERR_ARG, "rain, evaporation and infiltration rates must lie in [0, 1) m/s");
     if (p->ghost_ring && p->mode != SWE_FUSED) return fail(SWE_ERR_ARG, "ghost_ring needs SWE_FUSED");
     if (p->ghost_ring && p->skip_dry)
         return fail(SWE_ERR_ARG, "skip_dry needs wall boundaries (ghost cells are not stamped)");
@@ -1543,7 +1555,7 @@ int swe_nest_create(swe_ctx* c, swe_ctx* f, int32_t ix0, int32_t iy0, swe_nest**
     *out = nullptr;
     if (c->p.mode != SWE_FUSED || f->p.mode != SWE_FUSED) return fail(SWE_ERR_ARG, "nested contexts must be SWE_FUSED");
     if (c->p.precision != f->p.precision) return fail(SWE_ERR_ARG, "nested contexts must share the precision");
-    if (!f->p.ghost_ring || c->p.ghost_ring) return fail(SWE_ERR_ARG, "the fine context needs ghost_ring = 1, the coarse 0");
+    if (f->p.ghost_ring != 1 || c->p.ghost_ring) return fail(SWE_ERR_ARG, "the fine context needs ghost_ring = 1, the coarse 0");
     if (f->p.nx % 4 || f->p.ny % 4) return fail(SWE_ERR_ARG, "fine nx and ny must be multiples of 4");
     if (std::fabs(c->p.dx - 4.0 * f->p.dx) > 1e-12 * c->p.dx) return fail(SWE_ERR_ARG, "fine dx must be coarse dx / 4");
     if (!(c->p.dt_fixed > 0.0) || std::fabs(f->p.dt_fixed - 0.25 * c->p.dt_fixed) > 1e-12 * c->p.dt_fixed)

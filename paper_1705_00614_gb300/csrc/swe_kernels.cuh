@@ -373,9 +373,10 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             }
         }
         const T ts = tauT * sig;
-        const T ht = tmax(T(0), H + ts);
-        const T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
-        const T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
+        T ht = tmax(T(0), H + ts);
+        T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
+        T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
+        if (P.dist && b < T(WALL_TEST)) distributed_sources(P, tauT, H, ts, utx, uty, ht, qtx, qty);
         const bool wt = is_wet(ht, b, eps);
         T(*C)[WIN] = cS(r);
         C[0][c] = ht;
@@ -888,9 +889,10 @@ __global__ void ks_correct(const StagedArgs<T> a) {
         a.uhy[k] = T(0.5) * (a.uy[k] + uty);
         const T sig = a.sig[k];
         const T ts = tauT * sig;
-        const T ht = tmax(T(0), H + ts);
-        const T qtx = H * utx + (sig > T(0) ? ts * a.svx[k] : ts * utx);
-        const T qty = H * uty + (sig > T(0) ? ts * a.svy[k] : ts * uty);
+        T ht = tmax(T(0), H + ts);
+        T qtx = H * utx + (sig > T(0) ? ts * a.svx[k] : ts * utx);
+        T qty = H * uty + (sig > T(0) ? ts * a.svy[k] : ts * uty);
+        if (a.P.dist && b < T(WALL_TEST)) distributed_sources(a.P, tauT, H, ts, utx, uty, ht, qtx, qty);
         const bool wt = is_wet(ht, b, a.P.eps);
         a.ht[k] = ht;
         a.qtx[k] = qtx;
@@ -1224,6 +1226,36 @@ __global__ void k_nest_ring(const Grid<T> f, const Ctl* __restrict__ fctl, const
     f.Qy[fb][kf] = (T)qy;
 }
 
+// Open (outflow) boundary: before a step every ring cell that is not a wall
+// (bed below 1e29) takes the state of the nearest interior cell (zero
+// gradient across the boundary), so waves and flow leave the domain.
+template <class T>
+__global__ void k_ring_outflow(const Grid<T> g, const Ctl* __restrict__ ctl) {
+    const int nxe = g.nx + 2 * PAD;
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long nband = (long long)PAD * nxe, nside = (long long)g.ny * PAD;
+    if (e >= 2 * nband + 2 * nside) return;
+    int ip, jp;
+    if (e < 2 * nband) {
+        const int r = (int)(e / nxe);
+        ip = (int)(e % nxe);
+        jp = r < PAD ? r : g.ny + r;
+    } else {
+        const long long q = e - 2 * nband;
+        const int r = (int)(q / (2 * PAD)), k = (int)(q % (2 * PAD));
+        jp = PAD + r;
+        ip = k < PAD ? k : g.nx + k;
+    }
+    const size_t kg = (size_t)jp * g.pitch + (size_t)ip;
+    if (!(g.b[kg] < T(WALL_TEST))) return;
+    const int i = min(max(ip - PAD, 0), g.nx - 1), j = min(max(jp - PAD, 0), g.ny - 1);
+    const size_t ki = (size_t)(j + PAD) * g.pitch + (size_t)(i + PAD);
+    const int buf = (int)(*(volatile const long long*)&ctl->step & 1);
+    g.H[buf][kg] = g.H[buf][ki];
+    g.Qx[buf][kg] = g.Qx[buf][ki];
+    g.Qy[buf][kg] = g.Qy[buf][ki];
+}
+
 // Feedback of a fine patch: each coarse cell it covers takes the means of
 // its 4 x 4 fine cells' H, Qx, Qy (summed row by row in the state
 // precision), which keeps the patch's water volume and momentum.
@@ -1261,6 +1293,13 @@ cudaError_t launch_nest_ring(const Grid<T>& f, const Ctl* fctl, const Grid<T>& c
                              double w, double eps, cudaStream_t st) {
     const long long n = 2LL * PAD * (f.nx + 2 * PAD) + 2LL * PAD * f.ny;
     k_nest_ring<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(f, fctl, c, cctl, ix0, iy0, w, eps);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_ring_outflow(const Grid<T>& g, const Ctl* ctl, cudaStream_t st) {
+    const long long n = 2LL * PAD * (g.nx + 2 * PAD) + 2LL * PAD * g.ny;
+    k_ring_outflow<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, ctl);
     return cudaGetLastError();
 }
 
@@ -1334,6 +1373,7 @@ cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cud
     template cudaError_t launch_pack_full<T>(const double*, T*, int, int, int, cudaStream_t);       \
     template cudaError_t launch_nest_ring<T>(const Grid<T>&, const Ctl*, const Grid<T>&, const Ctl*, int, int, \
                                              double, double, cudaStream_t);                         \
+    template cudaError_t launch_ring_outflow<T>(const Grid<T>&, const Ctl*, cudaStream_t);         \
     template cudaError_t launch_nest_restrict<T>(const Grid<T>&, const Ctl*, const Grid<T>&, const Ctl*, int, \
                                                  int, cudaStream_t);                                \
     template size_t fused_smem_bytes<T>();

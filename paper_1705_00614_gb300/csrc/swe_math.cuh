@@ -35,7 +35,12 @@ struct Phys {
     T f;     // Coriolis parameter
     T wx, wy;  // wind
     T ca, ra;  // C_a and rho_a / rho
+    // distributed sources of Eq. 1 on every non-wall cell: rain r and the
+    // losses e + i (evaporation, infiltration); dist = any of them nonzero
+    T rain, loss;
+    int dist;
 };
+
 
 // Multiplications whose products must cancel exactly (h_R^2 - h_L^2 with
 // h_R == h_L at rest) are kept out of FMA contraction.
@@ -233,6 +238,17 @@ __device__ __forceinline__ void face_flux(const Phys<T>& P, const ECell<T>& L, c
     FH = hs * us;
     FQx = FH * (FH >= T(0) ? wl[3] : wr[3]);
     FQy = FH * (FH >= T(0) ? wl[4] : wr[4]);
+}
+
+// Rain, evaporation and infiltration (Eq. 1 sigma) on a non-wall cell after
+// the point sources: depth H~ = max(0, (H + tau sigma_pt) + tau (r - e - i));
+// rain brings water at rest, the losses take water with its velocity U~.
+template <class T>
+__device__ __forceinline__ void distributed_sources(const Phys<T>& P, T tau, T H, T ts, T utx, T uty, T& ht, T& qtx,
+                                                    T& qty) {
+    ht = tmax(T(0), (H + ts) + tau * (P.rain - P.loss));
+    qtx = qtx - tau * P.loss * utx;
+    qty = qty - tau * P.loss * uty;
 }
 
 // Hydrograph value q(t) of one row (kind, peak, t_p, s), in FP64.

@@ -123,6 +123,9 @@ extern "C" SWE_API int swe_step_f32_noalloc(const swe_params* p, const float* H,
     if (!(p->dx > 0.0) || !(p->g > 0.0) || !(p->cfl > 0.0 && p->cfl <= 1.0) || !(p->eps_dry >= 0.0) ||
         !(p->dt_max > 0.0) || !(p->dt_fixed >= 0.0) || !(p->nu >= 0.0) || !(p->c_a >= 0.0))
         return nfail(SWE_ERR_ARG, "physical or numerical parameter out of range");
+    if (!(p->rain_rate >= 0.0 && p->rain_rate < 1.0) || !(p->evap_rate >= 0.0 && p->evap_rate < 1.0) ||
+        !(p->infil_rate >= 0.0 && p->infil_rate < 1.0))
+        return nfail(SWE_ERR_ARG, "rain, evaporation and infiltration rates must lie in [0, 1) m/s");
     if (pitch < (int64_t)p->nx + 2 * PAD || (pitch % 4) != 0)
         return nfail(SWE_ERR_ARG, "pitch must be >= nx + 2*SWE_PAD and a multiple of 4 floats");
     const void* ptrs[8] = {H, Qx, Qy, b, n, H_out, Qx_out, Qy_out};
@@ -179,6 +182,9 @@ extern "C" SWE_API int swe_step_f32_noalloc(const swe_params* p, const float* H,
     a.P.wy = (float)p->wind_y;
     a.P.ca = (float)p->c_a;
     a.P.ra = (float)p->rho_air_over_rho;
+    a.P.rain = (float)p->rain_rate;
+    a.P.loss = (float)(p->evap_rate + p->infil_rate);
+    a.P.dist = (p->rain_rate != 0.0 || p->evap_rate != 0.0 || p->infil_rate != 0.0) ? 1 : 0;
     a.sp.dx = p->dx;
     a.sp.cfl = p->cfl;
     a.sp.dt_max = p->dt_max;

@@ -50,7 +50,8 @@ class Params(ctypes.Structure):
                 ("wind_x", ctypes.c_double), ("wind_y", ctypes.c_double), ("c_a", ctypes.c_double),
                 ("rho_air_over_rho", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("tile_w", ctypes.c_int32), ("seg_h", ctypes.c_int32),
-                ("skip_dry", ctypes.c_int32), ("ghost_ring", ctypes.c_int32)]
+                ("skip_dry", ctypes.c_int32), ("ghost_ring", ctypes.c_int32),
+                ("rain_rate", ctypes.c_double), ("evap_rate", ctypes.c_double), ("infil_rate", ctypes.c_double)]
 
 
 class StepInfo(ctypes.Structure):
@@ -182,13 +183,15 @@ def make_params(params, precision="f32", mode="fused", stream=None, seg_h=0, ski
     for k in ("nx", "ny", "dx", "g", "cfl", "dt_max", "dt_fixed", "nu", "coriolis_f", "wind_x", "wind_y",
               "c_a", "rho_air_over_rho"):
         setattr(p, k, getattr(params, k))
+    for k in ("rain_rate", "evap_rate", "infil_rate"):
+        setattr(p, k, float(getattr(params, k, 0.0)))
     p.eps_dry = params.eps
     p.precision = SWE_F64 if precision == "f64" else SWE_F32
     p.mode = SWE_STAGED if mode == "staged" else SWE_FUSED
     p.cuda_stream = stream
     p.seg_h = seg_h
     p.skip_dry = 1 if skip_dry else 0
-    p.ghost_ring = 1 if ghost_ring else 0
+    p.ghost_ring = int(ghost_ring)  # 0 walls, 1 nest ghosts, 2 open boundary
     return p
 
 

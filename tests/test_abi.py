@@ -48,9 +48,9 @@ def test_struct_layouts_match_header(tmp_path):
 #include <stddef.h>
 #include "{HDR}"
 int main(void) {{
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(swe_params), offsetof(swe_params, dx),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(swe_params), offsetof(swe_params, dx),
          offsetof(swe_params, cuda_stream), offsetof(swe_params, seg_h), offsetof(swe_params, skip_dry),
-         offsetof(swe_params, ghost_ring),
+         offsetof(swe_params, ghost_ring), offsetof(swe_params, infil_rate),
          sizeof(swe_step_info),
          offsetof(swe_step_info, wet_cells));
   return 0;
@@ -61,6 +61,7 @@ int main(void) {{
     vals = list(map(int, subprocess.check_output([str(exe)]).split()))
     assert vals == [ctypes.sizeof(swe.Params), swe.Params.dx.offset, swe.Params.cuda_stream.offset,
                     swe.Params.seg_h.offset, swe.Params.skip_dry.offset, swe.Params.ghost_ring.offset,
+                    swe.Params.infil_rate.offset,
                     ctypes.sizeof(swe.StepInfo),
                     swe.StepInfo.wet_cells.offset]
 
@@ -82,7 +83,8 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
                 {"nx": 4, "ny": 4, "dx": 1.0, "skip_dry": 2},
                 {"nx": 4, "ny": 4, "dx": 1.0, "skip_dry": 1, "mode": swe.SWE_STAGED},
                 {"nx": 4, "ny": 4, "dx": 1.0, "ghost_ring": 1, "mode": swe.SWE_STAGED},
-                {"nx": 4, "ny": 4, "dx": 1.0, "ghost_ring": 1, "skip_dry": 1}):
+                {"nx": 4, "ny": 4, "dx": 1.0, "ghost_ring": 1, "skip_dry": 1},
+                {"nx": 4, "ny": 4, "dx": 1.0, "rain_rate": -1e-3}):
         q = swe.Params()
         lib.swe_params_default(ctypes.byref(q))
         for k, v in bad.items():
