@@ -25,6 +25,10 @@ A fine sub-step is computed as one oracle step of the padded extent (ring
 cells as ordinary cells, walls beyond them), of which the interior is kept:
 one step moves information at most 6 cells, so the walls 10 cells out never
 reach the interior.
+
+The same construction gives the open (outflow) boundary of a single grid:
+before each step every ring cell that is not a wall takes the state of the
+nearest interior cell (zero gradient across the boundary).
 """
 from __future__ import annotations
 
@@ -115,3 +119,36 @@ def nest_run(coarse, fine, b_ext, n_ext, ix0, iy0, ncoarse):
         c = [a.copy() for a in new]
         c[0][csl], c[1][csl], c[2][csl] = rH, rQx, rQy
     return c, f
+
+
+def outflow_values(H, Qx, Qy, b_ext):
+    """Padded-extent state: the interior (H, Qx, Qy), and in every non-wall
+    ring cell the state of the nearest interior cell."""
+    ny, nx = H.shape
+    nye, nxe = b_ext.shape
+    jj = np.clip(np.arange(nye) - PAD, 0, ny - 1)
+    ii = np.clip(np.arange(nxe) - PAD, 0, nx - 1)
+    out = []
+    for a in (H, Qx, Qy):
+        e = np.asarray(a, dtype=np.float64)[np.ix_(jj, ii)]
+        e[b_ext >= WALL_TEST] = 0.0
+        out.append(e)
+    return out
+
+
+def open_run(prob, b_ext, n_ext, nsteps):
+    """nsteps steps of one grid with open boundaries (fixed steps); returns
+    the interior (H, Qx, Qy)."""
+    p = prob.params
+    ext = extended(prob, b_ext, n_ext)
+    bd = oracle._Bound(ext)
+    sl = (slice(PAD, PAD + p.ny), slice(PAD, PAD + p.nx))
+    s = [np.array(prob.H, dtype=np.float64), np.array(prob.Qx, dtype=np.float64),
+         np.array(prob.Qy, dtype=np.float64)]
+    t = 0.0
+    for _ in range(nsteps):
+        E = outflow_values(s[0], s[1], s[2], ext.b)
+        He, Qxe, Qye, info, _ = oracle.step(ext, E[0], E[1], E[2], t, bound=bd)
+        t = info["t_new"]
+        s = [He[sl].copy(), Qxe[sl].copy(), Qye[sl].copy()]
+    return s

@@ -186,6 +186,9 @@ cudaError_t launch_nest_ring(const Grid<T>& f, const Ctl* fctl, const Grid<T>& c
 template <class T>
 cudaError_t launch_nest_restrict(const Grid<T>& f, const Ctl* fctl, const Grid<T>& c, const Ctl* cctl, int ix0, int iy0,
                                  cudaStream_t st);
+// Open boundary: non-wall ring cells take the nearest interior cell's state.
+template <class T>
+cudaError_t launch_ring_outflow(const Grid<T>& g, const Ctl* ctl, cudaStream_t st);
 template <class T>
 size_t fused_smem_bytes();
 // Learned-closure kernels (swe_cnn.cu).

@@ -113,3 +113,51 @@ def test_ghost_ring_step_is_the_step_of_a_larger_grid():
     assert np.array_equal(He[sl], Hg[isl])
     assert np.array_equal(Qxe[sl], Qxg[isl])
     assert np.array_equal(Qye[sl], Qyg[isl])
+
+
+def _open_basin(n=40, H0=2.0, u0=0.6, v0=-0.3, slope=False):
+    """Flat (or linearly sloping, frictionless) domain with a uniform state;
+    the ring terrain extends the interior's."""
+    p = I.Params(nx=n, ny=n, dx=4.0, dt_fixed=0.05)
+    x = (np.arange(n + 2 * P) - P + 0.5) * 4.0
+    b_ext = np.tile(1e-3 * x, (n + 2 * P, 1)) if slope else np.zeros((n + 2 * P, n + 2 * P))
+    b = b_ext[P:P + n, P:P + n]
+    H = np.full((n, n), H0)
+    prob = I.Problem("open", p, b.copy(), np.zeros((n, n)), H, H * u0, H * v0, I.Sources.empty())
+    return prob, b_ext
+
+
+def test_uniform_flow_passes_open_boundaries_unchanged():
+    prob, b_ext = _open_basin()
+    H, Qx, Qy = N.open_run(prob, b_ext, None, 20)
+    assert np.abs(H - 2.0).max() <= 1e-13
+    assert np.abs(Qx - 2.0 * 0.6).max() <= 1e-13 and np.abs(Qy + 2.0 * 0.3).max() <= 1e-13
+
+
+def test_open_boundaries_let_a_wave_leave():
+    """A dam break released towards the east edge: with an open boundary the
+    interior matches a four times longer domain (whose far walls are not yet
+    reached) far better than with a wall, and water leaves the grid."""
+    n, ny = 48, 8
+    p = I.Params(nx=n, ny=ny, dx=1.0, dt_fixed=0.02)
+    H0 = np.where(np.arange(n) < 24, 2.0, 1.0)[None, :].repeat(ny, axis=0)
+    z = np.zeros((ny, n))
+    prob = I.Problem("wave", p, z.copy(), z.copy(), H0, z.copy(), z.copy(), I.Sources.empty())
+    b_ext = np.zeros((ny + 2 * P, n + 2 * P))
+    b_ext[:P, :] = 1e30  # north, south and west stay walls: only the east is open
+    b_ext[-P:, :] = 1e30
+    b_ext[:, :P] = 1e30
+    steps = 400  # 8 s: the bore passes the east edge at x = 48 (speed ~5 m/s)
+    Ho, _, _ = N.open_run(prob, b_ext, None, steps)
+    Hw, _, _, _, _ = oracle.run(prob, steps)
+    big = dataclasses.replace(prob, params=dataclasses.replace(p, nx=4 * n),
+                              b=np.zeros((ny, 4 * n)), n_manning=np.zeros((ny, 4 * n)),
+                              H=np.concatenate([H0, np.ones((ny, 3 * n))], axis=1),
+                              Qx=np.zeros((ny, 4 * n)), Qy=np.zeros((ny, 4 * n)))
+    Hb, _, _, _, _ = oracle.run(big, steps)
+    Hb = Hb[:, :n]
+    err_open = np.abs(Ho - Hb).max()
+    err_wall = np.abs(Hw - Hb).max()
+    # zero gradient reflects part of a subcritical bore, a wall all of it
+    assert err_open < 0.25 * err_wall, (err_open, err_wall)
+    assert Ho.sum() < H0.sum() - 1.0
