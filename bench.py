@@ -59,6 +59,43 @@ def kernel_hash():
     return h.hexdigest()[:16]
 
 
+def over_ranks(x, op="max"):
+    """x combined over the ranks of the initialised process group ("max" or
+    "sum"; a float64 all-reduce on the backend's device); x itself in a
+    single-process run.  Timing takes the slowest rank, counts of work the
+    sum: nothing of the solver's data crosses ranks."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_barrier():
+    """Barrier across the ranks of the initialised process group (no-op in a
+    single-process run)."""
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def shard(n, rank, world):
+    """Indices of the n independent units (ensemble scenarios) that `rank`
+    of `world` runs: round robin, disjoint across ranks, together all n."""
+    if not 0 <= rank < world:
+        raise ValueError(f"rank {rank} outside world {world}")
+    return list(range(rank, n, world))
+
+
+def job_rate(units, ms):
+    """Whole-job throughput in G-units/s: units processed by all ranks over
+    the slowest rank's time (ms)."""
+    return units / (ms * 1e-3) / 1e9
+
+
 def flooded_workload(name):
     """The benchmark problem: a named floodplain, filled to its median
     terrain height (still water), keeping the inflow strip and physics.
@@ -74,10 +111,11 @@ def flooded_workload(name):
     return I.Problem(name, p.params, p.b, p.n_manning, H, z, z.copy(), p.sources).to_f32_values(), eta0
 
 
-def flooded_ensemble(n):
-    """The batched-ensemble workload: n scenarios with N uniform in
-    [512, 2048], each filled to its median terrain height."""
-    probs, gates = I.ensemble(n)
+def flooded_ensemble(n, rank=0, world=1):
+    """The batched-ensemble workload of one rank: its share (round robin) of
+    an ensemble of n x world scenarios with N uniform in [512, 2048], each
+    filled to its median terrain height.  One rank runs all n."""
+    probs, gates = I.ensemble(n * world, indices=shard(n * world, rank, world))
     out = []
     for p in probs:
         eta0 = float(np.median(p.b))
@@ -88,10 +126,12 @@ def flooded_ensemble(n):
 
 
 def run_ensemble(args, torch, swe, stream, rank, world):
-    """Batched ensemble: all scenarios advance in one persistent launch per
-    step (CUDA graph of K steps); value counts every scenario's cells."""
+    """Batched ensemble: all of this rank's scenarios advance in one
+    persistent launch per step (CUDA graph of K steps); ranks run disjoint
+    scenarios (n each), value counts every rank's cells over the slowest
+    rank's time."""
     n = int(args.workload.split("-")[1])
-    probs, gates = flooded_ensemble(n)
+    probs, gates = flooded_ensemble(n, rank, world)
     cells = sum(p.params.nx * p.params.ny for p in probs)
     sols = [swe.Solver.from_problem(p, args.precision, stream=stream.cuda_stream) for p in probs]
     batch = swe.Batch(sols)
@@ -103,17 +143,20 @@ def run_ensemble(args, torch, swe, stream, rank, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        rank_barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         batch.step(args.steps, report=False)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+        rank_barrier()
+    ms = over_ranks(e0.elapsed_time(e1))
     infos = batch.step(0)
     batch.close()
     for x in sols:
         x.close()
-    value = world * cells * args.steps / (ms * 1e-3) / 1e9
+    job_cells = over_ranks(cells, "sum")
+    value = job_rate(job_cells * args.steps, ms)
     achieved = BYTES_PER_CELL[args.precision] * cells / (ms / args.steps * 1e-3) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak = json.load(open(peaks_path))["hbm_gbs"] if os.path.exists(peaks_path) else 6800.0
@@ -121,11 +164,13 @@ def run_ensemble(args, torch, swe, stream, rank, world):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
-                "config": {"workload": args.workload, "scenarios": n, "cells": cells,
+                "config": {"workload": args.workload, "scenarios": n * world, "scenarios_per_gpu": n,
+                           "cells": int(job_cells),
                            "sizes": [min(p.params.nx for p in probs), max(p.params.nx for p in probs)],
                            "seg_h_autotuned": seg, "gates": int(sum(len(g.ix) for g in gates)),
                            "wet_cells_end": int(sum(i["wet_cells"] for i in infos)),
-                           "l2": "inputs larger than L2", "parallelism": "replicas" if world > 1 else "single GPU"},
+                           "l2": "inputs larger than L2",
+                           "parallelism": f"scenarios sharded over {world} ranks" if world > 1 else "single GPU"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": None, "kernel": "k_fused_batch<float>",
                              "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision]},
@@ -159,6 +204,7 @@ def run_cnn(args, torch, swe, stream, rank, world):
     e1 = torch.cuda.Event(enable_timing=True)
     e2 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        rank_barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(args.steps):
@@ -168,8 +214,9 @@ def run_cnn(args, torch, swe, stream, rank, world):
             net.forward(x.data_ptr())
         e2.record(stream)
         torch.cuda.synchronize()
-    ms_train = e0.elapsed_time(e1) / args.steps
-    ms_fwd = e1.elapsed_time(e2) / args.steps
+        rank_barrier()
+    ms_train = over_ranks(e0.elapsed_time(e1)) / args.steps
+    ms_fwd = over_ranks(e1.elapsed_time(e2)) / args.steps
     net.close()
     px = n * n
     tflops = CNN_TRAIN_FLOP * px / (ms_train * 1e-3) / 1e12
@@ -178,7 +225,7 @@ def run_cnn(args, torch, swe, stream, rank, world):
     peak, src = (json.load(open(peaks_path))["bf16_tflops"], "measured") if os.path.exists(peaks_path) \
         else (1900.0, "fallback")
     if rank == 0:
-        line = {"metric": "closure CNN training throughput", "value": world * px / (ms_train * 1e-3) / 1e9,
+        line = {"metric": "closure CNN training throughput", "value": job_rate(world * px, ms_train),
                 "unit": "Gpixel-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": ms_train, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "bf16", "data": "synthetic",
@@ -355,12 +402,14 @@ def run_nest(args, torch, swe, stream, rank, world):
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+        rank_barrier()
         torch.cuda.synchronize()
         e0.record(stream)
         nest.step(args.steps, report=False)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
+        rank_barrier()
+    ms = over_ranks(e0.elapsed_time(e1)) / args.steps
     ic, jf = nest.step(0)
     nest.close()
     c.close()
@@ -368,7 +417,7 @@ def run_nest(args, torch, swe, stream, rank, world):
     updates = n * n + 4 * n * n
     if rank == 0:
         line = {"metric": "nested Gcell-updates/s (coarse + 4 fine sub-steps)",
-                "value": world * updates / (ms * 1e-3) / 1e9, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "value": job_rate(world * updates, ms), "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
                 "config": {"workload": args.workload, "coarse": f"{n}^2 dx 20 m", "patch": f"{n}^2 dx 5 m",
@@ -551,9 +600,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = rank_barrier
 
     from paper_1705_00614_gb300 import build as B
     from paper_1705_00614_gb300 import swe
@@ -618,14 +665,10 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = e0.elapsed_time(e1)
+    ms = over_ranks(e0.elapsed_time(e1))
     info = solver.step(0)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     ms_per_step = ms / args.steps
-    value = world * cells * args.steps / (ms * 1e-3) / 1e9
+    value = job_rate(world * cells * args.steps, ms)
 
     # end to end through the C ABI with pinned host buffers
     shape = (prob.params.ny, prob.params.nx)
@@ -644,12 +687,8 @@ def main():
         solver.step(1, report=False)
         solver.get_state_into(hb[3], hb[4], hb[5])
     torch.cuda.synchronize()
-    e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = world * cells * args.e2e_steps / e2e_s / 1e9
+    e2e_s = over_ranks(time.perf_counter() - t0)
+    e2e_val = job_rate(world * cells * args.e2e_steps, e2e_s * 1e3)
     io_bytes = 3 * cells * 8
 
     bpc = BYTES_PER_CELL[args.precision]

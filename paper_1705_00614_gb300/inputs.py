@@ -382,16 +382,20 @@ class GateSchedule:
 
 
 def ensemble(n: int, seed_base: int = 10000, nmin: int = 512, nmax: int = 2048, dx: float = 10.0,
-             toggle_steps: int = 2000, max_gates: int = 8):
+             toggle_steps: int = 2000, max_gates: int = 8, indices=None):
     """Seeded flood-scenario ensemble: scenario s has a square grid with N
     uniform in [nmin, nmax], its own fractal terrain (seed seed_base + s)
     with the carved channel, a 100-cell inflow strip fed by a Gaussian
     hydrograph with peak time uniform in [1, 6] h, peak uniform in
     [1, 10] m/s*cells and width t_p / 3, and 0..max_gates gate cells on the
     channel with a seeded initial state and one seeded toggle step in
-    [0, toggle_steps).  Returns (problems, gate schedules)."""
+    [0, toggle_steps).  Scenario s depends on s alone: `indices` (default
+    all of range(n)) picks which scenarios to build.  Returns (problems,
+    gate schedules)."""
     probs, gates = [], []
-    for s in range(n):
+    for s in (range(n) if indices is None else indices):
+        if not 0 <= s < n:
+            raise ValueError(f"scenario {s} outside an ensemble of {n}")
         u = uniform(seed_base, 20, np.arange(4) + 4 * s)
         N = int(nmin + int(u[0] * (nmax - nmin + 1)))
         tp = 3600.0 * (1.0 + 5.0 * u[1])
