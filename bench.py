@@ -47,6 +47,7 @@ from paper_1705_00614_gb300 import inputs as I  # noqa: E402
 METRIC = "Gcell-updates/s and HBM-roofline %; CNN-closure vs fine solve at ≤1% L2"
 UNIT = "Gcell-updates/s"
 BYTES_PER_CELL = {"f32": 32, "f64": 64}
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal (the measured copy bandwidth is the roofline peak)
 KERNEL_SOURCES = ["paper_1705_00614_gb300/csrc/swe_kernels.cuh", "paper_1705_00614_gb300/csrc/swe_math.cuh",
                   "paper_1705_00614_gb300/csrc/swe_launch.h"]
 
@@ -725,6 +726,7 @@ def main():
                            "final_t_s": info["t"], "wet_cells_end": info["wet_cells"]},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "peak_source": peak_src,
+                             "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
                              "traffic": None if prof is None else prof["dram"] * cells,
                              "kernel": f"k_fused<{'float' if args.precision == 'f32' else 'double'}>",
                              "algorithmic_bytes_per_cell": bpc},
