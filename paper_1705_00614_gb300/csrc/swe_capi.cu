@@ -158,6 +158,7 @@ Phys<T> phys_of(const swe_params& p) {
     P.rain = (T)p.rain_rate;
     P.loss = (T)(p.evap_rate + p.infil_rate);
     P.dist = (p.rain_rate != 0.0 || p.evap_rate != 0.0 || p.infil_rate != 0.0) ? 1 : 0;
+    phys_derive(P);
     return P;
 }
 

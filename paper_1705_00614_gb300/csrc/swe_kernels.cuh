@@ -135,13 +135,13 @@ struct FSmem {
     T inB[RB_][WIN];
     T inN[RN][WIN];
     T inA[3][RA][WIN];     // a_x, a_y, phi at t_n (ACC only)
-    T pU[DP][2][WIN];      // U at t_n (without ACC)
-    T aU[DA][2][WIN];      // predictor U*
+    T pU[2][DP][WIN];      // U at t_n (without ACC)
+    T aU[2][DA][WIN];      // predictor U*
     T bH[DB][WIN];         // particle depth H*
-    T cS[DC][9][WIN];      // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y, b, n
-    T sX[DX][5][WIN];      // x slopes of H~, U^, U~'
-    T fX[DF][3][WIN];      // x-face fluxes F_H, F_Qx, F_Qy
-    T nS[DN][4][WIN];      // new state H, Ux, Uy with the cell's b
+    T cS[9][DC][WIN];      // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y, b, n
+    T sX[5][DX][WIN];      // x slopes of H~, U^, U~'
+    T fX[3][DF][WIN];      // x-face fluxes F_H, F_Qx, F_Qy
+    T nS[4][DN][WIN];      // new state H, Ux, Uy with the cell's b
     unsigned long long bar[NBAR];
     double hq[MAX_HYDRO];
     double red[NT / 32];
@@ -149,6 +149,15 @@ struct FSmem {
     int last;
     int witem;
     int abort;
+};
+
+// One row of a field-major stage ring: row[q] is field q's WIN values.  All
+// rings keep rows WIN values apart, so one slot offset per row serves every
+// field (the field offsets are constants).
+template <class T, int FS>
+struct FRow {
+    T* p;
+    __device__ __forceinline__ T* operator[](int q) const { return p + q * FS; }
 };
 
 template <class T, bool ACC>
@@ -247,16 +256,18 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     auto rB = [&](int r) -> const T* { return s.inB[r & (S::RB_ - 1)]; };
     auto rN = [&](int r) -> const T* { return s.inN[r & (S::RN - 1)]; };
     auto rA = [&](int q, int r) -> const T* { return s.inA[q][r & (S::RA - 1)]; };
-    auto pU = [&](int r) { return s.pU[r & (S::DP - 1)]; };
-    auto aU = [&](int r) { return s.aU[r & (S::DA - 1)]; };
+    auto pU = [&](int r) { return FRow<T, S::DP * WIN>{&s.pU[0][r & (S::DP - 1)][0]}; };
+    auto aU = [&](int r) { return FRow<T, S::DA * WIN>{&s.aU[0][r & (S::DA - 1)][0]}; };
     auto bH = [&](int r) { return s.bH[r & (S::DB - 1)]; };
-    auto cS = [&](int r) { return s.cS[r & (S::DC - 1)]; };
-    auto sX = [&](int r) { return s.sX[r & (S::DX - 1)]; };
-    auto fX = [&](int r) { return s.fX[r & (S::DF - 1)]; };
-    auto nS = [&](int r) { return s.nS[r & (S::DN - 1)]; };
+    auto cS = [&](int r) { return FRow<T, S::DC * WIN>{&s.cS[0][r & (S::DC - 1)][0]}; };
+    auto sX = [&](int r) { return FRow<T, S::DX * WIN>{&s.sX[0][r & (S::DX - 1)][0]}; };
+    auto fX = [&](int r) { return FRow<T, S::DF * WIN>{&s.fX[0][r & (S::DF - 1)][0]}; };
+    auto nS = [&](int r) { return FRow<T, S::DN * WIN>{&s.nS[0][r & (S::DN - 1)][0]}; };
 
     int sp = a.src_off[item];
     const int se = a.src_off[item + 1];
+    // without point or distributed sources H~ = H exactly: nothing to add
+    const bool has_src = sp != se || P.dist;
     T syPrev[5] = {T(0), T(0), T(0), T(0), T(0)};
     T fyPrev[3] = {T(0), T(0), T(0)}, fyCur[3] = {T(0), T(0), T(0)};
     double acc_mass = 0.0, acc_src = 0.0, acc_clip = 0.0, vmax = 0.0;
@@ -270,10 +281,12 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         if (k >= nrows) return;
         const T H = rH(k)[c];
         const bool wet = is_wet(H, rB(k)[c], eps);
-        const T ux = wet ? rQx(k)[c] / H : T(0);
-        const T uy = wet ? rQy(k)[c] / H : T(0);
+        T ux, uy;
+        div2(rQx(k)[c], rQy(k)[c], H, ux, uy);
+        ux = wet ? ux : T(0);
+        uy = wet ? uy : T(0);
         if (!ACC) {
-            T(*U)[WIN] = pU(k);
+            const auto U = pU(k);
             U[0][c] = ux;
             U[1][c] = uy;
         }
@@ -281,10 +294,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             T usx = T(0), usy = T(0);
             if (wet) {
                 const T den = T(1) + th * rA(2, k)[c];
-                usx = (ux + th * rA(0, k)[c]) / den;
-                usy = (uy + th * rA(1, k)[c]) / den;
+                div2(ux + th * rA(0, k)[c], uy + th * rA(1, k)[c], den, usx, usy);
             }
-            T(*A)[WIN] = aU(k);
+            const auto A = aU(k);
             A[0][c] = usx;
             A[1][c] = usy;
         }
@@ -294,9 +306,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         if (!(r >= 1 && r <= nrows - 2 && c >= 1 && c < WIN - 1)) return;
         const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
         const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
-        const T(*U0)[WIN] = pU(r);
-        const T(*Um)[WIN] = pU(r - 1);
-        const T(*Up)[WIN] = pU(r + 1);
+        const auto U0 = pU(r);
+        const auto Um = pU(r - 1);
+        const auto Up = pU(r + 1);
         const T H = H0[c], b = b0[c];
         T usx = T(0), usy = T(0);
         if (is_wet(H, b, eps)) {
@@ -307,10 +319,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             T ax, ay, phi;
             forces(P, H, b, rN(r)[c], U0[0][c], U0[1][c], W, E, S, N, ax, ay, phi);
             const T den = T(1) + th * phi;
-            usx = (U0[0][c] + th * ax) / den;
-            usy = (U0[1][c] + th * ay) / den;
+            div2(U0[0][c] + th * ax, U0[1][c] + th * ay, den, usx, usy);
         }
-        T(*A)[WIN] = aU(r);
+        const auto A = aU(r);
         A[0][c] = usx;
         A[1][c] = usy;
     };
@@ -320,12 +331,14 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         const T H = rH(r)[c];
         T hs = H;
         if (is_wet(H, rB(r)[c], eps)) {
-            const T(*A0)[WIN] = aU(r);
+            const auto A0 = aU(r);
             const T u = A0[0][c], uW = A0[0][c - 1], uE = A0[0][c + 1];
             const T v = A0[1][c], vS = aU(r - 1)[1][c], vN = aU(r + 1)[1][c];
             const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
             const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
-            const T D = ((fxp - fxm) + (fyp - fym)) / P.h;
+            T D;
+            if constexpr (sizeof(T) == 4) D = ((fxp - fxm) + (fyp - fym)) * P.ih;
+            else D = ((fxp - fxm) + (fyp - fym)) / P.h;
             hs = H / tmax(T(0.5), T(1) + th * D);
         }
         bH(r)[c] = hs;
@@ -336,15 +349,16 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
         const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
         const T *B0 = bH(r), *Bm = bH(r - 1), *Bp = bH(r + 1);
-        const T(*A0)[WIN] = aU(r);
-        const T(*Am)[WIN] = aU(r - 1);
-        const T(*Ap)[WIN] = aU(r + 1);
+        const auto A0 = aU(r);
+        const auto Am = aU(r - 1);
+        const auto Ap = aU(r + 1);
         const T H = H0[c], b = b0[c];
         const bool wet = is_wet(H, b, eps);
         T ux, uy;
         if (ACC) {
-            ux = wet ? rQx(r)[c] / H : T(0);
-            uy = wet ? rQy(r)[c] / H : T(0);
+            div2(rQx(r)[c], rQy(r)[c], H, ux, uy);
+            ux = wet ? ux : T(0);
+            uy = wet ? uy : T(0);
         } else {
             ux = pU(r)[0][c];
             uy = pU(r)[1][c];
@@ -359,8 +373,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             T ax, ay, phi;
             forces(P, B0[c], b, nm, A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
             const T den = T(1) + tauT * phi;
-            utx = (ux + tauT * ax) / den;
-            uty = (uy + tauT * ay) / den;
+            div2(ux + tauT * ax, uy + tauT * ay, den, utx, uty);
         }
         const T uhx = T(0.5) * (ux + utx), uhy = T(0.5) * (uy + uty);
         T sig = T(0), vx = T(0), vy = T(0);
@@ -378,21 +391,23 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
         if (P.dist && b < T(WALL_TEST)) distributed_sources(P, tauT, H, ts, utx, uty, ht, qtx, qty);
         const bool wt = is_wet(ht, b, eps);
-        T(*C)[WIN] = cS(r);
+        const auto C = cS(r);
         C[0][c] = ht;
         C[1][c] = uhx;
         C[2][c] = uhy;
-        C[3][c] = wt ? qtx / ht : T(0);
-        C[4][c] = wt ? qty / ht : T(0);
+        T upx, upy;
+        div2(qtx, qty, ht, upx, upy);
+        C[3][c] = wt ? upx : T(0);
+        C[4][c] = wt ? upy : T(0);
         C[5][c] = qtx;
         C[6][c] = qty;
         C[7][c] = b;
         C[8][c] = nm;
-        if (out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
+        if (has_src && out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
     };
     auto ecell = [&](int rr, int col) {
         ECell<T> e;
-        const T(*C)[WIN] = cS(rr);
+        const auto C = cS(rr);
         const T bb = C[7][col];
         e.w[0] = C[0][col];
         e.w[1] = C[1][col];
@@ -409,7 +424,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         if (!(r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 5)) return;
         T sx[5];
         slopes(ecell(r, c - 1), ecell(r, c), ecell(r, c + 1), sx);
-        T(*X)[WIN] = sX(r);
+        const auto X = sX(r);
 #pragma unroll
         for (int q = 0; q < 5; ++q) X[q][c] = sx[q];
     };
@@ -425,7 +440,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
         if (r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 6) {
             const ECell<T> x1 = ecell(r, c + 1);
-            const T(*X)[WIN] = sX(r);
+            const auto X = sX(r);
             T sL[5], sR[5];
 #pragma unroll
             for (int q = 0; q < 5; ++q) {
@@ -434,7 +449,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             }
             T FH, FQx, FQy;
             face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
-            T(*F)[WIN] = fX(r);
+            const auto F = fX(r);
             F[0][c] = FH;
             F[1][c] = FQx;
             F[2][c] = FQy;
@@ -443,7 +458,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     // S6: final update of row r (K8)
     auto stage6 = [&](int r) {
         if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
-            const T(*FX)[WIN] = fX(r);
+            const auto FX = fX(r);
             T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
             T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
             T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
@@ -454,7 +469,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                 fqx += a.corr[a.corr_plane + gk];
                 fqy += a.corr[2 * a.corr_plane + gk];
             }
-            const T(*C)[WIN] = cS(r);
+            const auto C = cS(r);
             T hn = C[0][c] + dth * fh;
             double clip = 0.0;
             if (hn < T(0)) {
@@ -468,8 +483,11 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             }
             const T b = C[7][c];
             const bool wetn = is_wet(hn, b, eps);
-            const T uxn = wetn ? qxn / hn : T(0), uyn = wetn ? qyn / hn : T(0);
-            T(*Nw)[WIN] = nS(r);
+            T uxn, uyn;
+            div2(qxn, qyn, hn, uxn, uyn);
+            uxn = wetn ? uxn : T(0);
+            uyn = wetn ? uyn : T(0);
+            const auto Nw = nS(r);
             Nw[0][c] = hn;
             Nw[1][c] = uxn;
             Nw[2][c] = uyn;
@@ -505,9 +523,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     // carries b, so no input row older than S3's is needed.
     auto stage7 = [&](int r) {
         if (!(r >= HALO && r < HALO + sh && out_col)) return;
-        const T(*N0)[WIN] = nS(r);
-        const T(*Nm)[WIN] = nS(r - 1);
-        const T(*Np)[WIN] = nS(r + 1);
+        const auto N0 = nS(r);
+        const auto Nm = nS(r - 1);
+        const auto Np = nS(r + 1);
         const T H = N0[0][c], b = N0[3][c];
         T ax = T(0), ay = T(0);
         if (is_wet(H, b, eps)) {

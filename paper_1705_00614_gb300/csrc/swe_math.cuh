@@ -8,7 +8,11 @@
 // instantiation (compiled without FMA contraction) rounds like a plain
 // sequential evaluation of the same formulas, with one deliberate exception:
 // face depths eta - b* are formed as H + (b - b*) (see face_delta), which
-// differs from evaluating eta first by one rounding of eta.
+// differs from evaluating eta first by one rounding of eta.  The FP32
+// instantiation multiplies by reciprocals instead of dividing (one reciprocal
+// shared by the two components of a vector, and host-computed constants such
+// as -g / (4 h)); its accuracy is set against the FP64 oracle, not against a
+// sequential FP32 evaluation.
 //
 // Walls: the device layout surrounds every grid by a ring of cells whose bed
 // is WALL_BED (1e30) and whose depth is 0, and a closed gate is a cell whose
@@ -39,7 +43,34 @@ struct Phys {
     // losses e + i (evaporation, infiltration); dist = any of them nonzero
     T rain, loss;
     int dist;
+    // derived constants for the FP32 forms, which multiply by reciprocals
+    // (the fast-math build turns every division into one anyway):
+    // -g / (4 h), nu / h^2, C_a rho_a / rho, 1 / g, 1 / h (phys_derive)
+    T gq, cv, cara, ig, ih;
 };
+
+template <class T>
+__host__ __device__ inline void phys_derive(Phys<T>& P) {
+    P.gq = -P.g / (T(4) * P.h);
+    P.cv = P.nu / (P.h * P.h);
+    P.cara = P.ca * P.ra;
+    P.ig = T(1) / P.g;
+    P.ih = T(1) / P.h;
+}
+
+// q = a / d and r = b / d; FP32 shares one reciprocal, FP64 divides (the
+// oracle's rounding)
+template <class T>
+__device__ __forceinline__ void div2(T a, T b, T d, T& q, T& r) {
+    if constexpr (sizeof(T) == 4) {
+        const T id = T(1) / d;
+        q = a * id;
+        r = b * id;
+    } else {
+        q = a / d;
+        r = b / d;
+    }
+}
 
 
 // Multiplications whose products must cancel exactly (h_R^2 - h_L^2 with
@@ -51,10 +82,10 @@ template <class T> __device__ __forceinline__ T tmax(T a, T b) { return a > b ? 
 template <class T> __device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
 template <class T> __device__ __forceinline__ T tsgn(T a) { return a > T(0) ? T(1) : (a < T(0) ? T(-1) : T(0)); }
 
-// H^{4/3}.  FP64: H * cbrt(H).  FP32: 2^{(4/3) log2 H} (the f32 unit is built
-// with fast math, so this is two SFU operations; relative error ~2e-7).
+// H^{4/3} in FP64: H * cbrt(H).  The FP32 friction takes H^{-4/3} as
+// 2^{-(4/3) log2 H} instead (two SFU operations in the fast-math build;
+// relative error ~2e-7).
 __device__ __forceinline__ double pow43(double x) { return x * cbrt(x); }
-__device__ __forceinline__ float pow43(float x) { return exp2f(1.33333333f * log2f(x)); }
 
 template <class T>
 __device__ __forceinline__ bool is_wet(T H, T b, T eps) { return H > eps && b < T(WALL_TEST); }
@@ -96,7 +127,13 @@ __device__ __forceinline__ void accel(const Phys<T>& P, T hs, T b, T ux, T uy, c
     T dxp = face_delta(hs, b, E.hs, E.b);
     T dym = face_delta(S.hs, S.b, hs, b);
     T dyp = face_delta(hs, b, N.hs, N.b);
-    T coef = -P.g / (T(4) * P.h * hs);
+    T coef, ih = T(0);
+    if constexpr (sizeof(T) == 4) {
+        ih = T(1) / hs;
+        coef = P.gq * ih;
+    } else {
+        coef = -P.g / (T(4) * P.h * hs);
+    }
     T aPx = coef * (dxm + dxp);
     T aPy = coef * (dym + dyp);
     // viscosity: W, E, S, N; no stress from non-wet neighbours
@@ -105,14 +142,18 @@ __device__ __forceinline__ void accel(const Phys<T>& P, T hs, T b, T ux, T uy, c
     lx = lx + (E.wet ? E.ux - ux : T(0)); ly = ly + (E.wet ? E.uy - uy : T(0));
     lx = lx + (S.wet ? S.ux - ux : T(0)); ly = ly + (S.wet ? S.uy - uy : T(0));
     lx = lx + (N.wet ? N.ux - ux : T(0)); ly = ly + (N.wet ? N.uy - uy : T(0));
-    T cv = P.nu / (P.h * P.h);
+    T cv;
+    if constexpr (sizeof(T) == 4) cv = P.cv;
+    else cv = P.nu / (P.h * P.h);
     T aVx = cv * lx, aVy = cv * ly;
     // Coriolis 2 U x Omega
     T aCx = P.f * uy, aCy = -P.f * ux;
     // wind stress
     T dwx = P.wx - ux, dwy = P.wy - uy;
     T wm = sqrt(dwx * dwx + dwy * dwy);
-    T cw = P.ca * P.ra * wm / hs;
+    T cw;
+    if constexpr (sizeof(T) == 4) cw = P.cara * wm * ih;
+    else cw = P.ca * P.ra * wm / hs;
     T aWx = cw * dwx, aWy = cw * dwy;
     ax = ((aPx + aVx) + aCx) + aWx;
     ay = ((aPy + aVy) + aCy) + aWy;
@@ -123,7 +164,8 @@ __device__ __forceinline__ void accel(const Phys<T>& P, T hs, T b, T ux, T uy, c
 template <class T>
 __device__ __forceinline__ T friction(const Phys<T>& P, T hs, T nm, T ux, T uy) {
     T um = sqrt(ux * ux + uy * uy);
-    return P.g * nm * nm * um / pow43(hs);
+    if constexpr (sizeof(T) == 4) return P.g * nm * nm * um * exp2f(-1.33333333f * log2f(hs));
+    else return P.g * nm * nm * um / pow43(hs);
 }
 
 // Forces of Eqs. 2-4 on a wet cell: the accelerations and the friction
@@ -156,7 +198,12 @@ __device__ __forceinline__ T minmod(T a, T b) {
 // Two-rarefaction approximate Riemann solution (Toro 2001) sampled at
 // x/t = 0; a side with depth <= eps is dry (dry-bed fan).
 template <class T>
-__device__ __forceinline__ void riemann(T g, T eps, T hl, T ul, T hr, T ur, T& h, T& u) {
+__device__ __forceinline__ void riemann(T g, T ig, T eps, T hl, T ul, T hr, T ur, T& h, T& u) {
+    // c^2 / g: FP32 multiplies by 1/g
+    auto c2g = [&](T c) -> T {
+        if constexpr (sizeof(T) == 4) return c * c * ig;
+        else return c * c / g;
+    };
     bool dl = !(hl > eps), dr = !(hr > eps);
     h = T(0);
     u = T(0);
@@ -165,26 +212,26 @@ __device__ __forceinline__ void riemann(T g, T eps, T hl, T ul, T hr, T ur, T& h
     T cr = dr ? T(0) : sqrt(g * hr);
     if (dr) {
         if (ul - cl >= T(0)) { h = hl; u = ul; }
-        else if (ul + T(2) * cl > T(0)) { T c = (ul + T(2) * cl) / T(3); h = c * c / g; u = c; }
+        else if (ul + T(2) * cl > T(0)) { T c = (ul + T(2) * cl) / T(3); h = c2g(c); u = c; }
     } else if (dl) {
         if (ur + cr <= T(0)) { h = hr; u = ur; }
-        else if (ur - T(2) * cr < T(0)) { T c = (T(2) * cr - ur) / T(3); h = c * c / g; u = -c; }
+        else if (ur - T(2) * cr < T(0)) { T c = (T(2) * cr - ur) / T(3); h = c2g(c); u = -c; }
     } else if (T(2) * (cl + cr) <= ur - ul) {
         if (ul - cl >= T(0)) { h = hl; u = ul; }
-        else if (ul + T(2) * cl > T(0)) { T c = (ul + T(2) * cl) / T(3); h = c * c / g; u = c; }
+        else if (ul + T(2) * cl > T(0)) { T c = (ul + T(2) * cl) / T(3); h = c2g(c); u = c; }
         else if (ur + cr <= T(0)) { h = hr; u = ur; }
-        else if (ur - T(2) * cr < T(0)) { T c = (T(2) * cr - ur) / T(3); h = c * c / g; u = -c; }
+        else if (ur - T(2) * cr < T(0)) { T c = (T(2) * cr - ur) / T(3); h = c2g(c); u = -c; }
     } else {
         T us = T(0.5) * (ul + ur) + cl - cr;
         T cs = T(0.5) * (cl + cr) + T(0.25) * (ul - ur);
         if (us >= T(0)) {
             if (ul - cl >= T(0)) { h = hl; u = ul; }
-            else if (us - cs >= T(0)) { T c = (ul + T(2) * cl) / T(3); h = c * c / g; u = c; }
-            else { h = cs * cs / g; u = us; }
+            else if (us - cs >= T(0)) { T c = (ul + T(2) * cl) / T(3); h = c2g(c); u = c; }
+            else { h = c2g(cs); u = us; }
         } else {
             if (ur + cr <= T(0)) { h = hr; u = ur; }
-            else if (us + cs <= T(0)) { T c = (T(2) * cr - ur) / T(3); h = c * c / g; u = -c; }
-            else { h = cs * cs / g; u = us; }
+            else if (us + cs <= T(0)) { T c = (T(2) * cr - ur) / T(3); h = c2g(c); u = -c; }
+            else { h = c2g(cs); u = us; }
         }
     }
 }
@@ -234,7 +281,7 @@ __device__ __forceinline__ void face_flux(const Phys<T>& P, const ECell<T>& L, c
     T un_l = nq == 1 ? wl[1] : wl[2];
     T un_r = nq == 1 ? wr[1] : wr[2];
     T hs, us;
-    riemann(P.g, P.eps, hl, un_l, hr, un_r, hs, us);
+    riemann(P.g, P.ig, P.eps, hl, un_l, hr, un_r, hs, us);
     FH = hs * us;
     FQx = FH * (FH >= T(0) ? wl[3] : wr[3]);
     FQy = FH * (FH >= T(0) ? wl[4] : wr[4]);

@@ -185,6 +185,7 @@ extern "C" SWE_API int swe_step_f32_noalloc(const swe_params* p, const float* H,
     a.P.rain = (float)p->rain_rate;
     a.P.loss = (float)(p->evap_rate + p->infil_rate);
     a.P.dist = (p->rain_rate != 0.0 || p->evap_rate != 0.0 || p->infil_rate != 0.0) ? 1 : 0;
+    phys_derive(a.P);
     a.sp.dx = p->dx;
     a.sp.cfl = p->cfl;
     a.sp.dt_max = p->dt_max;
