@@ -139,7 +139,7 @@ struct FSmem {
     T aU[2][DA][WIN];      // predictor U*
     T bH[DB][WIN];         // particle depth H*
     T cS[9][DC][WIN];      // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y, b, n
-    T sX[5][DX][WIN];      // x slopes of H~, U^, U~'
+    T sX[4][DX][WIN];      // x slopes of H~, U^x, U~'x, U~'y (an x face needs no U^y slope)
     T fX[3][DF][WIN];      // x-face fluxes F_H, F_Qx, F_Qy
     T nS[4][DN][WIN];      // new state H, Ux, Uy with the cell's b
     unsigned long long bar[NBAR];
@@ -264,6 +264,12 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     auto fX = [&](int r) { return FRow<T, S::DF * WIN>{&s.fX[0][r & (S::DF - 1)][0]}; };
     auto nS = [&](int r) { return FRow<T, S::DN * WIN>{&s.nS[0][r & (S::DN - 1)][0]}; };
 
+    // the stages' column ranges for this thread: bit i (1..5) set when
+    // c is in [i, WIN-1-i], bit 6 when c is in [4, WIN-6]
+    unsigned cb = 0u;
+#pragma unroll
+    for (int i = 1; i <= 5; ++i) cb |= (c >= i && c <= WIN - 1 - i) ? (1u << i) : 0u;
+    cb |= (c >= 4 && c <= WIN - 6) ? 64u : 0u;
     int sp = a.src_off[item];
     const int se = a.src_off[item + 1];
     // without point or distributed sources H~ = H exactly: nothing to add
@@ -303,7 +309,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     };
     // S1: forces at t_n and predictor velocity U* (without ACC)
     auto stage1 = [&](int r) {
-        if (!(r >= 1 && r <= nrows - 2 && c >= 1 && c < WIN - 1)) return;
+        if (!(r >= 1 && r <= nrows - 2 && (cb & 2u))) return;
         const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
         const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
         const auto U0 = pU(r);
@@ -327,7 +333,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     };
     // S2: particle area change and H*
     auto stage2 = [&](int r) {
-        if (!(r >= 2 && r <= nrows - 3 && c >= 2 && c < WIN - 2)) return;
+        if (!(r >= 2 && r <= nrows - 3 && (cb & 4u))) return;
         const T H = rH(r)[c];
         T hs = H;
         if (is_wet(H, rB(r)[c], eps)) {
@@ -345,7 +351,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     };
     // S3: forces at t_{n+1/2}, corrector and sources
     auto stage3 = [&](int r) {
-        if (!(r >= 3 && r <= nrows - 4 && c >= 3 && c < WIN - 3)) return;
+        if (!(r >= 3 && r <= nrows - 4 && (cb & 8u))) return;
         const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
         const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
         const T *B0 = bH(r), *Bm = bH(r - 1), *Bp = bH(r + 1);
@@ -421,32 +427,30 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     // S5: MUSCL slopes along x of row r (each cell once; the face fluxes
     // read both sides' slopes)
     auto stage5 = [&](int r) {
-        if (!(r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 5)) return;
+        if (!(r >= 5 && r <= nrows - 6 && (cb & 16u))) return;
         T sx[5];
         slopes(ecell(r, c - 1), ecell(r, c), ecell(r, c + 1), sx);
         const auto X = sX(r);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) X[q][c] = sx[q];
+        X[0][c] = sx[0];
+        X[1][c] = sx[1];
+        X[2][c] = sx[3];
+        X[3][c] = sx[4];
     };
     // S4: MUSCL slopes along y and face fluxes of row r (x faces, and the y
     // face below the row)
     auto stage4 = [&](int r) {
-        if (!(r >= 4 && r <= nrows - 5 && c >= 3 && c < WIN - 3)) return;
+        if (!(r >= 4 && r <= nrows - 5 && (cb & 8u))) return;
         const ECell<T> em = ecell(r - 1, c), e0 = ecell(r, c), ep = ecell(r + 1, c);
         T syc[5];
         slopes(em, e0, ep, syc);
         if (r >= 5) face_flux(P, em, syPrev, e0, syc, 2, fyCur[0], fyCur[1], fyCur[2]);
 #pragma unroll
         for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
-        if (r >= 5 && r <= nrows - 6 && c >= 4 && c <= WIN - 6) {
+        if (r >= 5 && r <= nrows - 6 && (cb & 64u)) {
             const ECell<T> x1 = ecell(r, c + 1);
             const auto X = sX(r);
-            T sL[5], sR[5];
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                sL[q] = X[q][c];
-                sR[q] = X[q][c + 1];
-            }
+            const T sL[5] = {X[0][c], X[1][c], T(0), X[2][c], X[3][c]};
+            const T sR[5] = {X[0][c + 1], X[1][c + 1], T(0), X[2][c + 1], X[3][c + 1]};
             T FH, FQx, FQy;
             face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
             const auto F = fX(r);
@@ -457,7 +461,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     };
     // S6: final update of row r (K8)
     auto stage6 = [&](int r) {
-        if (r >= 5 && r <= nrows - 6 && c >= 5 && c <= WIN - 6) {
+        if (r >= 5 && r <= nrows - 6 && (cb & 32u)) {
             const auto FX = fX(r);
             T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
             T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);

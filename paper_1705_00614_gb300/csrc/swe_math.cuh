@@ -190,6 +190,12 @@ __device__ __forceinline__ T cell_speed(const Phys<T>& P, T H, T ux, T uy, T ax,
 
 template <class T>
 __device__ __forceinline__ T minmod(T a, T b) {
+    if constexpr (sizeof(T) == 4) {
+        // the same value without branches (a zero result may carry a's sign):
+        // the smaller magnitude when both have one sign, else zero
+        const float m = fminf(fabsf(a), fabsf(b));
+        return ((__float_as_uint(a) ^ __float_as_uint(b)) & 0x80000000u) ? 0.0f : copysignf(m, a);
+    }
     if (a > T(0) && b > T(0)) return a < b ? a : b;
     if (a < T(0) && b < T(0)) return a > b ? a : b;
     return T(0);

@@ -284,3 +284,27 @@ def test_full_size_16384_sampled_cells(swe):
             assert abs(g - o) <= 1e-5 * sc, (y, x, g, o)
         checked += 1
     assert checked == len(pts)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_dam_break_rows_identical_and_transposed(swe, prec):
+    """A dam break along x over several windows and segments keeps every row
+    bitwise equal with zero y momentum; the same dam break along y is its
+    transpose (bitwise in FP64; the x and y faces run through different
+    code, so FP32 within rounding)."""
+    px = I.dam_break(300, 1.0, 2.0, 1.0, ny=70)
+    py = I.Problem("dam_break_y", I.Params(**{**px.params.__dict__, "nx": 70, "ny": 300}), px.b.T.copy(),
+                   px.n_manning.T.copy(), px.H.T.copy(), px.Qy.T.copy(), px.Qx.T.copy(), I.Sources.empty())
+    with swe.Solver.from_problem(px, prec, seg_h=16) as a, swe.Solver.from_problem(py, prec, seg_h=16) as b:
+        ia = a.step(60)
+        ib = b.step(60)
+        Hx, Qxx, Qyx = a.get_state()[:3]
+        Hy, Qxy, Qyy = b.get_state()[:3]
+    for q in (Hx, Qxx):
+        assert np.array_equal(q, np.repeat(q[:1], q.shape[0], axis=0))
+    assert not np.asarray(Qyx).any() and not np.asarray(Qxy).any()
+    assert ia["t"] == ib["t"]
+    if prec == "f64":
+        assert np.array_equal(Hy, Hx.T) and np.array_equal(Qyy, Qxx.T)
+    else:
+        assert_state_close((Hy.T, Qyy.T, Qxy.T), (Hx, Qxx, Qyx), 1e-5)

@@ -364,3 +364,15 @@ def test_source_volume_matches_hydrograph_integral():
     assert abs(vol - integral * 100.0) < 2e-3 * integral * 100.0
     clip = sum(i["clip_vol"] for i in infos)
     assert abs(infos[-1]["mass"] - vol - clip) <= 1e-12 * infos[-1]["mass"]
+
+
+def test_y_invariant_dam_break_keeps_rows_identical():
+    """A dam break along x is the same in every row: after many steps all
+    rows are bitwise equal and the y momentum is exactly zero (the wall
+    rows see no y pressure difference and every y face carries no flux)."""
+    p = I.dam_break(64, 1.0, 2.0, 1.0, ny=24)
+    H, Qx, Qy, t, _ = oracle.run(p, 80)
+    for a in (H, Qx):
+        assert np.array_equal(a, np.repeat(a[:1], a.shape[0], axis=0))
+    assert not Qy.any()
+    assert H[0].max() < 2.0 and H[0].min() > 1.0  # the waves have moved
