@@ -173,8 +173,9 @@ SWE_API int swe_set_solid(swe_ctx* ctx, int32_t n, const int32_t* ix, const int3
 
 /* Advance nsteps time steps (Sec. 2.3 stages I-IV, kernels K2-K8).  tau of
  * each step comes from the state at its start (K3) unless dt_fixed is set;
- * if t_end > 0 the last step is shortened to land on t_end and later steps
- * do nothing.  With info != NULL the stream is synchronised and the step
+ * if t_end > 0 the last step is shortened to land on t_end (the reported
+ * time is then t_end exactly, although in FP32 the state advanced by that
+ * tau rounded to FP32) and later steps do nothing.  With info != NULL the stream is synchronised and the step
  * report copied out; device error bits turn into SWE_ERR_NONFINITE or
  * SWE_ERR_DEVICE_TIMEOUT.  With info == NULL the steps are only enqueued
  * (nsteps >= 2 run as one CUDA graph). */

@@ -32,14 +32,26 @@ namespace swe {
 __device__ __forceinline__ double dmin_(double a, double b) { return a < b ? a : b; }
 
 // tau_n from the max signal speed of the state at t_n (Fig. 2, K3).
-__device__ __forceinline__ double step_tau(const Ctl* ctl, const StepP& sp, int parity) {
+__device__ __forceinline__ double step_tau(const Ctl* ctl, const StepP& sp, int parity, bool* clamped = nullptr) {
     double smax = __longlong_as_double((long long)ctl->smax[parity]);
     double tau;
     if (sp.dt_fixed > 0.0) tau = sp.dt_fixed;
     else if (smax > 0.0) tau = dmin_(sp.dt_max, sp.cfl * sp.dx / smax);
     else tau = sp.dt_max;
-    if (ctl->t_end > 0.0 && ctl->t + tau > ctl->t_end) tau = ctl->t_end - ctl->t;
+    const bool cut = ctl->t_end > 0.0 && ctl->t + tau > ctl->t_end;
+    if (cut) tau = ctl->t_end - ctl->t;
+    if (clamped) *clamped = cut;
     return tau;
+}
+
+// t_{n+1} after a step that applied tau_applied (tau rounded to the state
+// precision): t_n + tau_applied, or t_end exactly when t_end cut the step
+// (in FP32 the rounded tau would otherwise land a few ulps off t_end).
+// Called before ctl->t and ctl->smax[parity] change.
+__device__ __forceinline__ double step_time_after(const Ctl* ctl, const StepP& sp, int parity, double tau_applied) {
+    bool cut = false;
+    step_tau(ctl, sp, parity, &cut);
+    return cut ? ctl->t_end : ctl->t + tau_applied;
 }
 
 // ------------------------------------------------------------------ reductions
@@ -297,14 +309,14 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             U[1][c] = uy;
         }
         if (ACC) {
-            T usx = T(0), usy = T(0);
-            if (wet) {
-                const T den = T(1) + th * rA(2, k)[c];
-                div2(ux + th * rA(0, k)[c], uy + th * rA(1, k)[c], den, usx, usy);
-            }
+            // every lane evaluates (a dry cell's stored accelerations are 0)
+            // and keeps the value where the cell is wet
+            const T den = T(1) + th * rA(2, k)[c];
+            T usx, usy;
+            div2(ux + th * rA(0, k)[c], uy + th * rA(1, k)[c], den, usx, usy);
             const auto A = aU(k);
-            A[0][c] = usx;
-            A[1][c] = usy;
+            A[0][c] = wet ? usx : T(0);
+            A[1][c] = wet ? usy : T(0);
         }
     };
     // S1: forces at t_n and predictor velocity U* (without ACC)
@@ -335,19 +347,17 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     auto stage2 = [&](int r) {
         if (!(r >= 2 && r <= nrows - 3 && (cb & 4u))) return;
         const T H = rH(r)[c];
-        T hs = H;
-        if (is_wet(H, rB(r)[c], eps)) {
-            const auto A0 = aU(r);
-            const T u = A0[0][c], uW = A0[0][c - 1], uE = A0[0][c + 1];
-            const T v = A0[1][c], vS = aU(r - 1)[1][c], vN = aU(r + 1)[1][c];
-            const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
-            const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
-            T D;
-            if constexpr (sizeof(T) == 4) D = ((fxp - fxm) + (fyp - fym)) * P.ih;
-            else D = ((fxp - fxm) + (fyp - fym)) / P.h;
-            hs = H / tmax(T(0.5), T(1) + th * D);
-        }
-        bH(r)[c] = hs;
+        // evaluated on every lane, kept where the cell is wet
+        const auto A0 = aU(r);
+        const T u = A0[0][c], uW = A0[0][c - 1], uE = A0[0][c + 1];
+        const T v = A0[1][c], vS = aU(r - 1)[1][c], vN = aU(r + 1)[1][c];
+        const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
+        const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
+        T D;
+        if constexpr (sizeof(T) == 4) D = ((fxp - fxm) + (fyp - fym)) * P.ih;
+        else D = ((fxp - fxm) + (fyp - fym)) / P.h;
+        const T hw = H / tmax(T(0.5), T(1) + th * D);
+        bH(r)[c] = is_wet(H, rB(r)[c], eps) ? hw : H;
     };
     // S3: forces at t_{n+1/2}, corrector and sources
     auto stage3 = [&](int r) {
@@ -475,16 +485,12 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             }
             const auto C = cS(r);
             T hn = C[0][c] + dth * fh;
-            double clip = 0.0;
-            if (hn < T(0)) {
-                clip = -(double)hn;
-                hn = T(0);
-            }
-            T qxn = T(0), qyn = T(0);
-            if (hn > eps) {
-                qxn = C[5][c] + dth * fqx;
-                qyn = C[6][c] + dth * fqy;
-            }
+            const bool neg = hn < T(0);
+            const double clip = neg ? -(double)hn : 0.0;
+            hn = neg ? T(0) : hn;
+            const bool pos = hn > eps;
+            const T qxn = pos ? C[5][c] + dth * fqx : T(0);
+            const T qyn = pos ? C[6][c] + dth * fqy : T(0);
             const T b = C[7][c];
             const bool wetn = is_wet(hn, b, eps);
             T uxn, uyn;
@@ -669,7 +675,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             ctl->wet = (long long)w;
             ctl->skipped = (long long)sk;
             ctl->tau_last = (double)tauT;
-            ctl->t = ctl->t + (double)tauT;
+            ctl->t = step_time_after(ctl, a.sp, buf, (double)tauT);
             ctl->max_speed = __longlong_as_double((long long)atomicAdd(&ctl->smax[buf ^ 1], 0ull));
             ctl->smax[buf] = 0ull;
             ctl->step = step + 1;
@@ -1108,7 +1114,7 @@ __global__ void ks_finish(const StagedArgs<T> a, int nblocks, int init) {
             ctl->src_vol = sr * h * h;
             ctl->clip_vol = cl * h * h;
             ctl->tau_last = (double)tauT;
-            ctl->t = ctl->t + (double)tauT;
+            ctl->t = step_time_after(ctl, a.sp, buf, (double)tauT);
             ctl->max_speed = __longlong_as_double((long long)ctl->smax[buf ^ 1]);
             ctl->smax[buf] = 0ull;
             ctl->step = ctl->step + 1;

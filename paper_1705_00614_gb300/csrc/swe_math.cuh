@@ -183,8 +183,15 @@ template <class T>
 __device__ __forceinline__ T cell_speed(const Phys<T>& P, T H, T ux, T uy, T ax, T ay) {
     T c = sqrt(P.g * H);
     T us = tmax(fabs(ux), fabs(uy)) + c;
-    T upx = fabs(ux + tsgn(ax) * sqrt(P.h * fabs(ax)));
-    T upy = fabs(uy + tsgn(ay) * sqrt(P.h * fabs(ay)));
+    T upx, upy;
+    if constexpr (sizeof(T) == 4) {
+        // sgn(a) sqrt(h |a|) as a sign transfer (the same value)
+        upx = fabs(ux + copysignf(sqrtf(P.h * fabsf(ax)), ax));
+        upy = fabs(uy + copysignf(sqrtf(P.h * fabsf(ay)), ay));
+    } else {
+        upx = fabs(ux + tsgn(ax) * sqrt(P.h * fabs(ax)));
+        upy = fabs(uy + tsgn(ay) * sqrt(P.h * fabs(ay)));
+    }
     return tmax(us, tmax(upx, upy));
 }
 
