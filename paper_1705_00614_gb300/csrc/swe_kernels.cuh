@@ -288,8 +288,11 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     const bool has_src = sp != se || P.dist;
     T syPrev[5] = {T(0), T(0), T(0), T(0), T(0)};
     T fyPrev[3] = {T(0), T(0), T(0)}, fyCur[3] = {T(0), T(0), T(0)};
-    double acc_mass = 0.0, acc_src = 0.0, acc_clip = 0.0, vmax = 0.0;
-    long long acc_wet = 0;
+    double acc_mass = 0.0, acc_src = 0.0, acc_clip = 0.0;
+    // the signal-speed max in the state precision (a max is exact in any
+    // precision); a thread counts at most a segment's rows of wet cells
+    T vmax = T(0);
+    int acc_wet = 0;
     bool bad = false;
     bool band_wet = false;  // a wet new cell in this column's current stamp band
 
@@ -545,9 +548,10 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             Nb<T> S{Nm[0][c], Nm[3][c], Nm[1][c], Nm[2][c], is_wet(Nm[0][c], Nm[3][c], eps)};
             Nb<T> N{Np[0][c], Np[3][c], Np[1][c], Np[2][c], is_wet(Np[0][c], Np[3][c], eps)};
             accel(P, H, b, ux, uy, W, E, S, N, ax, ay);
-            const double v = (double)cell_speed(P, H, ux, uy, ax, ay);
-            if (!(v <= DBL_MAX)) bad = true;
-            else if (v > vmax) vmax = v;
+            const T v = cell_speed(P, H, ux, uy, ax, ay);
+            const bool fin = v <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX);
+            bad = bad || !fin;
+            vmax = (fin && v > vmax) ? v : vmax;
         }
         if (ACC) {
             const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
@@ -629,7 +633,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     }
 
     // per-CTA partials, the next step's signal speed, and the step report
-    const double bmax = block_max<NT>(vmax, s.red);
+    const double bmax = block_max<NT>((double)vmax, s.red);
     const double bmass = block_sum<NT>(acc_mass, s.red);
     const double bsrc = block_sum<NT>(acc_src, s.red);
     const double bclip = block_sum<NT>(acc_clip, s.red);
