@@ -80,7 +80,7 @@ typedef struct {
     double rho_air_over_rho; /* rho_a / rho, Eq. 4 */
     void* cuda_stream;     /* cudaStream_t to run on; borrowed, may be NULL */
     int32_t tile_w;        /* fused mode: output columns per CTA (0 = auto) */
-    int32_t seg_h;         /* fused mode: output rows per CTA (0 = auto) */
+    int32_t seg_h;         /* fused mode: output rows per CTA (0 = auto: a launch-cost model, at most 256 with skip_dry) */
     int32_t skip_dry;      /* fused mode, 0 or 1: skip dry tiles (the wet-block
                               test of the paper's kernel K1, Sec. 3).  A work
                               item whose window (its cells and the 6-cell ring

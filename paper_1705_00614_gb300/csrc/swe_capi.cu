@@ -239,6 +239,8 @@ FusedArgs<T> fused_args(const swe_ctx* c, bool closed = false) {
 bool is64(const swe_ctx* c) { return c->p.precision == SWE_F64; }
 
 // Launch-cost model of the fused kernel: waves of CTAs times rows per CTA.
+// With dry-tile skipping the few wet items set the step time (each streams
+// its rows one after another), so segments stay at most 256 rows high.
 void choose_tiling(swe_ctx* c) {
     const int nx = c->p.nx, ny = c->p.ny;
     c->ntx = (nx + TW - 1) / TW;
@@ -246,8 +248,9 @@ void choose_tiling(swe_ctx* c) {
     double best_cost = 1e300;
     const int cand[] = {8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024};
     const int slots = std::max(1, c->sm_count * std::max(1, c->occ));
+    const int cap = c->p.skip_dry ? 256 : 1 << 30;
     for (int sh : cand) {
-        if (sh > ny && best != 0) break;
+        if ((sh > ny || sh > cap) && best != 0) break;
         const long long items = (long long)c->ntx * ((ny + sh - 1) / sh);
         const double waves = std::ceil((double)items / slots);
         const double cost = waves * (std::min(sh, ny) + 2 * HALO);
