@@ -21,6 +21,7 @@
 #pragma once
 
 #include <float.h>
+#include <limits.h>
 
 #include "swe_launch.h"
 #include "swe_ptx.cuh"
@@ -1017,65 +1018,73 @@ __global__ void ks_final(const StagedArgs<T> a) {
 // Signal speed (and mass) of the state in buffer `which` (0: current,
 // 1: next); atomicMax into the smax slot of that state's step parity.
 // Where the grid stores accelerations, also writes them for that state.
-// (i0, j0): origin of the cells the launch covers (a region of the grid);
+// [i0, i1) x [j0, j1): the cells the launch covers (a region of the grid);
 // parts = 0 leaves the per-block partial sums alone.
+// A block of 32 x 8 threads covers 32 columns x SPEED_ROWS rows (each
+// thread SPEED_ROWS / 8 rows): the speed max is kept in T (a max is exact
+// in any precision) and the wet count as an integer, so FP64 work (slow on
+// this part) is one conversion and one add per cell for the mass plus one
+// set of block reductions per SPEED_ROWS * 32 cells.
+constexpr int SPEED_ROWS = 64;
+
 template <class T>
-__global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 0, int parts = 1) {
+__global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 0, int parts = 1,
+                         int i1 = INT_MAX, int j1 = INT_MAX) {
     __shared__ double red[8];
-    const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x, j = j0 + blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
+    const int jb = j0 + blockIdx.y * SPEED_ROWS + threadIdx.y;
+    const int jend = min(min(a.g.ny, j1), j0 + (int)(blockIdx.y + 1) * SPEED_ROWS);
     const int buf = ctl_buf(a.ctl) ^ which;
-    double v = 0.0, mass = 0.0, wet = 0.0;
+    const long long stamp = *(volatile const long long*)&a.ctl->step + which;
+    T vmax = T(0);
+    double mass = 0.0;
+    int wet = 0;
     bool bad = false;
-    if (i < a.g.nx && j < a.g.ny) {
-        const PAcc<T> at{a.g.pitch};
-        const T* Hs = a.g.H[buf];
-        const T* Qx = a.g.Qx[buf];
-        const T* Qy = a.g.Qy[buf];
-        const T eps = a.P.eps;
-        auto nb = [&](size_t k) {
-            Nb<T> n;
-            n.hs = Hs[k];
-            n.b = a.g.b[k];
-            n.wet = is_wet(n.hs, n.b, eps);
-            n.ux = n.wet ? Qx[k] / n.hs : T(0);
-            n.uy = n.wet ? Qy[k] / n.hs : T(0);
-            return n;
-        };
-        const size_t k = at(i, j);
-        const Nb<T> C = nb(k);
-        mass = (double)C.hs;
-        if (C.wet) {
-            wet = 1.0;
-            if (a.act)
-                a.act[(size_t)(j >> ACT_LY) * a.act_nbx + (i >> ACT_LX)] =
-                    *(volatile const long long*)&a.ctl->step + which;
-            T ax, ay, phi;
-            forces(a.P, C.hs, C.b, a.g.n[k], C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)), nb(at(i, j - 1)),
-                   nb(at(i, j + 1)), ax, ay, phi);
-            v = (double)cell_speed(a.P, C.hs, C.ux, C.uy, ax, ay);
-            if (!(v <= DBL_MAX)) {
-                bad = true;
-                v = 0.0;
+    const PAcc<T> at{a.g.pitch};
+    const T* Hs = a.g.H[buf];
+    const T* Qx = a.g.Qx[buf];
+    const T* Qy = a.g.Qy[buf];
+    const T eps = a.P.eps;
+    auto nb = [&](size_t k) {
+        Nb<T> n;
+        n.hs = Hs[k];
+        n.b = a.g.b[k];
+        n.wet = is_wet(n.hs, n.b, eps);
+        n.ux = n.wet ? Qx[k] / n.hs : T(0);
+        n.uy = n.wet ? Qy[k] / n.hs : T(0);
+        return n;
+    };
+    if (i < a.g.nx && i < i1) {
+        for (int j = jb; j < jend; j += 8) {
+            const size_t k = at(i, j);
+            const Nb<T> C = nb(k);
+            mass += (double)C.hs;
+            if (!(C.hs >= T(0) && C.hs <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX))) bad = true;
+            T ax = T(0), ay = T(0), phi = T(0);
+            if (C.wet) {
+                ++wet;
+                if (a.act) a.act[(size_t)(j >> ACT_LY) * a.act_nbx + (i >> ACT_LX)] = stamp;
+                forces(a.P, C.hs, C.b, a.g.n[k], C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)),
+                       nb(at(i, j - 1)), nb(at(i, j + 1)), ax, ay, phi);
+                const T v = cell_speed(a.P, C.hs, C.ux, C.uy, ax, ay);
+                const bool fin = v <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX);
+                bad = bad || !fin;
+                vmax = (fin && v > vmax) ? v : vmax;
             }
             if (a.g.A[buf][0]) {
                 a.g.A[buf][0][k] = ax;
                 a.g.A[buf][1][k] = ay;
                 a.g.A[buf][2][k] = phi;
             }
-        } else if (a.g.A[buf][0]) {
-            a.g.A[buf][0][k] = T(0);
-            a.g.A[buf][1][k] = T(0);
-            a.g.A[buf][2][k] = T(0);
         }
-        if (!(mass <= DBL_MAX) || !(mass >= 0.0)) bad = true;
     }
-    const double bm = block_max<256>(v, red);
+    const double bm = block_max<256>((double)vmax, red);
     const double bs = block_sum<256>(mass, red);
-    const double bw = block_sum<256>(wet, red);
+    const double bw = block_sum<256>((double)wet, red);
     const int anybad = __syncthreads_or(bad);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         const int bl = blockIdx.y * gridDim.x + blockIdx.x;
-        const int slot = (int)((*(volatile const long long*)&a.ctl->step + which) & 1);
+        const int slot = (int)(stamp & 1);
         atomicMax(&a.ctl->smax[slot], (unsigned long long)__double_as_longlong(bm));
         if (anybad) atomicOr(&a.ctl->err, (unsigned)ERR_NONFINITE);
         if (which == 0 && parts) {
@@ -1083,6 +1092,11 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
             a.parts[bl].wet = (int)bw;
         }
     }
+}
+
+template <class T>
+dim3 speed_grid(int ni, int nj) {
+    return dim3((ni + 31) / 32, (nj + SPEED_ROWS - 1) / SPEED_ROWS);
 }
 
 // Reduce the partials of a staged step (fixed order) and advance the control
@@ -1149,7 +1163,7 @@ cudaError_t launch_staged(const StagedArgs<T>& a, cudaStream_t st) {
     ks_flux<T><<<grdx, blk, 0, st>>>(a, 0);
     ks_flux<T><<<grdy, blk, 0, st>>>(a, 1);
     ks_final<T><<<grd, blk, 0, st>>>(a);
-    ks_speed<T><<<grd, blk, 0, st>>>(a, 1);
+    ks_speed<T><<<speed_grid<T>(a.g.nx, a.g.ny), blk, 0, st>>>(a, 1);
     ks_finish<T><<<1, 256, 0, st>>>(a, nblocks, 0);
     return cudaGetLastError();
 }
@@ -1162,15 +1176,14 @@ static __global__ void k_zero_cur_slot(Ctl* ctl) { ctl->smax[ctl->step & 1] = 0u
 template <class T>
 cudaError_t launch_state_speed_region(const StagedArgs<T>& a, int i0, int j0, int ni, int nj, cudaStream_t st) {
     const dim3 blk(32, 8);
-    const dim3 grd((ni + 31) / 32, (nj + 7) / 8);
-    ks_speed<T><<<grd, blk, 0, st>>>(a, 0, i0, j0, 0);
+    ks_speed<T><<<speed_grid<T>(ni, nj), blk, 0, st>>>(a, 0, i0, j0, 0, i0 + ni, j0 + nj);
     return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st) {
     const dim3 blk(32, 8);
-    const dim3 grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
+    const dim3 grd = speed_grid<T>(a.g.nx, a.g.ny);
     k_zero_cur_slot<<<1, 1, 0, st>>>(a.ctl);
     ks_speed<T><<<grd, blk, 0, st>>>(a, 0);
     ks_finish<T><<<1, 256, 0, st>>>(a, (int)(grd.x * grd.y), 1);
@@ -1181,18 +1194,30 @@ cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st) {
 
 // FP64 host layout -> padded field.  With flag != nullptr, values that are
 // not finite (bit 0) or negative (bit 1, when check_neg) are reported there.
+__device__ __forceinline__ bool nonfinite_bits(float x) {
+    return (__float_as_uint(x) & 0x7F800000u) == 0x7F800000u;
+}
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ull) == 0x7FF0000000000000ull;
+}
+
 template <class T>
 __global__ void k_pack(const double* __restrict__ src, T* __restrict__ dst, int nx, int ny, int pitch,
                        unsigned* flag, int check_neg) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
     if (i < nx) {
         const double v = src[(size_t)j * nx + i];
-        dst[(size_t)(j + PAD) * pitch + (i + PAD)] = (T)v;
+        const T tv = (T)v;
+        dst[(size_t)(j + PAD) * pitch + (i + PAD)] = tv;
         if (flag) {
-            const T tv = (T)v;
-            unsigned bad = (!(fabs(v) <= DBL_MAX) || !(fabs((double)tv) <= DBL_MAX) || !(tv == tv) ||
-                            isinf((double)tv)) ? 1u : 0u;
-            if (check_neg && v < 0.0) bad |= 2u;
+            // the checks on the bits (integer work; FP64 compares are slow on
+            // this part): v infinite or NaN, or its rounding to T overflows
+            // (bit 0); v < 0, i.e. negative, not NaN and not -0 (bit 1)
+            const unsigned long long vb = (unsigned long long)__double_as_longlong(v);
+            const bool vnf = (vb & 0x7FF0000000000000ull) == 0x7FF0000000000000ull;
+            const bool vnan = vnf && (vb & 0x000FFFFFFFFFFFFFull) != 0ull;
+            unsigned bad = (vnf || nonfinite_bits(tv)) ? 1u : 0u;
+            if (check_neg && (vb >> 63) && !vnan && (vb << 1) != 0ull) bad |= 2u;
             if (__any_sync(__activemask(), bad != 0) && bad) atomicOr(flag, bad);
         }
     }
