@@ -11,9 +11,11 @@ Prints one JSON line:
   value        cell-updates/s (Gcell/s) of K device-resident steps (one CUDA
                graph of K launches), max over ranks, all ranks' cells counted
   e2e          the same metric through the C ABI with host buffers: each
-               step uploads the state from pinned host memory
-               (swe_set_state), advances one step (swe_step) and reads the
-               state back (swe_get_state), copies inside the timed region
+               step uploads the state from pinned host memory in the state's
+               precision (swe_set_state_native), advances one step
+               (swe_step) and reads the state back (swe_get_state_native),
+               copies inside the timed region; fp64_host: the same with the
+               FP64 host arrays of swe_set_state / swe_get_state
   roofline     the fused kernel against measured HBM copy bandwidth:
                32 algorithmic bytes per cell (read H, Qx, Qy, b, n; write
                H, Qx, Qy in FP32) over its CUDA-event time per launch;
@@ -671,26 +673,36 @@ def main():
     ms_per_step = ms / args.steps
     value = job_rate(world * cells * args.steps, ms)
 
-    # end to end through the C ABI with pinned host buffers
+    # end to end through the C ABI with pinned host buffers: the state in its
+    # own precision (swe_set_state_native / swe_get_state_native), and for
+    # comparison the FP64 host arrays of swe_set_state / swe_get_state
     shape = (prob.params.ny, prob.params.nx)
-    hb = [torch.empty(shape, dtype=torch.float64, pin_memory=True).numpy() for _ in range(6)]
-    hb[0][...] = prob.H
-    hb[1][...] = prob.Qx
-    hb[2][...] = prob.Qy
-    solver.set_state(hb[0], hb[1], hb[2], 0.0)
-    solver.step(1)
-    solver.get_state_into(hb[3], hb[4], hb[5])
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        solver.set_state(hb[0], hb[1], hb[2], 0.0)
-        solver.step(1, report=False)
-        solver.get_state_into(hb[3], hb[4], hb[5])
-    torch.cuda.synchronize()
-    e2e_s = over_ranks(time.perf_counter() - t0)
-    e2e_val = job_rate(world * cells * args.e2e_steps, e2e_s * 1e3)
-    io_bytes = 3 * cells * 8
+
+    def e2e_leg(tdt, native):
+        hb = [torch.empty(shape, dtype=tdt, pin_memory=True).numpy() for _ in range(6)]
+        hb[0][...] = prob.H
+        hb[1][...] = prob.Qx
+        hb[2][...] = prob.Qy
+        up = solver.set_state_native if native else solver.set_state
+        down = solver.get_state_native_into if native else solver.get_state_into
+        up(hb[0], hb[1], hb[2], 0.0)
+        solver.step(1)
+        down(hb[3], hb[4], hb[5])
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            up(hb[0], hb[1], hb[2], 0.0)
+            solver.step(1, report=False)
+            down(hb[3], hb[4], hb[5])
+        torch.cuda.synchronize()
+        e2e_s = over_ranks(time.perf_counter() - t0)
+        del hb
+        return job_rate(world * cells * args.e2e_steps, e2e_s * 1e3), 3 * cells * (4 if tdt == torch.float32 else 8)
+
+    state_dt = torch.float32 if args.precision == "f32" else torch.float64
+    e2e_val, io_bytes = e2e_leg(state_dt, True)
+    e2e64_val, io64_bytes = e2e_leg(torch.float64, False) if args.precision == "f32" else (e2e_val, io_bytes)
 
     bpc = BYTES_PER_CELL[args.precision]
     achieved = bpc * cells / (ms_per_step * 1e-3) / 1e9
@@ -732,7 +744,10 @@ def main():
                              "algorithmic_bytes_per_cell": bpc},
                 "alu_roofline": alu_roofline(prof, cells, ms_per_step, nsm, clk.summary()),
                 "cpu_baseline": cpu,
-                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes},
+                "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+                        "host_dtype": args.precision, "fp64_host": {"value": e2e64_val, "unit": UNIT,
+                                                                   "h2d_bytes_per_step": io64_bytes,
+                                                                   "d2h_bytes_per_step": io64_bytes}},
                 "gpu_launches": args.steps,
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)

@@ -154,6 +154,12 @@ SWE_API int swe_set_terrain_ext(swe_ctx* ctx, const double* b_ext, const double*
  * Errors: SWE_ERR_ARG (negative depth), SWE_ERR_NONFINITE. */
 SWE_API int swe_set_state(swe_ctx* ctx, const double* H, const double* Qx, const double* Qy, double t);
 
+/* swe_set_state with host arrays in the context's own precision (float for
+ * SWE_F32, double for SWE_F64; nx*ny row-major each): copied straight into
+ * the device planes by 2-D copies, half the bytes of the FP64 arrays for an
+ * FP32 context and no conversion.  Same checks, errors and effects. */
+SWE_API int swe_set_state_native(swe_ctx* ctx, const void* H, const void* Qx, const void* Qy, double t);
+
 /* Sources and drains sigma with source velocity V (Eqs. 1-3).  Cell m at
  * (ix[m], iy[m]) gets sigma = weight[m] * q_{hydro[m]}(t) [m/s], evaluated
  * at t_n + tau/2, where hydrograph r has the row
@@ -184,6 +190,11 @@ SWE_API int swe_step(swe_ctx* ctx, int32_t nsteps, double t_end, swe_step_info* 
 /* Copy the current state to host FP64 arrays (any of H, Qx, Qy may be
  * NULL) and the current time to *t (may be NULL).  Synchronises. */
 SWE_API int swe_get_state(swe_ctx* ctx, double* H, double* Qx, double* Qy, double* t);
+
+/* swe_get_state into host arrays in the context's own precision (float for
+ * SWE_F32, double for SWE_F64): the state's values as they are, by 2-D
+ * copies.  Synchronises. */
+SWE_API int swe_get_state_native(swe_ctx* ctx, void* H, void* Qx, void* Qy, double* t);
 
 /* Device pointers of the current state (first interior cell of H, Qx, Qy),
  * the row pitch in elements and the element size in bytes.  Valid until

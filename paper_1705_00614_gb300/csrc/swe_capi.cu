@@ -318,6 +318,18 @@ int upload_field(swe_ctx* c, const double* host, void* dev, unsigned* flag = nul
     return SWE_OK;
 }
 
+// Host [ny][nx] in the context's precision -> padded device field by one
+// 2-D copy (no staging, no conversion), then the same device checks.
+int upload_native(swe_ctx* c, const void* host, void* dev, unsigned* flag, int check_neg) {
+    const size_t row = (size_t)c->p.nx * c->esz;
+    char* dst = (char*)dev + ((size_t)PAD * c->pitch + PAD) * c->esz;
+    CK(cudaMemcpy2DAsync(dst, (size_t)c->pitch * c->esz, host, row, row, (size_t)c->p.ny, cudaMemcpyHostToDevice,
+                         c->st));
+    CK(is64(c) ? launch_check<double>((const double*)dev, c->p.nx, c->p.ny, c->pitch, c->st, flag, check_neg)
+               : launch_check<float>((const float*)dev, c->p.nx, c->p.ny, c->pitch, c->st, flag, check_neg));
+    return SWE_OK;
+}
+
 // Padded device field (base of the interior shifted by (ox, oy)) -> host
 // FP64 [ny][nx], both sizes given.
 int download_field(swe_ctx* c, const void* dev, double* host, int nx, int ny, long long shift_elems) {
@@ -669,6 +681,37 @@ int batch_sync_all(swe_batch* b) {
 
 }  // namespace
 
+// Reset the control block to time t, upload the three fields with
+// upload(k, check_neg) (k = 0: H, 1: Qx, 2: Qy), check them on the device
+// and compute the first time step's signal speed.
+template <class Up>
+int set_state_with(swe_ctx* c, double t, Up upload) {
+    if (!std::isfinite(t)) return fail(SWE_ERR_NONFINITE, "t not finite");
+    CK(cudaSetDevice(c->dev));
+    // the values are checked on the device while they are copied in
+    Ctl h;
+    std::memset(&h, 0, sizeof(h));
+    h.t = t;
+    *c->ctl_host = h;
+    CK(cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
+    int rc = upload(0, 1);
+    if (!rc) rc = upload(1, 0);
+    if (!rc) rc = upload(2, 0);
+    if (rc) return rc;
+    rc = read_ctl(c);
+    if (rc) return rc;
+    if (c->ctl_host->err) {
+        const unsigned e = c->ctl_host->err;
+        c->has_state = false;
+        if (e & 1u) return fail(SWE_ERR_NONFINITE, "state not finite (in FP64 or after conversion)");
+        return fail(SWE_ERR_ARG, "negative depth");
+    }
+    rc = state_speed(c);
+    if (rc) return rc;
+    c->has_state = true;
+    return SWE_OK;
+}
+
 extern "C" {
 
 void swe_params_default(swe_params* p) {
@@ -882,32 +925,14 @@ int swe_set_terrain_ext(swe_ctx* c, const double* b, const double* n) {
 
 int swe_set_state(swe_ctx* c, const double* H, const double* Qx, const double* Qy, double t) {
     if (!c || !H || !Qx || !Qy) return fail(SWE_ERR_ARG, "null argument");
-    const size_t N = (size_t)c->p.nx * c->p.ny;
-    (void)N;
-    if (!std::isfinite(t)) return fail(SWE_ERR_NONFINITE, "t not finite");
-    CK(cudaSetDevice(c->dev));
-    // the values are checked on the device while they are converted
-    Ctl h;
-    std::memset(&h, 0, sizeof(h));
-    h.t = t;
-    *c->ctl_host = h;
-    CK(cudaMemcpyAsync(c->ctl, c->ctl_host, sizeof(Ctl), cudaMemcpyHostToDevice, c->st));
-    int rc = upload_field(c, H, c->f[0], &c->ctl->err, 1);
-    if (!rc) rc = upload_field(c, Qx, c->f[1], &c->ctl->err, 0);
-    if (!rc) rc = upload_field(c, Qy, c->f[2], &c->ctl->err, 0);
-    if (rc) return rc;
-    rc = read_ctl(c);
-    if (rc) return rc;
-    if (c->ctl_host->err) {
-        const unsigned e = c->ctl_host->err;
-        c->has_state = false;
-        if (e & 1u) return fail(SWE_ERR_NONFINITE, "state not finite (in FP64 or after conversion)");
-        return fail(SWE_ERR_ARG, "negative depth");
-    }
-    rc = state_speed(c);
-    if (rc) return rc;
-    c->has_state = true;
-    return SWE_OK;
+    const double* src[3] = {H, Qx, Qy};
+    return set_state_with(c, t, [&](int k, int neg) { return upload_field(c, src[k], c->f[k], &c->ctl->err, neg); });
+}
+
+int swe_set_state_native(swe_ctx* c, const void* H, const void* Qx, const void* Qy, double t) {
+    if (!c || !H || !Qx || !Qy) return fail(SWE_ERR_ARG, "null argument");
+    const void* src[3] = {H, Qx, Qy};
+    return set_state_with(c, t, [&](int k, int neg) { return upload_native(c, src[k], c->f[k], &c->ctl->err, neg); });
 }
 
 int swe_set_sources(swe_ctx* c, int32_t n, const int32_t* ix, const int32_t* iy, const double* w,
@@ -1062,6 +1087,25 @@ int swe_get_state(swe_ctx* c, double* H, double* Qx, double* Qy, double* t) {
     for (int k = 0; k < 3 && !rc; ++k)
         if (outs[k]) rc = download_field(c, c->f[3 * buf + k], outs[k], c->p.nx, c->p.ny, 0);
     if (rc) return rc;
+    CK(cudaStreamSynchronize(c->st));
+    if (t) *t = c->ctl_host->t;
+    return SWE_OK;
+}
+
+int swe_get_state_native(swe_ctx* c, void* H, void* Qx, void* Qy, double* t) {
+    if (!c) return fail(SWE_ERR_ARG, "null context");
+    if (!c->has_state) return fail(SWE_ERR_STATE, "no state");
+    CK(cudaSetDevice(c->dev));
+    int rc = read_ctl(c);
+    if (rc) return rc;
+    const int buf = (int)(c->ctl_host->step & 1);
+    const size_t row = (size_t)c->p.nx * c->esz;
+    const size_t off = ((size_t)PAD * c->pitch + PAD) * c->esz;
+    void* outs[3] = {H, Qx, Qy};
+    for (int k = 0; k < 3; ++k)
+        if (outs[k])
+            CK(cudaMemcpy2DAsync(outs[k], row, (const char*)c->f[3 * buf + k] + off, (size_t)c->pitch * c->esz, row,
+                                 (size_t)c->p.ny, cudaMemcpyDeviceToHost, c->st));
     CK(cudaStreamSynchronize(c->st));
     if (t) *t = c->ctl_host->t;
     return SWE_OK;

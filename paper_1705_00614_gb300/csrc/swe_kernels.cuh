@@ -1368,6 +1368,20 @@ cudaError_t launch_nest_restrict(const Grid<T>& f, const Ctl* fctl, const Grid<T
     return cudaGetLastError();
 }
 
+// Checks of a state copied into a padded plane in its own precision (the
+// same flags as k_pack): non-finite (bit 0), negative and not NaN or -0
+// (bit 1, with check_neg).
+template <class T>
+__global__ void k_check(const T* __restrict__ plane, int nx, int ny, int pitch, unsigned* flag, int check_neg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i < nx) {
+        const T v = plane[(size_t)(j + PAD) * pitch + (i + PAD)];
+        const bool nf = nonfinite_bits(v);
+        unsigned bad = nf ? 1u : 0u;
+        if (check_neg && v < T(0)) bad |= 2u;
+        if (__any_sync(__activemask(), bad != 0) && bad) atomicOr(flag, bad);
+    }
+}
 template <class T>
 __global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, int nx, int ny, int pitch) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
@@ -1403,6 +1417,12 @@ cudaError_t launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cu
 }
 
 template <class T>
+cudaError_t launch_check(const T* plane, int nx, int ny, int pitch, cudaStream_t st, unsigned* flag, int check_neg) {
+    k_check<T><<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(plane, nx, ny, pitch, flag, check_neg);
+    return cudaGetLastError();
+}
+
+template <class T>
 cudaError_t launch_unpack(const T* src, double* dst, int nx, int ny, int pitch, cudaStream_t st) {
     k_unpack<T><<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(src, dst, nx, ny, pitch);
     return cudaGetLastError();
@@ -1424,6 +1444,7 @@ cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cud
     template cudaError_t launch_state_speed<T>(const StagedArgs<T>&, cudaStream_t);                  \
     template cudaError_t launch_state_speed_region<T>(const StagedArgs<T>&, int, int, int, int, cudaStream_t); \
     template cudaError_t launch_pack<T>(const double*, T*, int, int, int, cudaStream_t, unsigned*, int); \
+    template cudaError_t launch_check<T>(const T*, int, int, int, cudaStream_t, unsigned*, int);      \
     template cudaError_t launch_unpack<T>(const T*, double*, int, int, int, cudaStream_t);           \
     template cudaError_t launch_scatter<T>(T*, const int*, const double*, int, cudaStream_t);        \
     template cudaError_t launch_fill_bed<T>(T*, int, int, int, cudaStream_t);                        \

@@ -168,6 +168,8 @@ template <class T>
 cudaError_t launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cudaStream_t st,
                        unsigned* flag = nullptr, int check_neg = 0);
 template <class T>
+cudaError_t launch_check(const T* plane, int nx, int ny, int pitch, cudaStream_t st, unsigned* flag, int check_neg);
+template <class T>
 cudaError_t launch_unpack(const T* src, double* dst, int nx, int ny, int pitch, cudaStream_t st);
 // dst[idx[m]] = val[m]
 template <class T>

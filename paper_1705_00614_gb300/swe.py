@@ -27,7 +27,8 @@ API = ["swe_params_default", "swe_create", "swe_set_terrain", "swe_set_state", "
        "swe_batch_destroy", "swe_cnn_create", "swe_cnn_num_params", "swe_cnn_set_params", "swe_cnn_get_params",
        "swe_cnn_forward", "swe_cnn_gradients", "swe_cnn_train_step", "swe_cnn_destroy", "swe_restrict_state",
        "swe_closure_features", "swe_closure_targets", "swe_closure_attach", "swe_step_closed",
-       "swe_set_terrain_ext", "swe_nest_create", "swe_nest_step", "swe_nest_destroy"]
+       "swe_set_terrain_ext", "swe_nest_create", "swe_nest_step", "swe_nest_destroy", "swe_set_state_native",
+       "swe_get_state_native"]
 CNN_CHANNELS = (5, 32, 32, 32, 3)
 SWE_PAD = 10
 NOALLOC_MAX_ITEMS = 7000
@@ -93,6 +94,10 @@ def load(path=None):
     L.swe_set_solid.argtypes = [ctypes.c_void_p, ctypes.c_int32, _ip, _ip, ctypes.POINTER(ctypes.c_uint8)]
     L.swe_step.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_double, ctypes.POINTER(StepInfo)]
     L.swe_get_state.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
+    L.swe_set_state_native.restype = ctypes.c_int
+    L.swe_set_state_native.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_double]
+    L.swe_get_state_native.restype = ctypes.c_int
+    L.swe_get_state_native.argtypes = [ctypes.c_void_p] * 4 + [_dp]
     L.swe_get_device_ptrs.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
@@ -215,6 +220,7 @@ class Solver:
         p = make_params(params, precision, mode, stream, seg_h, skip_dry, ghost_ring)
         self.params = params
         self.nx, self.ny = params.nx, params.ny
+        self.dtype = np.float32 if precision == "f32" else np.float64
         h = ctypes.c_void_p()
         _check(self.L, self.L.swe_create(ctypes.byref(p), ctypes.byref(h)))
         self.h = h
@@ -264,6 +270,27 @@ class Solver:
     def set_state(self, H, Qx, Qy, t=0.0):
         H, Qx, Qy = _f64(H), _f64(Qx), _f64(Qy)
         _check(self.L, self.L.swe_set_state(self.h, _ptr(H), _ptr(Qx), _ptr(Qy), float(t)))
+
+    def _native(self, a, writable=False):
+        if not (isinstance(a, np.ndarray) and a.dtype == self.dtype and a.flags.c_contiguous
+                and a.shape == (self.ny, self.nx)) or (writable and not a.flags.writeable):
+            raise ValueError(f"expected a C-contiguous {np.dtype(self.dtype).name} array of shape "
+                             f"({self.ny}, {self.nx})")
+        return ctypes.c_void_p(a.ctypes.data)
+
+    def set_state_native(self, H, Qx, Qy, t=0.0):
+        """swe_set_state_native: arrays in the context's precision (float32
+        for f32, float64 for f64), e.g. pinned host buffers; no conversion."""
+        _check(self.L, self.L.swe_set_state_native(self.h, self._native(H), self._native(Qx), self._native(Qy),
+                                                   float(t)))
+
+    def get_state_native_into(self, H, Qx, Qy):
+        """swe_get_state_native into caller-owned arrays in the context's
+        precision; returns t."""
+        t = ctypes.c_double()
+        _check(self.L, self.L.swe_get_state_native(self.h, self._native(H, True), self._native(Qx, True),
+                                                   self._native(Qy, True), ctypes.byref(t)))
+        return t.value
 
     def set_sources(self, src):
         n = len(src)

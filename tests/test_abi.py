@@ -91,3 +91,16 @@ def test_create_rejects_bad_arguments_before_touching_the_device(lib):
             setattr(q, k, v)
         assert lib.swe_create(ctypes.byref(q), ctypes.byref(h)) == -1
         assert lib.swe_last_error()
+
+
+def test_state_calls_reject_null_arguments_before_touching_the_device(lib):
+    z = ctypes.c_void_p()
+    buf = (ctypes.c_double * 4)()
+    t = ctypes.c_double()
+    for rc in (lib.swe_set_state_native(None, buf, buf, buf, 0.0),
+               lib.swe_set_state_native(z, None, buf, buf, 0.0),
+               lib.swe_get_state_native(None, buf, buf, buf, ctypes.byref(t)),
+               lib.swe_set_state(None, ctypes.cast(buf, swe._dp), ctypes.cast(buf, swe._dp),
+                                 ctypes.cast(buf, swe._dp), 0.0),
+               lib.swe_get_state(None, None, None, None, None)):
+        assert rc == -1
