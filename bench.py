@@ -26,8 +26,9 @@ Prints one JSON line:
                actually bound by: warp instructions per cell (committed ncu
                summary) x cells / time, over SMs x 4 schedulers x the SM
                clock sampled during the timed region
-  cpu_baseline the FP64 CPU oracle on a bounded crop of the same workload
-``--impl reference`` times the oracle alone on the host cores.
+  cpu_baseline the FP64 CPU oracle on a bounded crop of the same workload,
+               one process per host core
+``--impl reference`` times the oracle alone on the host cores (the same way).
 """
 import argparse
 import hashlib
@@ -539,6 +540,52 @@ def oracle_rate(prob, steps, cells_hint=None):
     return cells / dt / 1e9, dt
 
 
+_BARRIER = None
+
+
+def _oracle_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_worker(job):
+    prob, steps = job
+    import oracle
+    bd = oracle._Bound(prob)
+    H, Qx, Qy, t = prob.H, prob.Qx, prob.Qy, 0.0
+    _BARRIER.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        H, Qx, Qy, info, _ = oracle.step(prob, H, Qx, Qy, t, bound=bd)
+        t = info["t_new"]
+    return time.perf_counter() - t0
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate_procs(prob, steps, procs):
+    """The oracle as it stands on `procs` host cores at once: one spawned
+    process per core, all on the same crop, started together by a barrier.
+    Returns (all processes' cell-updates / the slowest one's time, in G/s;
+    that time in s)."""
+    import oracle
+    oracle.build()
+    if procs <= 1:
+        return oracle_rate(prob, steps)
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    barrier = ctx.Barrier(procs)
+    with ctx.Pool(procs, initializer=_oracle_init, initargs=(barrier,)) as pool:
+        dts = pool.map(_oracle_worker, [(prob, steps)] * procs)
+    dt = max(dts)
+    return prob.params.nx * prob.params.ny * steps * procs / dt / 1e9, dt
+
+
 def run_reference(args, rank, world):
     """The oracle as it stands, on the host cores, on crops of the workload."""
     if rank != 0:
@@ -547,16 +594,18 @@ def run_reference(args, rank, world):
     n = args.ref_crop
     y0 = int(prob.sources.iy.min()) - n // 2
     c = crop(prob, max(0, y0), 0, n)
+    procs = args.cpu_procs or host_cores()
     oracle_rate(c, args.warmup)
-    val, dt = oracle_rate(c, args.steps)
+    val, dt = oracle_rate_procs(c, args.steps, procs)
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
             "config": {"workload": args.workload, "sample": f"{n}x{n} crop at the inflow strip",
-                       "parallelism": "single core"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} oracle steps of a {n}x{n} crop of {args.workload}"},
+                       "parallelism": f"{procs} host cores, one oracle process each"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps of a {n}x{n} crop of {args.workload} "
+                                       f"in each of {procs} processes"},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -573,6 +622,8 @@ def main():
     ap.add_argument("--ref-crop", type=int, default=768)
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-procs", type=int, default=0,
+                    help="oracle processes for the CPU baseline and the reference arm (0 = one per host core)")
     ap.add_argument("--skip-dry", action="store_true",
                     help="skip dry work items (the paper's K1 wet-block test); off for the headline")
     ap.add_argument("--seg-h", type=int, default=0, help="output rows per work item (0 = automatic)")
@@ -722,9 +773,11 @@ def main():
             n = args.ref_crop
             y0 = int(prob.sources.iy.min()) - n // 2
             c = crop(prob, max(0, y0), 0, n)
-            val, dt = oracle_rate(c, args.cpu_steps)
-            cpu = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{args.cpu_steps} FP64 oracle steps of a {n}x{n} crop at the inflow strip ({dt:.1f} s)"}
+            procs = args.cpu_procs or host_cores()
+            val, dt = oracle_rate_procs(c, args.cpu_steps, procs)
+            cpu = {"value": val, "unit": UNIT, "cores": procs, "kind": "oracle",
+                   "sample": f"{args.cpu_steps} FP64 oracle steps of a {n}x{n} crop at the inflow strip in each "
+                             f"of {procs} processes, one per host core ({dt:.1f} s)"}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": args.precision, "data": "synthetic",
