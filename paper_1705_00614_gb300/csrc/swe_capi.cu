@@ -370,8 +370,13 @@ int launch_one_step(swe_ctx* c) {
         else CK(launch_staged<float>(staged_args<float>(c), c->st));
     } else {
         if (c->p.ghost_ring == 2) {  // open boundary: extend the state into the ring
-            if (is64(c)) CK(launch_ring_outflow<double>(grid_of<double>(c), c->ctl, c->st));
-            else CK(launch_ring_outflow<float>(grid_of<float>(c), c->ctl, c->st));
+            if (is64(c)) {
+                CK(launch_ring_outflow<double>(grid_of<double>(c), c->ctl, c->st));
+                CK(launch_band_acc<double>(staged_args<double>(c), c->st));
+            } else {
+                CK(launch_ring_outflow<float>(grid_of<float>(c), c->ctl, c->st));
+                CK(launch_band_acc<float>(staged_args<float>(c), c->st));
+            }
         }
         if (is64(c)) CK(launch_fused<double>(fused_args<double>(c), c->st));
         else CK(launch_fused<float>(fused_args<float>(c), c->st));
@@ -788,9 +793,9 @@ int swe_create(const swe_params* p, swe_ctx** out) {
             return bail(SWE_ERR_CUDA, "stream creation");
         c->own_stream = true;
     }
-    // stored accelerations: fused contexts with wall rings (a ghost ring's
-    // forces change with every fill, so those contexts evaluate them in the kernel)
-    const int nplanes = (p->mode == SWE_FUSED && !p->ghost_ring) ? 14 : 8;
+    // stored accelerations: every fused context (with a ghost ring, the band
+    // a fill changes is refreshed after each fill, launch_band_acc)
+    const int nplanes = p->mode == SWE_FUSED ? 14 : 8;
     for (int k = 0; k < nplanes; ++k) {
         if (cudaMalloc(&c->f[k], c->plane) != cudaSuccess) return bail(SWE_ERR_OOM, "state allocation");
         if (cudaMemsetAsync(c->f[k], 0, c->plane, c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "memset");
@@ -1649,6 +1654,8 @@ int swe_nest_step(swe_nest* n, int32_t ncoarse, swe_step_info* info_c, swe_step_
                                             f->p.eps_dry, f->st)
                  : launch_nest_ring<float>(grid_of<float>(f), f->ctl, grid_of<float>(c), c->ctl, n->ix0, n->iy0, w,
                                            (double)(float)f->p.eps_dry, f->st));
+            CK(d ? launch_band_acc<double>(staged_args<double>(f), f->st)
+                 : launch_band_acc<float>(staged_args<float>(f), f->st));
             rc = swe_step(f, 1, 0.0, nullptr);
             if (rc) return rc;
         }

@@ -21,6 +21,7 @@
 #pragma once
 
 #include <float.h>
+#include <algorithm>
 #include <limits.h>
 
 #include "swe_launch.h"
@@ -1094,6 +1095,67 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
     }
 }
 
+// Stored accelerations (a_x, a_y, phi) of the current state on the band a
+// ghost-ring fill changes: ring cells within HALO of the interior (the
+// fused kernel's predictor reads them) and the first interior row and
+// column (their forces see the ring).  Four strips of width HALO + 1 over
+// a linear index; no speed or mass report (the ring is not part of either).
+template <class T>
+__global__ void k_band_acc(const StagedArgs<T> a) {
+    constexpr int B = HALO + 1;
+    const int W = a.g.nx + 2 * HALO;
+    const long long ntop = (long long)B * W;
+    const long long nside = (long long)max(0, a.g.ny - 2) * B;
+    long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i, j;
+    if (idx < ntop) {
+        j = -HALO + (int)(idx / W);
+        i = -HALO + (int)(idx % W);
+    } else if ((idx -= ntop) < ntop) {
+        j = a.g.ny - 1 + (int)(idx / W);
+        i = -HALO + (int)(idx % W);
+    } else if ((idx -= ntop) < nside) {
+        j = 1 + (int)(idx / B);
+        i = -HALO + (int)(idx % B);
+    } else if ((idx -= nside) < nside) {
+        j = 1 + (int)(idx / B);
+        i = a.g.nx - 1 + (int)(idx % B);
+    } else {
+        return;
+    }
+    const int buf = ctl_buf(a.ctl);
+    const PAcc<T> at{a.g.pitch};
+    const T* Hs = a.g.H[buf];
+    const T* Qx = a.g.Qx[buf];
+    const T* Qy = a.g.Qy[buf];
+    const T eps = a.P.eps;
+    auto nb = [&](size_t k) {
+        Nb<T> n;
+        n.hs = Hs[k];
+        n.b = a.g.b[k];
+        n.wet = is_wet(n.hs, n.b, eps);
+        n.ux = n.wet ? Qx[k] / n.hs : T(0);
+        n.uy = n.wet ? Qy[k] / n.hs : T(0);
+        return n;
+    };
+    const size_t k = at(i, j);
+    const Nb<T> C = nb(k);
+    T ax = T(0), ay = T(0), phi = T(0);
+    if (C.wet)
+        forces(a.P, C.hs, C.b, a.g.n[k], C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)), nb(at(i, j - 1)),
+               nb(at(i, j + 1)), ax, ay, phi);
+    a.g.A[buf][0][k] = ax;
+    a.g.A[buf][1][k] = ay;
+    a.g.A[buf][2][k] = phi;
+}
+
+template <class T>
+cudaError_t launch_band_acc(const StagedArgs<T>& a, cudaStream_t st) {
+    const long long n = 2LL * (HALO + 1) * (a.g.nx + 2 * HALO) + 2LL * std::max(0, a.g.ny - 2) * (HALO + 1);
+    k_band_acc<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 template <class T>
 dim3 speed_grid(int ni, int nj) {
     return dim3((ni + 31) / 32, (nj + SPEED_ROWS - 1) / SPEED_ROWS);
@@ -1445,6 +1507,7 @@ cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cud
     template cudaError_t launch_state_speed_region<T>(const StagedArgs<T>&, int, int, int, int, cudaStream_t); \
     template cudaError_t launch_pack<T>(const double*, T*, int, int, int, cudaStream_t, unsigned*, int); \
     template cudaError_t launch_check<T>(const T*, int, int, int, cudaStream_t, unsigned*, int);      \
+    template cudaError_t launch_band_acc<T>(const StagedArgs<T>&, cudaStream_t);                     \
     template cudaError_t launch_unpack<T>(const T*, double*, int, int, int, cudaStream_t);           \
     template cudaError_t launch_scatter<T>(T*, const int*, const double*, int, cudaStream_t);        \
     template cudaError_t launch_fill_bed<T>(T*, int, int, int, cudaStream_t);                        \

@@ -163,6 +163,9 @@ cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st);
 // slot takes the max with the region's (an over-estimate at most).
 template <class T>
 cudaError_t launch_state_speed_region(const StagedArgs<T>& a, int i0, int j0, int ni, int nj, cudaStream_t st);
+// Stored accelerations of the ring band after a ghost-ring fill.
+template <class T>
+cudaError_t launch_band_acc(const StagedArgs<T>& a, cudaStream_t st);
 // FP64 row-major [ny][nx] staging -> padded field of type T, and back.
 template <class T>
 cudaError_t launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cudaStream_t st,
