@@ -269,7 +269,7 @@ def run_closure(args, torch, swe, stream, rank, world):
     X, T = [], []
     for sd in train_seeds:
         x, t = CL.collect(torch, scenario(sd), args.closure_collect, tau_c, norm.inp(), norm.out(), 8, 128, rng,
-                          stream=stream.cuda_stream)
+                          stream=stream.cuda_stream, noise=args.closure_noise)
         X.append(x)
         T.append(t)
     X = torch.cat(X)
@@ -356,7 +356,7 @@ def run_closure(args, torch, swe, stream, rank, world):
                            "scenario": "fractal floodplain, flood release (+2 m over the first quarter) and inflow",
                            "tau_coarse_s": tau_c, "train_seeds": len(train_seeds), "test_seeds": len(test_seeds),
                            "collect_steps_per_seed": args.closure_collect, "train_iters": args.closure_iters,
-                           "dagger_rounds": args.closure_dagger,
+                           "dagger_rounds": args.closure_dagger, "input_noise": args.closure_noise,
                            "final_train_loss": hist[-1][1], "train_wall_s": t_train,
                            "rel_l2": mean, "reported": best,
                            "target": 0.01, "speedup_closed_coarse_vs_fine": speedup,
@@ -618,7 +618,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="floodplain-16384sq-dx2m-flooded")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--ref-crop", type=int, default=768)
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
@@ -634,6 +634,8 @@ def main():
     ap.add_argument("--closure-steps", type=int, default=5000, help="closure workload: longest horizon")
     ap.add_argument("--closure-alpha", default="1",
                     help="closure workload: comma-separated correction scales to evaluate side by side")
+    ap.add_argument("--closure-noise", type=float, default=0.0,
+                    help="closure workload: relative input noise on the coarse states the training pairs start from")
     ap.add_argument("--closure-dagger", type=int, default=0,
                     help="closure workload: rounds of training pairs from the closed model's own trajectory")
     args = ap.parse_args()

@@ -98,11 +98,25 @@ class Norm:
         return np.concatenate([self.inp(), self.out()]).astype(np.float32)
 
 
-def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, crop, rng, stream=None):
+def perturb(H, Qx, Qy, rel, rng):
+    """The state with relative Gaussian noise on the depth and momentum of
+    cells deeper than 5 cm (depths kept >= 0; shallower cells unchanged)."""
+    wet = H > 0.05
+    H2 = np.where(wet, np.maximum(0.0, H * (1.0 + rel * rng.standard_normal(H.shape))), H)
+    Qx2 = np.where(wet, Qx * (1.0 + rel * rng.standard_normal(H.shape)), Qx)
+    Qy2 = np.where(wet, Qy * (1.0 + rel * rng.standard_normal(H.shape)), Qy)
+    return H2, Qx2, Qy2
+
+
+def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, crop, rng, stream=None, noise=0.0):
     """Run the fine grid and, for every coarse step, the coarse step taken
     from the restricted fine state; return standardised (inputs, targets)
     crops as device tensors [S, crop, crop, 16] BF16 and [S, crop, crop, 3]
-    FP32."""
+    FP32.  With noise > 0 the coarse step starts from the restricted fine
+    state perturbed by that relative noise (perturb) while the target stays
+    the restricted fine state one step later, so the network also learns to
+    pull a state that has drifted back (input noise against the distribution
+    shift of closed runs)."""
     cp = coarse_problem(fine_prob)
     nyc, nxc = cp.params.ny, cp.params.nx
     fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
@@ -114,6 +128,9 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
     try:
         for _ in range(steps):
             A.restrict_from(fine)
+            if noise > 0.0:
+                H, Qx, Qy, t = A.get_state()
+                A.set_state(*perturb(H, Qx, Qy, noise, rng), t)
             A.closure_features(norm_in, xfull.data_ptr())
             A.step(1)
             fine.step(4)
