@@ -21,7 +21,7 @@ Prints one JSON line:
                H, Qx, Qy in FP32) over its CUDA-event time per launch;
                traffic = DRAM bytes per launch from the committed ncu
                summary (the kernel also stores the state's accelerations,
-               56 B/cell in all)
+               48 B/cell in all)
   alu_roofline the same kernel against the instruction-issue ceiling it is
                actually bound by: warp instructions per cell (committed ncu
                summary) x cells / time, over SMs x 4 schedulers x the SM

@@ -68,7 +68,7 @@ struct swe_ctx {
     int esz = 4;
     int pitch = 0, rows = 0;
     size_t plane = 0;
-    void* f[14] = {};  // H0 Qx0 Qy0 H1 Qx1 Qy1 b n, then (fused) ax0 ay0 phi0 ax1 ay1 phi1
+    void* f[8 + 2 * NACC] = {};  // H0 Qx0 Qy0 H1 Qx1 Qy1 b n, then (fused) ax0 ay0 ax1 ay1
     Ctl* ctl = nullptr;
     Ctl* ctl_host = nullptr;
     Part* parts = nullptr;
@@ -101,7 +101,7 @@ struct swe_ctx {
     double* d_tmp_d = nullptr;
     size_t tmp_cap = 0;
     CUtensorMap tmH[2], tmQx[2], tmQy[2], tmB, tmN;
-    CUtensorMap tmA[2][3];
+    CUtensorMap tmA[2][NACC];
     cudaGraphExec_t gexec = nullptr;
     int gsteps = 0;
     bool has_state = false;
@@ -139,7 +139,7 @@ Grid<T> grid_of(const swe_ctx* c) {
     g.b = (T*)c->f[6];
     g.n = (T*)c->f[7];
     for (int b = 0; b < 2; ++b)
-        for (int q = 0; q < 3; ++q) g.A[b][q] = (T*)c->f[8 + 3 * b + q];
+        for (int q = 0; q < NACC; ++q) g.A[b][q] = (T*)c->f[8 + NACC * b + q];
     return g;
 }
 
@@ -212,7 +212,7 @@ FusedArgs<T> fused_args(const swe_ctx* c, bool closed = false) {
     a.tmB = c->tmB;
     a.tmN = c->tmN;
     for (int b = 0; b < 2; ++b)
-        for (int q = 0; q < 3; ++q) a.tmA[b][q] = c->tmA[b][q];
+        for (int q = 0; q < NACC; ++q) a.tmA[b][q] = c->tmA[b][q];
     a.g = grid_of<T>(c);
     a.P = phys_of<T>(c->p);
     a.sp = stepp_of(c->p);
@@ -487,7 +487,7 @@ int retile(swe_ctx* c, int seg_h) {
 // Device copy of a context's current state (with its stored accelerations)
 // and control block, for trial runs that must leave the state as it was.
 struct Snapshot {
-    void* planes[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    void* planes[3 + NACC] = {};
     Ctl ctl;
     int buf = 0;
 };
@@ -497,8 +497,8 @@ int snapshot_take(swe_ctx* c, Snapshot& sn) {
     if (rc) return rc;
     sn.ctl = *c->ctl_host;
     sn.buf = (int)(sn.ctl.step & 1);
-    for (int k = 0; k < 6; ++k) {
-        void* src = k < 3 ? c->f[3 * sn.buf + k] : c->f[8 + 3 * sn.buf + (k - 3)];
+    for (int k = 0; k < 3 + NACC; ++k) {
+        void* src = k < 3 ? c->f[3 * sn.buf + k] : c->f[8 + NACC * sn.buf + (k - 3)];
         if (!src) continue;
         if (cudaMalloc(&sn.planes[k], c->plane) != cudaSuccess) return fail(SWE_ERR_OOM, "snapshot");
         CK(cudaMemcpyAsync(sn.planes[k], src, c->plane, cudaMemcpyDeviceToDevice, c->st));
@@ -507,8 +507,8 @@ int snapshot_take(swe_ctx* c, Snapshot& sn) {
 }
 
 int snapshot_restore(swe_ctx* c, Snapshot& sn) {
-    for (int k = 0; k < 6; ++k) {
-        void* dst = k < 3 ? c->f[3 * sn.buf + k] : c->f[8 + 3 * sn.buf + (k - 3)];
+    for (int k = 0; k < 3 + NACC; ++k) {
+        void* dst = k < 3 ? c->f[3 * sn.buf + k] : c->f[8 + NACC * sn.buf + (k - 3)];
         if (dst && sn.planes[k])
             CK(cudaMemcpyAsync(dst, sn.planes[k], c->plane, cudaMemcpyDeviceToDevice, c->st));
     }
@@ -795,7 +795,7 @@ int swe_create(const swe_params* p, swe_ctx** out) {
     }
     // stored accelerations: every fused context (with a ghost ring, the band
     // a fill changes is refreshed after each fill, launch_band_acc)
-    const int nplanes = p->mode == SWE_FUSED ? 14 : 8;
+    const int nplanes = p->mode == SWE_FUSED ? 8 + 2 * NACC : 8;
     for (int k = 0; k < nplanes; ++k) {
         if (cudaMalloc(&c->f[k], c->plane) != cudaSuccess) return bail(SWE_ERR_OOM, "state allocation");
         if (cudaMemsetAsync(c->f[k], 0, c->plane, c->st) != cudaSuccess) return bail(SWE_ERR_CUDA, "memset");
@@ -836,7 +836,7 @@ int swe_create(const swe_params* p, swe_ctx** out) {
         if (!rc) rc = encode_map(c, &c->tmB, c->f[6]);
         if (!rc) rc = encode_map(c, &c->tmN, c->f[7]);
         for (int b = 0; b < 2 && !rc && c->f[8]; ++b)
-            for (int q = 0; q < 3 && !rc; ++q) rc = encode_map(c, &c->tmA[b][q], c->f[8 + 3 * b + q]);
+            for (int q = 0; q < NACC && !rc; ++q) rc = encode_map(c, &c->tmA[b][q], c->f[8 + NACC * b + q]);
         if (rc) {
             std::string m = g_err;
             return bail(rc, m);

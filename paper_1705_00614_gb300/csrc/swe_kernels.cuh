@@ -104,14 +104,16 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 // update (K8); S7 signal speed of the new state (the next step's K3).
 //
 // ACC = true (contexts): S7 also stores the new state's accelerations
-// (a_x, a_y, phi) in a second pair of ping-pong planes, and the next step's
-// S1 loads them instead of evaluating the forces again, so S0 and S1 merge.
+// (a_x, a_y) in a second pair of ping-pong planes, and the next step's S1
+// loads them instead of evaluating the forces again (the friction
+// coefficient, local to the cell, it computes from H, U and n), so S0 and
+// S1 merge.
 // Groups: L = {S0+S1 (lag 0), S2 (2), S3 (4), S7 (9)}, E = {S5 (5),
 // S4 (6), S6 (7)}.
 // ACC = false (caller-owned planes, no acceleration storage): groups
 // L = {S0 (0), S1 (2), S2 (4), S3 (6), S5 (7)}, E = {S4 (8), S6 (9),
 // S7 (11)}.
-// Input rows (H, Qx, Qy, b, n and, with ACC, a_x, a_y, phi) arrive by TMA
+// Input rows (H, Qx, Qy, b, n and, with ACC, a_x, a_y) arrive by TMA
 // one row per copy, PREF rows ahead of the row S0 reads, into per-field
 // row rings.  Every ring holds a power of two of rows, so a row's slot is a
 // mask of its index.  The copy of row k + PREF, issued at iteration k,
@@ -148,7 +150,7 @@ struct FSmem {
     T inQy[RQ][WIN];
     T inB[RB_][WIN];
     T inN[RN][WIN];
-    T inA[3][RA][WIN];     // a_x, a_y, phi at t_n (ACC only)
+    T inA[NACC][RA][WIN];  // a_x, a_y at t_n (ACC only)
     T pU[2][DP][WIN];      // U at t_n (without ACC)
     T aU[2][DA][WIN];      // predictor U*
     T bH[DB][WIN];         // particle depth H*
@@ -188,7 +190,7 @@ __device__ __forceinline__ void issue_row(FSmem<T, ACC>& s, const FusedArgs<T>& 
                                           int gx0, int gy0, unsigned cbase) {
     using S = FSmem<T, ACC>;
     unsigned long long* bar = &s.bar[(cbase + (unsigned)r0) % NBAR];
-    mbar_expect_tx(bar, (ACC ? 8u : 5u) * WIN * sizeof(T));
+    mbar_expect_tx(bar, (ACC ? 5u + (unsigned)NACC : 5u) * WIN * sizeof(T));
     const int y = gy0 + r0;
     tma_load_2d(&s.inH[r0 & (S::RH - 1)][0], &a.tmH[buf], gx0, y, bar);
     tma_load_2d(&s.inQx[r0 & (S::RQ - 1)][0], &a.tmQx[buf], gx0, y, bar);
@@ -197,7 +199,7 @@ __device__ __forceinline__ void issue_row(FSmem<T, ACC>& s, const FusedArgs<T>& 
     tma_load_2d(&s.inN[r0 & (S::RN - 1)][0], &a.tmN, gx0, y, bar);
     if (ACC) {
 #pragma unroll
-        for (int q = 0; q < 3; ++q) tma_load_2d(&s.inA[q][r0 & (S::RA - 1)][0], &a.tmA[buf][q], gx0, y, bar);
+        for (int q = 0; q < NACC; ++q) tma_load_2d(&s.inA[q][r0 & (S::RA - 1)][0], &a.tmA[buf][q], gx0, y, bar);
     }
 }
 
@@ -315,8 +317,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         }
         if (ACC) {
             // every lane evaluates (a dry cell's stored accelerations are 0)
-            // and keeps the value where the cell is wet
-            const T den = T(1) + th * rA(2, k)[c];
+            // and keeps the value where the cell is wet; the friction
+            // coefficient is the cell's own (Eq. 4), from H, U and n
+            const T den = T(1) + th * friction(P, H, rN(k)[c], ux, uy);
             T usx, usy;
             div2(ux + th * rA(0, k)[c], uy + th * rA(1, k)[c], den, usx, usy);
             const auto A = aU(k);
@@ -512,9 +515,6 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                 outH[gi] = hn;
                 outQx[gi] = qxn;
                 outQy[gi] = qyn;
-                // the friction coefficient of the new state is local to the
-                // cell; the next step's predictor reads it with a_x, a_y
-                if (ACC) a.g.A[buf ^ 1][2][gi] = wetn ? friction(P, hn, C[8][c], uxn, uyn) : T(0);
                 acc_mass += (double)hn;
                 acc_clip += clip;
                 acc_wet += wetn ? 1 : 0;
@@ -572,7 +572,6 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                     if (ACC) {
                         a.g.A[buf ^ 1][0][gi] = T(0);
                         a.g.A[buf ^ 1][1][gi] = T(0);
-                        a.g.A[buf ^ 1][2][gi] = T(0);
                     }
                 }
             } else {
@@ -1061,12 +1060,12 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
             const Nb<T> C = nb(k);
             mass += (double)C.hs;
             if (!(C.hs >= T(0) && C.hs <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX))) bad = true;
-            T ax = T(0), ay = T(0), phi = T(0);
+            T ax = T(0), ay = T(0);
             if (C.wet) {
                 ++wet;
                 if (a.act) a.act[(size_t)(j >> ACT_LY) * a.act_nbx + (i >> ACT_LX)] = stamp;
-                forces(a.P, C.hs, C.b, a.g.n[k], C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)),
-                       nb(at(i, j - 1)), nb(at(i, j + 1)), ax, ay, phi);
+                accel(a.P, C.hs, C.b, C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)), nb(at(i, j - 1)),
+                      nb(at(i, j + 1)), ax, ay);
                 const T v = cell_speed(a.P, C.hs, C.ux, C.uy, ax, ay);
                 const bool fin = v <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX);
                 bad = bad || !fin;
@@ -1075,7 +1074,6 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
             if (a.g.A[buf][0]) {
                 a.g.A[buf][0][k] = ax;
                 a.g.A[buf][1][k] = ay;
-                a.g.A[buf][2][k] = phi;
             }
         }
     }
@@ -1095,7 +1093,7 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
     }
 }
 
-// Stored accelerations (a_x, a_y, phi) of the current state on the band a
+// Stored accelerations (a_x, a_y) of the current state on the band a
 // ghost-ring fill changes: ring cells within HALO of the interior (the
 // fused kernel's predictor reads them) and the first interior row and
 // column (their forces see the ring).  Four strips of width HALO + 1 over
@@ -1140,13 +1138,12 @@ __global__ void k_band_acc(const StagedArgs<T> a) {
     };
     const size_t k = at(i, j);
     const Nb<T> C = nb(k);
-    T ax = T(0), ay = T(0), phi = T(0);
+    T ax = T(0), ay = T(0);
     if (C.wet)
-        forces(a.P, C.hs, C.b, a.g.n[k], C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)), nb(at(i, j - 1)),
-               nb(at(i, j + 1)), ax, ay, phi);
+        accel(a.P, C.hs, C.b, C.ux, C.uy, nb(at(i - 1, j)), nb(at(i + 1, j)), nb(at(i, j - 1)), nb(at(i, j + 1)),
+              ax, ay);
     a.g.A[buf][0][k] = ax;
     a.g.A[buf][1][k] = ay;
-    a.g.A[buf][2][k] = phi;
 }
 
 template <class T>

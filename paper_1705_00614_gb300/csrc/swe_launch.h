@@ -15,6 +15,9 @@ namespace swe {
 // Ring of wall cells around every grid (>= the 6-cell dependence radius of
 // one fused step; 10 keeps every TMA box start 16-byte aligned).
 constexpr int PAD = 10;
+// stored accelerations per state buffer: a_x, a_y (the friction coefficient
+// is local to the cell and recomputed from the state by the predictor)
+constexpr int NACC = 2;
 // Fused kernel geometry: a CTA owns a window of WIN columns (one thread per
 // column) and streams it down the rows of its segment; HALO columns on each
 // side are recomputed, so TW = WIN - 2 HALO columns are produced.
@@ -72,13 +75,13 @@ struct Grid {
     T* b;
     T* n;
     // accelerations (a_x, a_y, phi) of the state in each buffer, or null
-    T* A[2][3];
+    T* A[2][NACC];
 };
 
 template <class T>
 struct FusedArgs {
     CUtensorMap tmH[2], tmQx[2], tmQy[2], tmB, tmN;
-    CUtensorMap tmA[2][3];
+    CUtensorMap tmA[2][NACC];
     // wet-block stamps (skip_dry) or null: per 32 x 16-cell block of the
     // interior grid, the last step at which the block held a wet cell
     long long* act;
