@@ -619,7 +619,7 @@ def main():
     ap.add_argument("--workload", default="floodplain-16384sq-dx2m-flooded")
     ap.add_argument("--precision", default="f32", choices=["f32", "f64"])
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--ref-crop", type=int, default=768)
+    ap.add_argument("--ref-crop", type=int, default=1024)
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-procs", type=int, default=0,
