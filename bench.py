@@ -188,6 +188,12 @@ def run_ensemble(args, torch, swe, stream, rank, world):
 _CNN_CH = (5, 32, 32, 32, 3)
 CNN_FWD_FLOP = sum(2 * 9 * a * b for a, b in zip(_CNN_CH[:-1], _CNN_CH[1:]))
 CNN_TRAIN_FLOP = 3 * CNN_FWD_FLOP - 2 * 9 * _CNN_CH[0] * _CNN_CH[1]
+# algorithmic HBM bytes per pixel of the forward pass: read the 16-channel
+# BF16 input (32 B) and each hidden layer's 32 BF16 channels once (3 x 64 B),
+# write the hidden layers (3 x 64 B) and the 3 FP32 outputs (12 B).  With 32
+# channels a 3x3 layer does 144 FLOP per byte moved, below GB300's ridge
+# point (~280), so the forward is bound by HBM, not the tensor cores.
+CNN_FWD_BYTES = 32 + 3 * 64 + 3 * 64 + 12
 
 
 def run_cnn(args, torch, swe, stream, rank, world):
@@ -228,6 +234,8 @@ def run_cnn(args, torch, swe, stream, rank, world):
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, src = (json.load(open(peaks_path))["bf16_tflops"], "measured") if os.path.exists(peaks_path) \
         else (1900.0, "fallback")
+    hbm_peak = json.load(open(peaks_path))["hbm_gbs"] if os.path.exists(peaks_path) else 6800.0
+    fwd_gbs = CNN_FWD_BYTES * px / (ms_fwd * 1e-3) / 1e9
     if rank == 0:
         line = {"metric": "closure CNN training throughput", "value": job_rate(world * px, ms_train),
                 "unit": "Gpixel-steps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -240,6 +248,9 @@ def run_cnn(args, torch, swe, stream, rank, world):
                 "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                              "frac": tflops / peak, "peak_source": src, "traffic": None,
                              "kernel": "k_conv (tcgen05) + k_wgrad (mma.sync), BF16"},
+                "forward_roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                     "frac": fwd_gbs / hbm_peak, "bytes_per_pixel": CNN_FWD_BYTES,
+                                     "kernel": "k_conv x 4 (forward)"},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
 

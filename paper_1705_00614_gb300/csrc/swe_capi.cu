@@ -319,14 +319,13 @@ int upload_field(swe_ctx* c, const double* host, void* dev, unsigned* flag = nul
 }
 
 // Host [ny][nx] in the context's precision -> padded device field by one
-// 2-D copy (no staging, no conversion), then the same device checks.
-int upload_native(swe_ctx* c, const void* host, void* dev, unsigned* flag, int check_neg) {
+// 2-D copy (no staging, no conversion); the values are checked by the speed
+// pass that follows (launch_state_speed with check).
+int upload_native(swe_ctx* c, const void* host, void* dev) {
     const size_t row = (size_t)c->p.nx * c->esz;
     char* dst = (char*)dev + ((size_t)PAD * c->pitch + PAD) * c->esz;
     CK(cudaMemcpy2DAsync(dst, (size_t)c->pitch * c->esz, host, row, row, (size_t)c->p.ny, cudaMemcpyHostToDevice,
                          c->st));
-    CK(is64(c) ? launch_check<double>((const double*)dev, c->p.nx, c->p.ny, c->pitch, c->st, flag, check_neg)
-               : launch_check<float>((const float*)dev, c->p.nx, c->p.ny, c->pitch, c->st, flag, check_neg));
     return SWE_OK;
 }
 
@@ -350,9 +349,9 @@ int read_ctl(swe_ctx* c) {
     return SWE_OK;
 }
 
-int state_speed(swe_ctx* c) {
-    if (is64(c)) CK(launch_state_speed<double>(staged_args<double>(c), c->st));
-    else CK(launch_state_speed<float>(staged_args<float>(c), c->st));
+int state_speed(swe_ctx* c, int check = 0) {
+    if (is64(c)) CK(launch_state_speed<double>(staged_args<double>(c), c->st, check));
+    else CK(launch_state_speed<float>(staged_args<float>(c), c->st, check));
     return SWE_OK;
 }
 
@@ -688,9 +687,10 @@ int batch_sync_all(swe_batch* b) {
 
 // Reset the control block to time t, upload the three fields with
 // upload(k, check_neg) (k = 0: H, 1: Qx, 2: Qy), check them on the device
-// and compute the first time step's signal speed.
+// and compute the first time step's signal speed.  With speed_checks the
+// uploads leave the checks to the speed pass, which then runs first.
 template <class Up>
-int set_state_with(swe_ctx* c, double t, Up upload) {
+int set_state_with(swe_ctx* c, double t, Up upload, bool speed_checks = false) {
     if (!std::isfinite(t)) return fail(SWE_ERR_NONFINITE, "t not finite");
     CK(cudaSetDevice(c->dev));
     // the values are checked on the device while they are copied in
@@ -703,6 +703,10 @@ int set_state_with(swe_ctx* c, double t, Up upload) {
     if (!rc) rc = upload(1, 0);
     if (!rc) rc = upload(2, 0);
     if (rc) return rc;
+    if (speed_checks) {
+        rc = state_speed(c, 1);
+        if (rc) return rc;
+    }
     rc = read_ctl(c);
     if (rc) return rc;
     if (c->ctl_host->err) {
@@ -711,8 +715,10 @@ int set_state_with(swe_ctx* c, double t, Up upload) {
         if (e & 1u) return fail(SWE_ERR_NONFINITE, "state not finite (in FP64 or after conversion)");
         return fail(SWE_ERR_ARG, "negative depth");
     }
-    rc = state_speed(c);
-    if (rc) return rc;
+    if (!speed_checks) {
+        rc = state_speed(c);
+        if (rc) return rc;
+    }
     c->has_state = true;
     return SWE_OK;
 }
@@ -937,7 +943,7 @@ int swe_set_state(swe_ctx* c, const double* H, const double* Qx, const double* Q
 int swe_set_state_native(swe_ctx* c, const void* H, const void* Qx, const void* Qy, double t) {
     if (!c || !H || !Qx || !Qy) return fail(SWE_ERR_ARG, "null argument");
     const void* src[3] = {H, Qx, Qy};
-    return set_state_with(c, t, [&](int k, int neg) { return upload_native(c, src[k], c->f[k], &c->ctl->err, neg); });
+    return set_state_with(c, t, [&](int k, int) { return upload_native(c, src[k], c->f[k]); }, true);
 }
 
 int swe_set_sources(swe_ctx* c, int32_t n, const int32_t* ix, const int32_t* iy, const double* w,

@@ -1029,7 +1029,7 @@ constexpr int SPEED_ROWS = 64;
 
 template <class T>
 __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 0, int parts = 1,
-                         int i1 = INT_MAX, int j1 = INT_MAX) {
+                         int i1 = INT_MAX, int j1 = INT_MAX, int check = 0) {
     __shared__ double red[8];
     const int i = i0 + blockIdx.x * blockDim.x + threadIdx.x;
     const int jb = j0 + blockIdx.y * SPEED_ROWS + threadIdx.y;
@@ -1039,7 +1039,7 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
     T vmax = T(0);
     double mass = 0.0;
     int wet = 0;
-    bool bad = false;
+    bool bad = false, neg = false;
     const PAcc<T> at{a.g.pitch};
     const T* Hs = a.g.H[buf];
     const T* Qx = a.g.Qx[buf];
@@ -1059,7 +1059,14 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
             const size_t k = at(i, j);
             const Nb<T> C = nb(k);
             mass += (double)C.hs;
-            if (!(C.hs >= T(0) && C.hs <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX))) bad = true;
+            if (check) {
+                // a state just copied in: non-finite H, Qx or Qy (bit 0);
+                // negative depth (bit 1; not NaN, not -0)
+                bad = bad || nonfinite_bits(C.hs) || nonfinite_bits(Qx[k]) || nonfinite_bits(Qy[k]);
+                neg = neg || C.hs < T(0);
+            } else if (!(C.hs >= T(0) && C.hs <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX))) {
+                bad = true;
+            }
             T ax = T(0), ay = T(0);
             if (C.wet) {
                 ++wet;
@@ -1081,11 +1088,13 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
     const double bs = block_sum<256>(mass, red);
     const double bw = block_sum<256>((double)wet, red);
     const int anybad = __syncthreads_or(bad);
+    const int anyneg = __syncthreads_or(neg);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         const int bl = blockIdx.y * gridDim.x + blockIdx.x;
         const int slot = (int)(stamp & 1);
         atomicMax(&a.ctl->smax[slot], (unsigned long long)__double_as_longlong(bm));
         if (anybad) atomicOr(&a.ctl->err, (unsigned)ERR_NONFINITE);
+        if (anyneg) atomicOr(&a.ctl->err, 2u);
         if (which == 0 && parts) {
             a.parts[bl].mass = bs;
             a.parts[bl].wet = (int)bw;
@@ -1240,11 +1249,11 @@ cudaError_t launch_state_speed_region(const StagedArgs<T>& a, int i0, int j0, in
 }
 
 template <class T>
-cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st) {
+cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st, int check) {
     const dim3 blk(32, 8);
     const dim3 grd = speed_grid<T>(a.g.nx, a.g.ny);
     k_zero_cur_slot<<<1, 1, 0, st>>>(a.ctl);
-    ks_speed<T><<<grd, blk, 0, st>>>(a, 0);
+    ks_speed<T><<<grd, blk, 0, st>>>(a, 0, 0, 0, 1, INT_MAX, INT_MAX, check);
     ks_finish<T><<<1, 256, 0, st>>>(a, (int)(grd.x * grd.y), 1);
     return cudaGetLastError();
 }
@@ -1253,13 +1262,6 @@ cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st) {
 
 // FP64 host layout -> padded field.  With flag != nullptr, values that are
 // not finite (bit 0) or negative (bit 1, when check_neg) are reported there.
-__device__ __forceinline__ bool nonfinite_bits(float x) {
-    return (__float_as_uint(x) & 0x7F800000u) == 0x7F800000u;
-}
-__device__ __forceinline__ bool nonfinite_bits(double x) {
-    return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ull) == 0x7FF0000000000000ull;
-}
-
 template <class T>
 __global__ void k_pack(const double* __restrict__ src, T* __restrict__ dst, int nx, int ny, int pitch,
                        unsigned* flag, int check_neg) {
@@ -1427,20 +1429,6 @@ cudaError_t launch_nest_restrict(const Grid<T>& f, const Ctl* fctl, const Grid<T
     return cudaGetLastError();
 }
 
-// Checks of a state copied into a padded plane in its own precision (the
-// same flags as k_pack): non-finite (bit 0), negative and not NaN or -0
-// (bit 1, with check_neg).
-template <class T>
-__global__ void k_check(const T* __restrict__ plane, int nx, int ny, int pitch, unsigned* flag, int check_neg) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
-    if (i < nx) {
-        const T v = plane[(size_t)(j + PAD) * pitch + (i + PAD)];
-        const bool nf = nonfinite_bits(v);
-        unsigned bad = nf ? 1u : 0u;
-        if (check_neg && v < T(0)) bad |= 2u;
-        if (__any_sync(__activemask(), bad != 0) && bad) atomicOr(flag, bad);
-    }
-}
 template <class T>
 __global__ void k_unpack(const T* __restrict__ src, double* __restrict__ dst, int nx, int ny, int pitch) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
@@ -1476,12 +1464,6 @@ cudaError_t launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cu
 }
 
 template <class T>
-cudaError_t launch_check(const T* plane, int nx, int ny, int pitch, cudaStream_t st, unsigned* flag, int check_neg) {
-    k_check<T><<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(plane, nx, ny, pitch, flag, check_neg);
-    return cudaGetLastError();
-}
-
-template <class T>
 cudaError_t launch_unpack(const T* src, double* dst, int nx, int ny, int pitch, cudaStream_t st) {
     k_unpack<T><<<dim3((nx + 255) / 256, ny), 256, 0, st>>>(src, dst, nx, ny, pitch);
     return cudaGetLastError();
@@ -1500,10 +1482,9 @@ cudaError_t launch_scatter(T* dst, const int* idx, const double* val, int n, cud
     template cudaError_t prepare_fused_batch<T>(int*);                                               \
     template cudaError_t launch_fused_batch<T>(const BatchArgs<T>&, int, cudaStream_t);              \
     template cudaError_t launch_staged<T>(const StagedArgs<T>&, cudaStream_t);                       \
-    template cudaError_t launch_state_speed<T>(const StagedArgs<T>&, cudaStream_t);                  \
+    template cudaError_t launch_state_speed<T>(const StagedArgs<T>&, cudaStream_t, int);                  \
     template cudaError_t launch_state_speed_region<T>(const StagedArgs<T>&, int, int, int, int, cudaStream_t); \
     template cudaError_t launch_pack<T>(const double*, T*, int, int, int, cudaStream_t, unsigned*, int); \
-    template cudaError_t launch_check<T>(const T*, int, int, int, cudaStream_t, unsigned*, int);      \
     template cudaError_t launch_band_acc<T>(const StagedArgs<T>&, cudaStream_t);                     \
     template cudaError_t launch_unpack<T>(const T*, double*, int, int, int, cudaStream_t);           \
     template cudaError_t launch_scatter<T>(T*, const int*, const double*, int, cudaStream_t);        \

@@ -161,7 +161,9 @@ template <class T>
 cudaError_t launch_staged(const StagedArgs<T>& a, cudaStream_t st);
 // Signal speed and mass of the current state (the first step's K3).
 template <class T>
-cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st);
+// With check != 0 the pass also checks a state just copied in: non-finite
+// H, Qx, Qy set error bit 0, a negative depth bit 1.
+cudaError_t launch_state_speed(const StagedArgs<T>& a, cudaStream_t st, int check = 0);
 // The same over a region of the grid, without the mass report: the speed
 // slot takes the max with the region's (an over-estimate at most).
 template <class T>
@@ -173,8 +175,6 @@ cudaError_t launch_band_acc(const StagedArgs<T>& a, cudaStream_t st);
 template <class T>
 cudaError_t launch_pack(const double* src, T* dst, int nx, int ny, int pitch, cudaStream_t st,
                        unsigned* flag = nullptr, int check_neg = 0);
-template <class T>
-cudaError_t launch_check(const T* plane, int nx, int ny, int pitch, cudaStream_t st, unsigned* flag, int check_neg);
 template <class T>
 cudaError_t launch_unpack(const T* src, double* dst, int nx, int ny, int pitch, cudaStream_t st);
 // dst[idx[m]] = val[m]

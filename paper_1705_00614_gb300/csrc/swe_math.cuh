@@ -90,6 +90,14 @@ __device__ __forceinline__ double pow43(double x) { return x * cbrt(x); }
 template <class T>
 __device__ __forceinline__ bool is_wet(T H, T b, T eps) { return H > eps && b < T(WALL_TEST); }
 
+// infinite or NaN, tested on the exponent bits (integer work)
+__device__ __forceinline__ bool nonfinite_bits(float x) {
+    return (__float_as_uint(x) & 0x7F800000u) == 0x7F800000u;
+}
+__device__ __forceinline__ bool nonfinite_bits(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7FF0000000000000ull) == 0x7FF0000000000000ull;
+}
+
 __device__ __forceinline__ bool is_neg_zero(float x) { return __float_as_uint(x) == 0x80000000u; }
 __device__ __forceinline__ bool is_neg_zero(double x) {
     return (unsigned long long)__double_as_longlong(x) == 0x8000000000000000ull;
