@@ -242,7 +242,8 @@ SWE_API int swe_autotune(swe_ctx* ctx, int32_t trial_steps, int32_t* seg_h_out);
 typedef struct swe_batch swe_batch; /* opaque */
 
 /* Batch over n >= 1 distinct SWE_FUSED contexts of one precision on one
- * device, each with a state set.  The batch borrows the contexts (destroy it
+ * device, each with a state set and wall boundaries (ghost_ring = 0;
+ * SWE_ERR_ARG otherwise).  The batch borrows the contexts (destroy it
  * before them) and runs on the first context's stream.  Contexts may still
  * be changed (sources, terrain, gates, state) between batch steps. */
 SWE_API int swe_batch_create(swe_ctx* const* ctxs, int32_t n, swe_batch** out);

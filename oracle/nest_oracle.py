@@ -136,9 +136,7 @@ def outflow_values(H, Qx, Qy, b_ext):
     return out
 
 
-def open_run(prob, b_ext, n_ext, nsteps):
-    """nsteps steps of one grid with open boundaries (fixed steps); returns
-    the interior (H, Qx, Qy)."""
+def _open_steps(prob, b_ext, n_ext, nsteps):
     p = prob.params
     ext = extended(prob, b_ext, n_ext)
     bd = oracle._Bound(ext)
@@ -151,4 +149,16 @@ def open_run(prob, b_ext, n_ext, nsteps):
         He, Qxe, Qye, info, _ = oracle.step(ext, E[0], E[1], E[2], t, bound=bd)
         t = info["t_new"]
         s = [He[sl].copy(), Qxe[sl].copy(), Qye[sl].copy()]
-    return s
+    return s, t
+
+
+def open_run(prob, b_ext, n_ext, nsteps):
+    """nsteps steps of one grid with open boundaries (fixed or CFL steps; a
+    CFL step sees the whole padded extent, ring included); returns the
+    interior (H, Qx, Qy)."""
+    return _open_steps(prob, b_ext, n_ext, nsteps)[0]
+
+
+def open_run_time(prob, b_ext, n_ext, nsteps):
+    """The time open_run reaches."""
+    return _open_steps(prob, b_ext, n_ext, nsteps)[1]

@@ -197,6 +197,7 @@ StagedArgs<T> staged_args(const swe_ctx* c) {
     a.act_nbx = c->act_nbx;
     a.hist = c->d_hist;
     a.nhist = c->d_hist ? c->parts_cap : 0;
+    a.open_ring = c->p.ghost_ring == 2 ? 1 : 0;
     return a;
 }
 
@@ -233,6 +234,7 @@ FusedArgs<T> fused_args(const swe_ctx* c, bool closed = false) {
     a.skip = (c->d_act && !closed && !a.P.dist) ? 1 : 0;
     a.hist = c->d_hist;
     a.corr_plane = (size_t)c->pitch * (size_t)c->rows;
+    a.open_ring = c->p.ghost_ring == 2 ? 1 : 0;
     return a;
 }
 
@@ -1220,6 +1222,7 @@ int swe_batch_create(swe_ctx* const* ctxs, int32_t n, swe_batch** out) {
     for (int k = 0; k < n; ++k) {
         if (!ctxs[k]) return fail(SWE_ERR_ARG, "null context");
         if (ctxs[k]->p.mode != SWE_FUSED) return fail(SWE_ERR_ARG, "batched contexts must be SWE_FUSED");
+        if (ctxs[k]->p.ghost_ring) return fail(SWE_ERR_ARG, "batched contexts need wall boundaries (no ghost ring)");
         if (ctxs[k]->p.precision != ctxs[0]->p.precision) return fail(SWE_ERR_ARG, "mixed precisions");
         if (ctxs[k]->dev != ctxs[0]->dev) return fail(SWE_ERR_ARG, "contexts on different devices");
         if (!ctxs[k]->has_state) return fail(SWE_ERR_STATE, "a context has no state");

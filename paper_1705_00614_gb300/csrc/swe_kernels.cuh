@@ -207,7 +207,7 @@ __device__ __forceinline__ void issue_row(FSmem<T, ACC>& s, const FusedArgs<T>& 
 // `cbase` counts the TMA rows this CTA has waited for so far, so the
 // mbarrier phases stay consistent across the items a persistent CTA runs.
 // Returns false when a bounded wait gave up (the CTA must stop).
-template <class T, bool ACC>
+template <class T, bool ACC, bool OPEN = false>
 __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>& a, const int item,
                                            unsigned& cbase) {
     using LG = Lags<ACC>;
@@ -553,7 +553,15 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             const T v = cell_speed(P, H, ux, uy, ax, ay);
             const bool fin = v <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX);
             bad = bad || !fin;
-            vmax = (fin && v > vmax) ? v : vmax;
+            if constexpr (OPEN) {
+                // with an open ring the edge cells' speeds depend on the
+                // next fill: the band pass after it supplies them
+                const int gy = y0 + r - HALO, gx = x0 + c - HALO;
+                const bool edge = gy == 0 || gy == a.g.ny - 1 || gx == 0 || gx == a.g.nx - 1;
+                vmax = (fin && !edge && v > vmax) ? v : vmax;
+            } else {
+                vmax = (fin && v > vmax) ? v : vmax;
+            }
         }
         if (ACC) {
             const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
@@ -713,13 +721,15 @@ __device__ __forceinline__ void fused_init_barriers(FSmem<T, ACC>& s) {
     __syncthreads();
 }
 
-// One grid: CTA b runs work item b.
-template <class T, bool ACC>
+// One grid: CTA b runs work item b.  OPEN: the grid has an open
+// (zero-gradient) ghost ring, whose band pass supplies the edge cells'
+// signal speeds.
+template <class T, bool ACC, bool OPEN = false>
 __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) k_fused(const __grid_constant__ FusedArgs<T> a) {
     FSmem<T, ACC>& s = fused_smem<T, ACC>();
     fused_init_barriers(s);
     unsigned cbase = 0;
-    fused_item<T, ACC>(s, a, blockIdx.x, cbase);
+    fused_item<T, ACC, OPEN>(s, a, blockIdx.x, cbase);
 }
 
 // Many grids in one persistent launch (batched ensemble): CTAs take
@@ -756,6 +766,8 @@ cudaError_t prepare_fused(int* ctas_per_sm) {
     const size_t smem = fused_smem_bytes_v<T, true>();
     cudaError_t e = cudaFuncSetAttribute(k_fused<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fused<T, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fused<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)fused_smem_bytes_v<T, false>());
     if (e != cudaSuccess) return e;
@@ -778,7 +790,8 @@ cudaError_t launch_fused_batch(const BatchArgs<T>& b, int grid, cudaStream_t st)
 
 template <class T>
 cudaError_t launch_fused(const FusedArgs<T>& a, cudaStream_t st) {
-    if (a.g.A[0][0]) k_fused<T, true><<<a.nitems, NT, fused_smem_bytes_v<T, true>(), st>>>(a);
+    if (a.g.A[0][0] && a.open_ring) k_fused<T, true, true><<<a.nitems, NT, fused_smem_bytes_v<T, true>(), st>>>(a);
+    else if (a.g.A[0][0]) k_fused<T, true><<<a.nitems, NT, fused_smem_bytes_v<T, true>(), st>>>(a);
     else k_fused<T, false><<<a.nitems, NT, fused_smem_bytes_v<T, false>(), st>>>(a);
     return cudaGetLastError();
 }
@@ -1076,7 +1089,9 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
                 const T v = cell_speed(a.P, C.hs, C.ux, C.uy, ax, ay);
                 const bool fin = v <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX);
                 bad = bad || !fin;
-                vmax = (fin && v > vmax) ? v : vmax;
+                // open ring: the edge cells' speeds come from the band pass
+                const bool edge = a.open_ring && (i == 0 || i == a.g.nx - 1 || j == 0 || j == a.g.ny - 1);
+                vmax = (fin && !edge && v > vmax) ? v : vmax;
             }
             if (a.g.A[buf][0]) {
                 a.g.A[buf][0][k] = ax;
@@ -1153,6 +1168,15 @@ __global__ void k_band_acc(const StagedArgs<T> a) {
               ax, ay);
     a.g.A[buf][0][k] = ax;
     a.g.A[buf][1][k] = ay;
+    if (a.open_ring && C.wet) {
+        // the step's signal speed over the state the fill completed: the
+        // edge cells and the ring (along a normal every ring cell repeats
+        // the state and forces of the one at distance 1, so distances up to
+        // HALO cover the whole ring)
+        const T v = cell_speed(a.P, C.hs, C.ux, C.uy, ax, ay);
+        if (!(v <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX))) atomicOr(&a.ctl->err, (unsigned)ERR_NONFINITE);
+        else atomicMax(&a.ctl->smax[buf], (unsigned long long)__double_as_longlong((double)v));
+    }
 }
 
 template <class T>

@@ -100,6 +100,9 @@ struct FusedArgs {
     const double* hydro;  // [nh][4]
     int nh;
     int ntx, seg_h, nitems;
+    // open (zero-gradient) ghost ring: the signal speeds of the outermost
+    // interior rows and columns come from the band pass after each fill
+    int open_ring;
     // learned closure: corrections of the net face-flux sums (3 padded
     // planes F_H, F_Qx, F_Qy), or null
     const T* corr;
@@ -147,6 +150,7 @@ struct StagedArgs {
     int act_nbx;
     unsigned char* hist;  // per-item skip history to clear, or null
     int nhist;
+    int open_ring;  // as in FusedArgs
 };
 
 template <class T>
