@@ -802,13 +802,16 @@ def main():
                            "l2": f"inputs larger than L2 ({8 * cells * (4 if args.precision == 'f32' else 8) / 1e9:.1f} GB read per step)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "final_t_s": info["t"], "wet_cells_end": info["wet_cells"]},
-                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                             "frac": achieved / peak, "peak_source": peak_src,
-                             "nominal_peak": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                "roofline": {"bound": "hbm", "achieved": None if args.skip_dry else achieved, "peak": peak,
+                             "unit": "GB/s", "frac": None if args.skip_dry else achieved / peak,
+                             "peak_source": peak_src, "nominal_peak": NOMINAL_HBM_GBS,
+                             "frac_nominal": None if args.skip_dry else achieved / NOMINAL_HBM_GBS,
+                             "note": ("skip_dry: skipped items move (almost) no state, so the method's 32 B per "
+                                      "counted cell-update does not apply") if args.skip_dry else None,
                              "traffic": None if prof is None else prof["dram"] * cells,
                              "kernel": f"k_fused<{'float' if args.precision == 'f32' else 'double'}>",
                              "algorithmic_bytes_per_cell": bpc},
-                "alu_roofline": alu_roofline(prof, cells, ms_per_step, nsm, clk.summary()),
+                "alu_roofline": None if args.skip_dry else alu_roofline(prof, cells, ms_per_step, nsm, clk.summary()),
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
                         "host_dtype": args.precision, "fp64_host": {"value": e2e64_val, "unit": UNIT,

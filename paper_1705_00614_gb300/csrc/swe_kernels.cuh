@@ -307,21 +307,22 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         const T H = rH(k)[c];
         const bool wet = is_wet(H, rB(k)[c], eps);
         T ux, uy;
-        div2(rQx(k)[c], rQy(k)[c], H, ux, uy);
-        ux = wet ? ux : T(0);
-        uy = wet ? uy : T(0);
+        div2_if(wet, rQx(k)[c], rQy(k)[c], H, ux, uy);
         if (!ACC) {
             const auto U = pU(k);
             U[0][c] = ux;
             U[1][c] = uy;
         }
         if (ACC) {
-            // every lane evaluates (a dry cell's stored accelerations are 0)
-            // and keeps the value where the cell is wet; the friction
-            // coefficient is the cell's own (Eq. 4), from H, U and n
-            const T den = T(1) + th * friction(P, H, rN(k)[c], ux, uy);
-            T usx, usy;
-            div2(ux + th * rA(0, k)[c], uy + th * rA(1, k)[c], den, usx, usy);
+            // FP32: every lane evaluates (a dry cell's stored accelerations
+            // are 0) and keeps the value where the cell is wet; FP64 only
+            // where wet.  The friction coefficient is the cell's own (Eq. 4),
+            // from H, U and n.
+            T usx = T(0), usy = T(0);
+            if (sizeof(T) == 4 || wet) {
+                const T den = T(1) + th * friction(P, H, rN(k)[c], ux, uy);
+                div2(ux + th * rA(0, k)[c], uy + th * rA(1, k)[c], den, usx, usy);
+            }
             const auto A = aU(k);
             A[0][c] = wet ? usx : T(0);
             A[1][c] = wet ? usy : T(0);
@@ -355,17 +356,22 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     auto stage2 = [&](int r) {
         if (!(r >= 2 && r <= nrows - 3 && (cb & 4u))) return;
         const T H = rH(r)[c];
-        // evaluated on every lane, kept where the cell is wet
-        const auto A0 = aU(r);
-        const T u = A0[0][c], uW = A0[0][c - 1], uE = A0[0][c + 1];
-        const T v = A0[1][c], vS = aU(r - 1)[1][c], vN = aU(r + 1)[1][c];
-        const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
-        const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
-        T D;
-        if constexpr (sizeof(T) == 4) D = ((fxp - fxm) + (fyp - fym)) * P.ih;
-        else D = ((fxp - fxm) + (fyp - fym)) / P.h;
-        const T hw = H / tmax(T(0.5), T(1) + th * D);
-        bH(r)[c] = is_wet(H, rB(r)[c], eps) ? hw : H;
+        const bool wet = is_wet(H, rB(r)[c], eps);
+        // FP32: evaluated on every lane, kept where the cell is wet; FP64
+        // only where wet
+        T hw = H;
+        if (sizeof(T) == 4 || wet) {
+            const auto A0 = aU(r);
+            const T u = A0[0][c], uW = A0[0][c - 1], uE = A0[0][c + 1];
+            const T v = A0[1][c], vS = aU(r - 1)[1][c], vN = aU(r + 1)[1][c];
+            const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
+            const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
+            T D;
+            if constexpr (sizeof(T) == 4) D = ((fxp - fxm) + (fyp - fym)) * P.ih;
+            else D = ((fxp - fxm) + (fyp - fym)) / P.h;
+            hw = H / tmax(T(0.5), T(1) + th * D);
+        }
+        bH(r)[c] = wet ? hw : H;
     };
     // S3: forces at t_{n+1/2}, corrector and sources
     auto stage3 = [&](int r) {
@@ -380,9 +386,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         const bool wet = is_wet(H, b, eps);
         T ux, uy;
         if (ACC) {
-            div2(rQx(r)[c], rQy(r)[c], H, ux, uy);
-            ux = wet ? ux : T(0);
-            uy = wet ? uy : T(0);
+            div2_if(wet, rQx(r)[c], rQy(r)[c], H, ux, uy);
         } else {
             ux = pU(r)[0][c];
             uy = pU(r)[1][c];
@@ -420,9 +424,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         C[1][c] = uhx;
         C[2][c] = uhy;
         T upx, upy;
-        div2(qtx, qty, ht, upx, upy);
-        C[3][c] = wt ? upx : T(0);
-        C[4][c] = wt ? upy : T(0);
+        div2_if(wt, qtx, qty, ht, upx, upy);
+        C[3][c] = upx;
+        C[4][c] = upy;
         C[5][c] = qtx;
         C[6][c] = qty;
         C[7][c] = b;
@@ -502,9 +506,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             const T b = C[7][c];
             const bool wetn = is_wet(hn, b, eps);
             T uxn, uyn;
-            div2(qxn, qyn, hn, uxn, uyn);
-            uxn = wetn ? uxn : T(0);
-            uyn = wetn ? uyn : T(0);
+            div2_if(wetn, qxn, qyn, hn, uxn, uyn);
             const auto Nw = nS(r);
             Nw[0][c] = hn;
             Nw[1][c] = uxn;

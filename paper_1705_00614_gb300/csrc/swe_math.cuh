@@ -72,6 +72,22 @@ __device__ __forceinline__ void div2(T a, T b, T d, T& q, T& r) {
     }
 }
 
+// div2 where cond holds, else q = r = 0.  FP32 evaluates on every lane and
+// selects (cheaper than diverging); FP64, whose divisions are long sequences
+// on a slow pipe, divides only where cond holds.  Same values either way.
+template <class T>
+__device__ __forceinline__ void div2_if(bool cond, T a, T b, T d, T& q, T& r) {
+    if constexpr (sizeof(T) == 4) {
+        div2(a, b, d, q, r);
+        q = cond ? q : T(0);
+        r = cond ? r : T(0);
+    } else {
+        q = T(0);
+        r = T(0);
+        if (cond) div2(a, b, d, q, r);
+    }
+}
+
 
 // Multiplications whose products must cancel exactly (h_R^2 - h_L^2 with
 // h_R == h_L at rest) are kept out of FMA contraction.
