@@ -105,8 +105,11 @@ typedef struct {
                               flow and waves leave the grid; ghosts with a bed
                               of 1e29 or more stay walls (set the ring terrain,
                               e.g. edge-extended, with swe_set_terrain_ext).
-                              Contexts with 1 or 2 evaluate the forces of every
-                              step in the kernel instead of storing them. */
+                              With CFL steps the signal speed then covers the
+                              filled ring too (the padded extent stepped as
+                              one grid).  After every fill the stored forces
+                              of the ring band are recomputed.  Not in
+                              batches (swe_batch_create refuses them). */
     /* Distributed sources of Eq. 1 on every non-wall cell, m/s, >= 0: rain
      * adds water at rest; evaporation and infiltration remove water (down
      * to a dry cell) with its velocity.  Nonzero rates switch skip_dry off. */
