@@ -573,7 +573,7 @@ __global__ void k_restrict(const Grid<T> f, const Ctl* __restrict__ fctl, const 
 
 // Training targets: the flux-sum corrections that turn the coarse step
 // into the restricted fine state, standardised; zero correction outside the
-// cells the closure acts on (judged on the state before the step).
+// cells the closure acts on (decided on the state before the step).
 template <class T>
 __global__ void k_targets(const Grid<T> p, const Ctl* __restrict__ pctl, const Grid<T> r, const Ctl* __restrict__ rctl,
                           double h, T eps, const float* __restrict__ nrm, float* __restrict__ t) {
