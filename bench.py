@@ -805,7 +805,8 @@ def main():
                            "wet_fraction": float((prob.H > prob.params.eps).mean()),
                            "skip_dry": args.skip_dry, "seg_h": args.seg_h or "auto",
                            "skipped_items_last_step": info["skipped"],
-                           "l2": f"inputs larger than L2 ({8 * cells * (4 if args.precision == 'f32' else 8) / 1e9:.1f} GB read per step)",
+                           # H, Qx, Qy, b, n and the two stored accelerations
+                           "l2": f"inputs larger than L2 ({7 * cells * (4 if args.precision == 'f32' else 8) / 1e9:.1f} GB read per step)",
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "final_t_s": info["t"], "wet_cells_end": info["wet_cells"]},
                 "roofline": {"bound": "hbm", "achieved": None if args.skip_dry else achieved, "peak": peak,
