@@ -532,7 +532,7 @@ void snapshot_free(Snapshot& sn) {
     }
 }
 
-const int kTileCandidates[] = {16, 32, 64, 128, 256, 512, 1024};
+const int kTileCandidates[] = {16, 32, 64, 128, 192, 256, 384, 512, 768, 1024};
 
 }  // namespace
 
