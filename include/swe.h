@@ -222,6 +222,13 @@ SWE_API int swe_sync(swe_ctx* ctx);
 /* Release every resource of the context (NULL is ignored). */
 SWE_API void swe_destroy(swe_ctx* ctx);
 
+/* Failure-path check (no counterpart in the paper): one device thread
+ * waits, bounded by limit_ms (1..2000), for an mbarrier phase that nothing
+ * completes -- the same bounded wait the step kernels use for their input
+ * rows -- and returns SWE_ERR_DEVICE_TIMEOUT through the same error bit.
+ * The device stays usable.  Any other status is a failure. */
+SWE_API int swe_check_bounded_wait(int32_t limit_ms);
+
 SWE_API const char* swe_status_str(int status);
 SWE_API const char* swe_last_error(void);
 

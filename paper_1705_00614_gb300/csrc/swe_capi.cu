@@ -10,6 +10,7 @@
 
 #include "../../include/swe.h"
 #include "swe_launch.h"
+#include "swe_ptx.cuh"
 
 using namespace swe;
 
@@ -727,6 +728,21 @@ int set_state_with(swe_ctx* c, double t, Up upload, bool speed_checks = false) {
     }
     c->has_state = true;
     return SWE_OK;
+}
+
+// A bounded wait on an mbarrier phase that nothing completes: the wait the
+// step kernels use for their TMA rows, run out on purpose so the error path
+// (error bit, status to the host, usable context) can be checked without a
+// fault or a hang.
+static __global__ void k_wait_probe(unsigned* err, unsigned long long limit_ns) {
+    __shared__ __align__(8) unsigned long long bar;
+    if (threadIdx.x == 0) {
+        swe::mbar_init(&bar, 1);
+        swe::fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !swe::mbar_wait_bounded(&bar, 0u, limit_ns)) atomicOr(err, (unsigned)swe::ERR_TIMEOUT);
+    __syncthreads();
 }
 
 extern "C" {
@@ -1693,6 +1709,23 @@ int swe_nest_step(swe_nest* n, int32_t ncoarse, swe_step_info* info_c, swe_step_
         CK(cudaStreamWaitEvent(f->st, n->ev_c, 0));
     }
     return rc;
+}
+
+int swe_check_bounded_wait(int32_t limit_ms) {
+    if (limit_ms < 1 || limit_ms > 2000) return fail(SWE_ERR_ARG, "limit_ms must be in [1, 2000]");
+    unsigned* d = nullptr;
+    if (cudaMalloc(&d, sizeof(unsigned)) != cudaSuccess) return fail(SWE_ERR_OOM, "probe word");
+    unsigned h = 0;
+    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        k_wait_probe<<<1, 32>>>(d, (unsigned long long)limit_ms * 1000000ull);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) return fail(SWE_ERR_CUDA, cudaGetErrorString(e));
+    if (h & ERR_TIMEOUT) return fail(SWE_ERR_DEVICE_TIMEOUT, "the probe's bounded wait ran out, as it must");
+    return SWE_OK;
 }
 
 }  // extern "C"

@@ -28,7 +28,7 @@ API = ["swe_params_default", "swe_create", "swe_set_terrain", "swe_set_state", "
        "swe_cnn_forward", "swe_cnn_gradients", "swe_cnn_train_step", "swe_cnn_destroy", "swe_restrict_state",
        "swe_closure_features", "swe_closure_targets", "swe_closure_attach", "swe_step_closed",
        "swe_set_terrain_ext", "swe_nest_create", "swe_nest_step", "swe_nest_destroy", "swe_set_state_native",
-       "swe_get_state_native"]
+       "swe_get_state_native", "swe_check_bounded_wait"]
 CNN_CHANNELS = (5, 32, 32, 32, 3)
 SWE_PAD = 10
 NOALLOC_MAX_ITEMS = 7000
@@ -98,6 +98,8 @@ def load(path=None):
     L.swe_set_state_native.argtypes = [ctypes.c_void_p] * 4 + [ctypes.c_double]
     L.swe_get_state_native.restype = ctypes.c_int
     L.swe_get_state_native.argtypes = [ctypes.c_void_p] * 4 + [_dp]
+    L.swe_check_bounded_wait.restype = ctypes.c_int
+    L.swe_check_bounded_wait.argtypes = [ctypes.c_int32]
     L.swe_get_device_ptrs.argtypes = [ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_void_p),
                                       ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
@@ -410,6 +412,13 @@ class Nest:
 
     def __exit__(self, *a):
         self.close()
+
+
+def check_bounded_wait(limit_ms=20):
+    """swe_check_bounded_wait: a device wait on a phase nothing completes,
+    bounded by limit_ms; raises SweError(SWE_ERR_DEVICE_TIMEOUT) as it must."""
+    L = load()
+    _check(L, L.swe_check_bounded_wait(int(limit_ms)))
 
 
 class Batch:

@@ -104,3 +104,8 @@ def test_state_calls_reject_null_arguments_before_touching_the_device(lib):
                                  ctypes.cast(buf, swe._dp), 0.0),
                lib.swe_get_state(None, None, None, None, None)):
         assert rc == -1
+
+
+def test_bounded_wait_check_rejects_bad_limits_before_touching_the_device(lib):
+    for bad in (0, -3, 2001):
+        assert lib.swe_check_bounded_wait(bad) == -1
