@@ -1065,8 +1065,9 @@ __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 
         n.hs = Hs[k];
         n.b = a.g.b[k];
         n.wet = is_wet(n.hs, n.b, eps);
-        n.ux = n.wet ? Qx[k] / n.hs : T(0);
-        n.uy = n.wet ? Qy[k] / n.hs : T(0);
+        // the fused kernel's form of U = Q/H, so a state set from the host
+        // gets the stored forces the kernel would have stored
+        div2_if(n.wet, Qx[k], Qy[k], n.hs, n.ux, n.uy);
         return n;
     };
     if (i < a.g.nx && i < i1) {
@@ -1158,8 +1159,9 @@ __global__ void k_band_acc(const StagedArgs<T> a) {
         n.hs = Hs[k];
         n.b = a.g.b[k];
         n.wet = is_wet(n.hs, n.b, eps);
-        n.ux = n.wet ? Qx[k] / n.hs : T(0);
-        n.uy = n.wet ? Qy[k] / n.hs : T(0);
+        // the fused kernel's form of U = Q/H, so a state set from the host
+        // gets the stored forces the kernel would have stored
+        div2_if(n.wet, Qx[k], Qy[k], n.hs, n.ux, n.uy);
         return n;
     };
     const size_t k = at(i, j);

@@ -138,22 +138,26 @@ def test_lake_at_rest_stays_at_rest(swe, prec):
     assert np.array_equal(H, Hr)
 
 
-def test_determinism_graph_and_resume_f64(swe):
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_determinism_graph_and_resume(swe, prec):
     """Same inputs give bitwise-equal results; one 10-step graph equals ten
     single steps; stopping, copying the state out and resuming in a new
-    context continues bitwise identically."""
+    context continues bitwise identically (the speed pass of the new
+    context stores the forces the kernel would have stored)."""
     p = I.random_wet_dry(140, 100, seed=17)
-    with swe.Solver.from_problem(p, "f64") as a:
+    if prec == "f32":
+        p = p.to_f32_values()
+    with swe.Solver.from_problem(p, prec) as a:
         a.step(10)
         ref = a.get_state()
-    with swe.Solver.from_problem(p, "f64") as b:
+    with swe.Solver.from_problem(p, prec) as b:
         for _ in range(10):
             b.step(1)
         one = b.get_state()
-    with swe.Solver.from_problem(p, "f64") as c:
+    with swe.Solver.from_problem(p, prec) as c:
         c.step(4)
         H, Qx, Qy, t = c.get_state()
-    with swe.Solver.from_problem(p, "f64") as d:
+    with swe.Solver.from_problem(p, prec) as d:
         d.set_state(H, Qx, Qy, t)
         d.step(6)
         res = d.get_state()
