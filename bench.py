@@ -638,6 +638,8 @@ def main():
     ap.add_argument("--skip-dry", action="store_true",
                     help="skip dry work items (the paper's K1 wet-block test); off for the headline")
     ap.add_argument("--seg-h", type=int, default=0, help="output rows per work item (0 = automatic)")
+    ap.add_argument("--mode", default="fused", choices=["fused", "staged"],
+                    help="staged: one kernel per stage (the paper's K2-K8 split), for per-stage time shares")
     ap.add_argument("--closure-train", type=int, default=8, help="closure workload: training seeds")
     ap.add_argument("--closure-test", type=int, default=4, help="closure workload: held-out seeds")
     ap.add_argument("--closure-collect", type=int, default=100, help="closure workload: coarse steps per seed")
@@ -711,8 +713,8 @@ def main():
     # CUDA events below are recorded on it
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    solver = swe.Solver.from_problem(prob, args.precision, stream=stream.cuda_stream, seg_h=args.seg_h,
-                                     skip_dry=args.skip_dry)
+    solver = swe.Solver.from_problem(prob, args.precision, mode=args.mode, stream=stream.cuda_stream,
+                                     seg_h=args.seg_h, skip_dry=args.skip_dry)
 
     # instantiate the CUDA graph of K steps once, restart, then W untimed
     # single-launch warm-up steps (they leave the cached K-step graph alone)
@@ -786,6 +788,7 @@ def main():
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     solver.close()
 
+    no_roof = args.skip_dry or args.mode == "staged"
     if rank == 0:
         cpu = None
         if not args.no_cpu:
@@ -807,24 +810,26 @@ def main():
                            "skipped_items_last_step": info["skipped"],
                            # H, Qx, Qy, b, n and the two stored accelerations
                            "l2": f"inputs larger than L2 ({7 * cells * (4 if args.precision == 'f32' else 8) / 1e9:.1f} GB read per step)",
-                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "parallelism": "replicas" if world > 1 else "single GPU", "mode": args.mode,
                            "final_t_s": info["t"], "wet_cells_end": info["wet_cells"]},
-                "roofline": {"bound": "hbm", "achieved": None if args.skip_dry else achieved, "peak": peak,
-                             "unit": "GB/s", "frac": None if args.skip_dry else achieved / peak,
+                "roofline": {"bound": "hbm", "achieved": None if no_roof else achieved, "peak": peak,
+                             "unit": "GB/s", "frac": None if no_roof else achieved / peak,
                              "peak_source": peak_src, "nominal_peak": NOMINAL_HBM_GBS,
-                             "frac_nominal": None if args.skip_dry else achieved / NOMINAL_HBM_GBS,
+                             "frac_nominal": None if no_roof else achieved / NOMINAL_HBM_GBS,
                              "note": ("skip_dry: skipped items move (almost) no state, so the method's 32 B per "
-                                      "counted cell-update does not apply") if args.skip_dry else None,
+                                      "counted cell-update does not apply") if args.skip_dry else
+                                     ("staged: one kernel per stage, every intermediate in HBM; see the launch "
+                                      "list for per-stage times") if args.mode == "staged" else None,
                              "traffic": None if prof is None else prof["dram"] * cells,
                              "kernel": f"k_fused<{'float' if args.precision == 'f32' else 'double'}>",
                              "algorithmic_bytes_per_cell": bpc},
-                "alu_roofline": None if args.skip_dry else alu_roofline(prof, cells, ms_per_step, nsm, clk.summary()),
+                "alu_roofline": None if no_roof else alu_roofline(prof, cells, ms_per_step, nsm, clk.summary()),
                 "cpu_baseline": cpu,
                 "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
                         "host_dtype": args.precision, "fp64_host": {"value": e2e64_val, "unit": UNIT,
                                                                    "h2d_bytes_per_step": io64_bytes,
                                                                    "d2h_bytes_per_step": io64_bytes}},
-                "gpu_launches": args.steps,
+                "gpu_launches": args.steps * (1 if args.mode == "fused" else 12 + (1 if len(prob.sources) else 0)),
                 "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if dist is not None:

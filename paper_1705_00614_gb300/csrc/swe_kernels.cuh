@@ -812,6 +812,18 @@ __device__ __forceinline__ int ctl_buf(const Ctl* ctl) {
     return (int)(*(volatile const long long*)&ctl->step & 1);
 }
 
+// tau_n for a staged kernel, evaluated once per block: it is an FP64
+// division, and a warp-wide FP64 instruction holds this part's FP64 pipe for
+// 16 cycles, so evaluating it per cell cost each stage ~0.4 ms per 4096^2
+// launch.  Every thread of the block must call it (it synchronises).
+template <class T>
+__device__ __forceinline__ T block_tau(const StagedArgs<T>& a) {
+    __shared__ double st;
+    if (threadIdx.x == 0 && threadIdx.y == 0) st = step_tau(a.ctl, a.sp, ctl_buf(a.ctl));
+    __syncthreads();
+    return (T)st;
+}
+
 template <class T>
 __device__ __forceinline__ Nb<T> nb_at(const StagedArgs<T>& a, const T* Hwet, const T* hs, const T* ux,
                                        const T* uy, size_t k) {
@@ -865,9 +877,9 @@ __global__ void ks_forces(const StagedArgs<T> a, int second) {
 template <class T>
 __global__ void ks_predict(const StagedArgs<T> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const T tauT = block_tau(a);
     if (i >= a.g.nx || j >= a.g.ny) return;
     const int buf = ctl_buf(a.ctl);
-    const T tauT = (T)step_tau(a.ctl, a.sp, buf);
     const T th = T(0.5) * tauT;
     const size_t k = PAcc<T>{a.g.pitch}(i, j);
     T usx = T(0), usy = T(0);
@@ -883,9 +895,9 @@ __global__ void ks_predict(const StagedArgs<T> a) {
 template <class T>
 __global__ void ks_hstar(const StagedArgs<T> a) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const T tauT = block_tau(a);
     if (i >= a.g.nx || j >= a.g.ny) return;
     const int buf = ctl_buf(a.ctl);
-    const T tauT = (T)step_tau(a.ctl, a.sp, buf);
     const T th = T(0.5) * tauT;
     const PAcc<T> at{a.g.pitch};
     const size_t k = at(i, j);
@@ -920,9 +932,9 @@ __global__ void ks_correct(const StagedArgs<T> a) {
     __shared__ double red[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     double src = 0.0;
+    const T tauT = block_tau(a);
     if (i < a.g.nx && j < a.g.ny) {
         const int buf = ctl_buf(a.ctl);
-        const T tauT = (T)step_tau(a.ctl, a.sp, buf);
         const size_t k = PAcc<T>{a.g.pitch}(i, j);
         const T H = a.g.H[buf][k], b = a.g.b[k];
         T utx = T(0), uty = T(0);
@@ -994,9 +1006,9 @@ __global__ void ks_final(const StagedArgs<T> a) {
     __shared__ double red[8];
     const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
     double mass = 0.0, clip = 0.0, wet = 0.0;
+    const T tauT = block_tau(a);
     if (i < a.g.nx && j < a.g.ny) {
         const int buf = ctl_buf(a.ctl);
-        const T tauT = (T)step_tau(a.ctl, a.sp, buf);
         const T dth = tauT / a.P.h;
         const PAcc<T> at{a.g.pitch};
         const size_t k = at(i, j), kw = at(i - 1, j), ks = at(i, j - 1);
