@@ -138,3 +138,27 @@ def test_batch_autotune_keeps_results(swe):
             ref = one.get_state()
         for x, y in zip(ref, got[k]):
             assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def test_full_size_ensemble_scenarios_batched_equal_alone(swe):
+    """The benchmark's own scenarios (bench.flooded_ensemble: N between 512
+    and 2048, own terrain and hydrograph, gates closed as generated, flooded
+    to the median bed), batched, equal each scenario run alone bitwise."""
+    import bench
+    probs, _ = bench.flooded_ensemble(4)
+    assert max(p.params.nx for p in probs) > 1024
+    sols = [swe.Solver.from_problem(p, "f32", seg_h=256) for p in probs]
+    try:
+        b = swe.Batch(sols)
+        b.step(12)
+        batched = [s.get_state() for s in sols]
+        b.close()
+    finally:
+        for s in sols:
+            s.close()
+    for p, g in zip(probs, batched):
+        with swe.Solver.from_problem(p, "f32", seg_h=256) as s:
+            s.step(12)
+            a = s.get_state()
+        for x, y in zip(a, g):
+            assert np.array_equal(np.asarray(x), np.asarray(y))
