@@ -812,6 +812,10 @@ __device__ __forceinline__ int ctl_buf(const Ctl* ctl) {
     return (int)(*(volatile const long long*)&ctl->step & 1);
 }
 
+// Rows per block of the kernels that reduce FP64 budgets (speed pass,
+// corrector, final update): 32 columns x SPEED_ROWS rows, 8 rows per thread.
+constexpr int SPEED_ROWS = 64;
+
 // tau_n for a staged kernel, evaluated once per block: it is an FP64
 // division, and a warp-wide FP64 instruction holds this part's FP64 pipe for
 // 16 cycles, so evaluating it per cell cost each stage ~0.4 ms per 4096^2
@@ -929,11 +933,15 @@ __global__ void ks_sources(const StagedArgs<T> a) {
 
 template <class T>
 __global__ void ks_correct(const StagedArgs<T> a) {
+    // a block covers 32 columns x SPEED_ROWS rows (each thread SPEED_ROWS / 8
+    // rows), so the FP64 source budget is reduced once per 2048 cells
     __shared__ double red[8];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jend = min(a.g.ny, (int)(blockIdx.y + 1) * SPEED_ROWS);
     double src = 0.0;
     const T tauT = block_tau(a);
-    if (i < a.g.nx && j < a.g.ny) {
+    if (i < a.g.nx)
+    for (int j = blockIdx.y * SPEED_ROWS + threadIdx.y; j < jend; j += 8) {
         const int buf = ctl_buf(a.ctl);
         const size_t k = PAcc<T>{a.g.pitch}(i, j);
         const T H = a.g.H[buf][k], b = a.g.b[k];
@@ -959,7 +967,7 @@ __global__ void ks_correct(const StagedArgs<T> a) {
         a.qty[k] = qty;
         a.upx[k] = wt ? qtx / ht : T(0);
         a.upy[k] = wt ? qty / ht : T(0);
-        src = (double)ht - (double)H;
+        src += (double)ht - (double)H;
     }
     const double s = block_sum<256>(src, red);
     if (threadIdx.x == 0 && threadIdx.y == 0) a.parts2[blockIdx.y * gridDim.x + blockIdx.x].src = s;
@@ -1003,11 +1011,15 @@ __global__ void ks_flux(const StagedArgs<T> a, int dir) {
 
 template <class T>
 __global__ void ks_final(const StagedArgs<T> a) {
+    // 32 columns x SPEED_ROWS rows per block, as ks_correct
     __shared__ double red[8];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    double mass = 0.0, clip = 0.0, wet = 0.0;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jend = min(a.g.ny, (int)(blockIdx.y + 1) * SPEED_ROWS);
+    double mass = 0.0, clip = 0.0;
+    int wet = 0;
     const T tauT = block_tau(a);
-    if (i < a.g.nx && j < a.g.ny) {
+    if (i < a.g.nx)
+    for (int j = blockIdx.y * SPEED_ROWS + threadIdx.y; j < jend; j += 8) {
         const int buf = ctl_buf(a.ctl);
         const T dth = tauT / a.P.h;
         const PAcc<T> at{a.g.pitch};
@@ -1017,7 +1029,7 @@ __global__ void ks_final(const StagedArgs<T> a) {
         const T fqy = (a.fx[2][kw] - a.fx[2][k]) + (a.fy[2][ks] - a.fy[2][k]);
         T hn = a.ht[k] + dth * fh;
         if (hn < T(0)) {
-            clip = -(double)hn;
+            clip += -(double)hn;
             hn = T(0);
         }
         T qxn = T(0), qyn = T(0);
@@ -1028,13 +1040,13 @@ __global__ void ks_final(const StagedArgs<T> a) {
         a.g.H[buf ^ 1][k] = hn;
         a.g.Qx[buf ^ 1][k] = qxn;
         a.g.Qy[buf ^ 1][k] = qyn;
-        mass = (double)hn;
-        wet = is_wet(hn, a.g.b[k], a.P.eps) ? 1.0 : 0.0;
+        mass += (double)hn;
+        wet += is_wet(hn, a.g.b[k], a.P.eps) ? 1 : 0;
     }
     const int bl = blockIdx.y * gridDim.x + blockIdx.x;
     const double m = block_sum<256>(mass, red);
     const double c = block_sum<256>(clip, red);
-    const double w = block_sum<256>(wet, red);
+    const double w = block_sum<256>((double)wet, red);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         a.parts[bl].mass = m;
         a.parts[bl].clip = c;
@@ -1052,7 +1064,6 @@ __global__ void ks_final(const StagedArgs<T> a) {
 // in any precision) and the wet count as an integer, so FP64 work (slow on
 // this part) is one conversion and one add per cell for the mass plus one
 // set of block reductions per SPEED_ROWS * 32 cells.
-constexpr int SPEED_ROWS = 64;
 
 template <class T>
 __global__ void ks_speed(const StagedArgs<T> a, int which, int i0 = 0, int j0 = 0, int parts = 1,
@@ -1256,7 +1267,9 @@ cudaError_t launch_staged(const StagedArgs<T>& a, cudaStream_t st) {
     const dim3 grd((a.g.nx + 31) / 32, (a.g.ny + 7) / 8);
     const dim3 grdx((a.g.nx + 1 + 31) / 32, (a.g.ny + 7) / 8);
     const dim3 grdy((a.g.nx + 31) / 32, (a.g.ny + 1 + 7) / 8);
-    const int nblocks = (int)(grd.x * grd.y);
+    // the budget kernels (corrector, final update) run 32 x SPEED_ROWS blocks
+    const dim3 grdb = speed_grid<T>(a.g.nx, a.g.ny);
+    const int nblocks = (int)(grdb.x * grdb.y);
     const size_t plane = (size_t)a.g.pitch * (size_t)(a.g.ny + 2 * PAD) * sizeof(T);
     ks_prim<T><<<grd, blk, 0, st>>>(a);
     ks_forces<T><<<grd, blk, 0, st>>>(a, 0);
@@ -1267,10 +1280,10 @@ cudaError_t launch_staged(const StagedArgs<T>& a, cudaStream_t st) {
     cudaMemsetAsync(a.svx, 0, plane, st);
     cudaMemsetAsync(a.svy, 0, plane, st);
     if (a.nsrc > 0) ks_sources<T><<<(a.nsrc + 127) / 128, 128, 0, st>>>(a);
-    ks_correct<T><<<grd, blk, 0, st>>>(a);
+    ks_correct<T><<<grdb, blk, 0, st>>>(a);
     ks_flux<T><<<grdx, blk, 0, st>>>(a, 0);
     ks_flux<T><<<grdy, blk, 0, st>>>(a, 1);
-    ks_final<T><<<grd, blk, 0, st>>>(a);
+    ks_final<T><<<grdb, blk, 0, st>>>(a);
     ks_speed<T><<<speed_grid<T>(a.g.nx, a.g.ny), blk, 0, st>>>(a, 1);
     ks_finish<T><<<1, 256, 0, st>>>(a, nblocks, 0);
     return cudaGetLastError();
