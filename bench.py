@@ -276,11 +276,11 @@ def run_closure(args, torch, swe, stream, rank, world):
 
     rng = np.random.default_rng(0)
     t0 = time.perf_counter()
-    norm = CL.estimate_norm(torch, [scenario(train_seeds[0])], 10, tau_c, rng, 128)
+    norm = CL.estimate_norm(torch, [scenario(train_seeds[0])], 10, tau_c, rng, 128, bed=args.closure_bed)
     X, T = [], []
     for sd in train_seeds:
         x, t = CL.collect(torch, scenario(sd), args.closure_collect, tau_c, norm.inp(), norm.out(), 8, 128, rng,
-                          stream=stream.cuda_stream, noise=args.closure_noise)
+                          stream=stream.cuda_stream, noise=args.closure_noise, bed=args.closure_bed)
         X.append(x)
         T.append(t)
     X = torch.cat(X)
@@ -290,7 +290,7 @@ def run_closure(args, torch, swe, stream, rank, world):
     for r in range(args.closure_dagger):
         for sd in train_seeds:
             x, t = CL.collect_closed(torch, scenario(sd), args.closure_collect, tau_c, params, norm, 8, 128, rng,
-                                     stream=stream.cuda_stream)
+                                     stream=stream.cuda_stream, bed=args.closure_bed)
             if x is not None:
                 X = torch.cat([X, x])
                 T = torch.cat([T, t])
@@ -306,7 +306,7 @@ def run_closure(args, torch, swe, stream, rank, world):
     ms_fine, ms_closed = [], []
     for sd in test_seeds:
         fp = scenario(sd)
-        cp = CL.coarse_problem(fp)
+        cp = CL.coarse_problem(fp, args.closure_bed)
         fine = swe.Solver.from_problem(CL.with_dt(fp, tau_c / 4.0), "f32", stream=stream.cuda_stream)
         plain = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
         closed = [swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream) for _ in alphas]
@@ -368,6 +368,7 @@ def run_closure(args, torch, swe, stream, rank, world):
                            "tau_coarse_s": tau_c, "train_seeds": len(train_seeds), "test_seeds": len(test_seeds),
                            "collect_steps_per_seed": args.closure_collect, "train_iters": args.closure_iters,
                            "dagger_rounds": args.closure_dagger, "input_noise": args.closure_noise,
+                           "coarse_bed": args.closure_bed,
                            "final_train_loss": hist[-1][1], "train_wall_s": t_train,
                            "rel_l2": mean, "reported": best,
                            "target": 0.01, "speedup_closed_coarse_vs_fine": speedup,
@@ -647,6 +648,8 @@ def main():
     ap.add_argument("--closure-steps", type=int, default=5000, help="closure workload: longest horizon")
     ap.add_argument("--closure-alpha", default="1",
                     help="closure workload: comma-separated correction scales to evaluate side by side")
+    ap.add_argument("--closure-bed", default="volume", choices=["mean", "volume"],
+                    help="closure workload: coarse bed from 4x4 means, or volume-matched in partly wet cells")
     ap.add_argument("--closure-noise", type=float, default=0.0,
                     help="closure workload: relative input noise on the coarse states the training pairs start from")
     ap.add_argument("--closure-dagger", type=int, default=0,

@@ -27,15 +27,34 @@ NORM_ID_IN = np.array([0, 0, 0, 0, 0, 1, 1, 1, 1, 1], dtype=np.float32)
 NORM_ID_OUT = np.array([0, 0, 0, 1, 1, 1], dtype=np.float32)
 
 
-def coarse_problem(fine: I.Problem) -> I.Problem:
+def coarse_problem(fine: I.Problem, bed: str = "mean") -> I.Problem:
     """The 4x coarser grid over the same domain: statics are the 4x4 block
     means of the fine ones, each fine source cell feeds its coarse cell with
-    1/16 of its weight, same physics.  (Input preparation only.)"""
+    1/16 of its weight, same physics.  (Input preparation only.)
+
+    bed = "volume": a coarse cell that is partly wet in the fine state takes
+    the bed that makes its depth at the block's fine water level equal to
+    the mean depth of its fine cells (sub-grid storage: with the mean bed a
+    partly wet cell holds a different volume at a given level than its fine
+    cells, and the coarse grid settles to a different shoreline)."""
     p = fine.params
     nx, ny = p.nx // 4, p.ny // 4
 
     def r(a):
         return np.asarray(a, dtype=np.float64).reshape(ny, 4, nx, 4).mean(axis=(1, 3))
+
+    def blocks(a):
+        return np.asarray(a, dtype=np.float64).reshape(ny, 4, nx, 4)
+
+    if bed not in ("mean", "volume"):
+        raise ValueError(f"bed must be 'mean' or 'volume', not {bed!r}")
+    b_c = r(fine.b)
+    if bed == "volume":
+        wet = blocks(fine.H) > 0.0
+        eta = blocks(np.asarray(fine.H) + np.asarray(fine.b))
+        part = wet.any(axis=(1, 3)) & ~wet.all(axis=(1, 3))
+        level = np.max(np.where(wet, eta, -np.inf), axis=(1, 3))
+        b_c = np.where(part, level - r(fine.H), b_c)
 
     s = fine.sources
     cells = {}
@@ -54,8 +73,7 @@ def coarse_problem(fine: I.Problem) -> I.Problem:
                     np.array([cells[k][2] for k in keys]) / np.where(ws > 0, ws, 1),
                     np.array([k[2] for k in keys], np.int32), s.hydrographs)
     par = I.Params(**{**p.__dict__, "nx": nx, "ny": ny, "dx": 4 * p.dx})
-    return I.Problem(fine.name + "-coarse", par, r(fine.b), r(fine.n_manning), r(fine.H), r(fine.Qx), r(fine.Qy),
-                     src)
+    return I.Problem(fine.name + "-coarse", par, b_c, r(fine.n_manning), r(fine.H), r(fine.Qx), r(fine.Qy), src)
 
 
 def flooded(prob: I.Problem, quantile: float = 0.5) -> I.Problem:
@@ -108,7 +126,8 @@ def perturb(H, Qx, Qy, rel, rng):
     return H2, Qx2, Qy2
 
 
-def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, crop, rng, stream=None, noise=0.0):
+def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, crop, rng, stream=None, noise=0.0,
+            bed="mean"):
     """Run the fine grid and, for every coarse step, the coarse step taken
     from the restricted fine state; return standardised (inputs, targets)
     crops as device tensors [S, crop, crop, 16] BF16 and [S, crop, crop, 3]
@@ -117,7 +136,7 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
     the restricted fine state one step later, so the network also learns to
     pull a state that has drifted back (input noise against the distribution
     shift of closed runs)."""
-    cp = coarse_problem(fine_prob)
+    cp = coarse_problem(fine_prob, bed)
     nyc, nxc = cp.params.ny, cp.params.nx
     fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
     A = S.Solver.from_problem(with_dt(cp, tau_c), "f32", stream=stream)
@@ -149,14 +168,14 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
     return torch.stack(xs), torch.stack(ts)
 
 
-def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step, crop, rng, stream=None):
+def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step, crop, rng, stream=None, bed="mean"):
     """Training pairs along the closed model's own coarse trajectory: the
     closed grid runs beside the fine grid; at every coarse step the plain
     coarse step is taken from the closed grid's state and the target is the
     correction that would have put it on the restricted fine state.  A
     network trained on them also learns to undo its own drift (pairs from
     the states it visits, not only from restricted fine states)."""
-    cp = coarse_problem(fine_prob)
+    cp = coarse_problem(fine_prob, bed)
     nyc, nxc = cp.params.ny, cp.params.nx
     fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
     C = S.Solver.from_problem(with_dt(cp, tau_c), "f32", stream=stream)
@@ -200,12 +219,12 @@ def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step,
     return torch.stack(xs), torch.stack(ts).clamp_(-10.0, 10.0)
 
 
-def estimate_norm(torch, probs, steps, tau_c, rng, crop):
+def estimate_norm(torch, probs, steps, tau_c, rng, crop, bed="mean"):
     """Per-channel mean and standard deviation of inputs and targets from a
     short pilot collection with identity normalisation."""
     X, T = [], []
     for p in probs:
-        x, t = collect(torch, p, steps, tau_c, NORM_ID_IN, NORM_ID_OUT, 4, crop, rng)
+        x, t = collect(torch, p, steps, tau_c, NORM_ID_IN, NORM_ID_OUT, 4, crop, rng, bed=bed)
         X.append(x.float().cpu().numpy().reshape(-1, 16)[:, :5])
         T.append(t.cpu().numpy().reshape(-1, 3))
     X = np.concatenate(X).astype(np.float64)
@@ -255,10 +274,10 @@ def shrink(norm: Norm, alpha: float) -> Norm:
     return Norm(norm.mu_in, norm.sd_in, norm.mu_out * alpha, norm.sd_out * alpha)
 
 
-def evaluate(torch, fine_prob, params, norm, nsteps, tau_c, stream=None):
+def evaluate(torch, fine_prob, params, norm, nsteps, tau_c, stream=None, bed="mean"):
     """Relative L2 error in H after nsteps coarse steps against the
     restricted fine solution, with and without the closure."""
-    cp = coarse_problem(fine_prob)
+    cp = coarse_problem(fine_prob, bed)
     fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
     plain = S.Solver.from_problem(with_dt(cp, tau_c), "f32", stream=stream)
     closed = S.Solver.from_problem(with_dt(cp, tau_c), "f32", stream=stream)
