@@ -411,18 +411,20 @@ __global__ void k_pack_w(const float* __restrict__ wm, __nv_bfloat16* __restrict
 
 // Mean-squared error over the real output channels and its gradient, as
 // BF16 [N][H][W][16] (channels 3.. zero) for the last layer's backward pass.
+// A warp's 32 pixels are summed in FP32 (fixed shuffle tree) and the block's
+// warps in FP64: one FP64 operation per warp rather than several per pixel.
 __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, __nv_bfloat16* __restrict__ gy,
                       double* __restrict__ part, long long npix, int co, float scale) {
     __shared__ double red[8];
     const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    double l = 0.0;
+    float l = 0.f;
     if (p < npix) {
         __nv_bfloat16 gv[16];
         for (int o = 0; o < 16; ++o) {
             float g = 0.f;
             if (o < co) {
                 const float d = y[p * co + o] - t[p * co + o];
-                l += (double)d * d;
+                l = fmaf(d, d, l);
                 g = 2.f * d * scale;
             }
             gv[o] = __float2bfloat16(g);
@@ -432,7 +434,7 @@ __global__ void k_mse(const float* __restrict__ y, const float* __restrict__ t, 
         dst[1] = *reinterpret_cast<const uint4*>(&gv[8]);
     }
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = l;
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = (double)l;
     __syncthreads();
     if (threadIdx.x == 0) {
         double s = 0.0;
@@ -722,6 +724,9 @@ ConvPlan conv_plan(const swe_cnn* c) {
     const long long tiles = (long long)c->n * c->h * tpr;
     int rc = (int)std::max<long long>(4, (tiles + c->ntc - 1) / c->ntc);
     rc = std::min(rc, c->h);
+    // taller items until they fit one pass of the CTAs: a few items left
+    // over for a second pass would double the makespan
+    while (rc < c->h && (long long)c->n * tpr * ((c->h + rc - 1) / rc) > c->ntc) ++rc;
     ConvPlan p;
     p.rc = rc;
     p.nitems = c->n * tpr * ((c->h + rc - 1) / rc);

@@ -124,3 +124,32 @@ def test_trained_closure_beats_plain_coarse_grid(env):
     print("closure evaluation", res, "loss", hist)
     assert math.isfinite(res["rel_l2_closed"])
     assert res["rel_l2_closed"] < res["rel_l2_plain"], res
+
+
+@pytest.mark.parametrize("bed", ["volume", "mean"])
+def test_coarse_lake_on_gpu_matches_oracle(env, bed):
+    """A still lake over fractal terrain, restricted to the 4x coarser grid
+    (160^2, two column tiles with a ragged tail): 20 fixed coarse steps of
+    the FP64 GPU path equal the FP64 oracle to 1e-12.  With the
+    volume-matched bed the coarse lake stays at rest, as the fine one does
+    (the hydrostatic balance of Sec. 2.3's pressure term on a flat surface);
+    with the 4 x 4 mean bed the partly wet cells stand above the lake and
+    the water moves."""
+    import dataclasses
+
+    import oracle
+    torch, swe, closure = env
+    fine = I.lake_at_rest(640, 5.0, 3, eta0=12.0, nu=0.0, coriolis_f=0.0)
+    fine = dataclasses.replace(fine, params=dataclasses.replace(fine.params, wind_x=0.0, wind_y=0.0))
+    c = closure.with_dt(closure.coarse_problem(fine, bed), 0.5)
+    H, Qx, Qy, t, _ = oracle.run(c, 20)
+    with swe.Solver.from_problem(c, "f64") as s:
+        s.step(20)
+        g = s.get_state()
+    assert abs(g[3] - t) <= 1e-12 * t
+    scale = max(np.abs(H).max(), 1e-3)
+    for name, a, b in zip(("H", "Qx", "Qy"), g[:3], (H, Qx, Qy)):
+        err = np.abs(np.asarray(a) - b).max()
+        assert err <= 1e-12 * scale, (bed, name, err)
+    moved = max(np.abs(np.asarray(g[1])).max(), np.abs(np.asarray(g[2])).max())
+    assert (moved <= 1e-12) == (bed == "volume"), (bed, moved)
