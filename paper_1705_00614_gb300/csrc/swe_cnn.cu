@@ -279,10 +279,19 @@ __global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restri
     constexpr int PS = CI + 8, GS = CO + 8;
     constexpr int UNITS = 9 * (CI / 16);
     constexpr int UPW = (UNITS + TY - 1) / TY;
+    constexpr int NT = 32 * TY;
+    // 16-byte elements of a tile's inputs (with halo) and output gradients,
+    // and how many of each one thread moves
+    constexpr int NXE = (TY + 2) * (TX + 2) * (CI / 8), NGE = TY * TX * (CO / 8);
+    constexpr int XPT = (NXE + NT - 1) / NT, GPT = (NGE + NT - 1) / NT;
+    constexpr int BG = NT / CO;  // threads summing one output's bias gradient
     __shared__ __align__(16) __nv_bfloat16 sx[(TY + 2) * (TX + 2) * PS];
     __shared__ __align__(16) __nv_bfloat16 sg[TY * TX * GS];
+    __shared__ float sb[NT];
     static_assert(CO % 16 == 0, "B fragments are loaded in pairs");
+    static_assert(NT % CO == 0, "bias groups");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bo = tid % CO, bg = tid / CO;
     const int gx = W / TX, gy = H / TY;
     const int r0 = lane >> 2, kc = (lane & 3) * 2;
     const int lq = lane >> 3, lr = lane & 7;  // ldmatrix: matrix and row this lane addresses
@@ -294,21 +303,39 @@ __global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restri
     float bsum = 0.f;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const int n = t / (gx * gy), i0 = ((t / gx) % gy) * TY, j0 = (t % gx) * TX;
-        __syncthreads();  // the previous tile's shared data is no longer read
-        for (int e = tid; e < (TY + 2) * (TX + 2) * (CI / 8); e += blockDim.x) {
-            const int p = e / (CI / 8), c8 = e % (CI / 8);
-            const int ti = p / (TX + 2), tj = p % (TX + 2);
-            const int gi = i0 + ti - 1, gj = j0 + tj - 1;
-            uint4 v = make_uint4(0, 0, 0, 0);
-            if (gi >= 0 && gi < H && gj >= 0 && gj < W)
-                v = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * c8]);
-            *reinterpret_cast<uint4*>(&sx[p * PS + 8 * c8]) = v;
+        // all of this thread's loads are issued before the barrier that
+        // retires the previous tile, so their latencies overlap
+        uint4 vx[XPT], vg[GPT];
+#pragma unroll
+        for (int k = 0; k < XPT; ++k) {
+            const int e = tid + k * NT;
+            vx[k] = make_uint4(0, 0, 0, 0);
+            if (e < NXE) {
+                const int p = e / (CI / 8), c8 = e % (CI / 8);
+                const int gi = i0 + p / (TX + 2) - 1, gj = j0 + p % (TX + 2) - 1;
+                if (gi >= 0 && gi < H && gj >= 0 && gj < W)
+                    vx[k] = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * c8]);
+            }
         }
-        for (int e = tid; e < TY * TX * (CO / 8); e += blockDim.x) {
-            const int p = e / (CO / 8), c8 = e % (CO / 8);
-            const int ti = p / TX, tj = p % TX;
-            const uint4 v = *reinterpret_cast<const uint4*>(&g[(((size_t)n * H + i0 + ti) * W + j0 + tj) * CO + 8 * c8]);
-            *reinterpret_cast<uint4*>(&sg[p * GS + 8 * c8]) = v;
+#pragma unroll
+        for (int k = 0; k < GPT; ++k) {
+            const int e = tid + k * NT;
+            if (e < NGE) {
+                const int p = e / (CO / 8), c8 = e % (CO / 8);
+                vg[k] = *reinterpret_cast<const uint4*>(
+                    &g[(((size_t)n * H + i0 + p / TX) * W + j0 + p % TX) * CO + 8 * c8]);
+            }
+        }
+        __syncthreads();  // the previous tile's shared data is no longer read
+#pragma unroll
+        for (int k = 0; k < XPT; ++k) {
+            const int e = tid + k * NT;
+            if (e < NXE) *reinterpret_cast<uint4*>(&sx[(e / (CI / 8)) * PS + 8 * (e % (CI / 8))]) = vx[k];
+        }
+#pragma unroll
+        for (int k = 0; k < GPT; ++k) {
+            const int e = tid + k * NT;
+            if (e < NGE) *reinterpret_cast<uint4*>(&sg[(e / (CO / 8)) * GS + 8 * (e % (CO / 8))]) = vg[k];
         }
         __syncthreads();
 #pragma unroll
@@ -336,9 +363,9 @@ __global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restri
                 }
             }
         }
-        // bias gradient: sum of g over the tile, pixels in order
-        if (tid < CO)
-            for (int p = 0; p < TY * TX; ++p) bsum += __bfloat162float(sg[p * GS + tid]);
+        // bias gradient: thread (bg, bo) sums output bo over the pixels
+        // bg, bg + BG, ... of each of its tiles, in order
+        for (int p = bg; p < TY * TX; p += BG) bsum += __bfloat162float(sg[p * GS + bo]);
     }
 #pragma unroll
     for (int q = 0; q < UPW; ++q) {
@@ -355,7 +382,13 @@ __global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restri
             P[(cb + r0 + 8) * CO + o + 1] = acc[q][f][3];
         }
     }
-    if (tid < CO) bpart[(size_t)blockIdx.x * CO + tid] = bsum;
+    sb[tid] = bsum;
+    __syncthreads();
+    if (tid < CO) {
+        float b = 0.f;
+        for (int k = 0; k < BG; ++k) b += sb[k * CO + tid];
+        bpart[(size_t)blockIdx.x * CO + tid] = b;
+    }
 }
 
 // Fixed-order sum of the per-CTA partials -> FP32 gradients in the master
@@ -655,7 +688,8 @@ struct swe_cnn {
     __nv_bfloat16* act[NLAYER] = {};  // act[0] unused (input given); act[l] = output of layer l-1 (BF16)
     float* yout = nullptr;            // last layer output FP32 [n][h][w][3]
     __nv_bfloat16* gbuf[2] = {};      // gradient ping-pong, BF16 [n][h][w][32]
-    int nwg = 0;                      // persistent weight-gradient CTAs
+    int nwg = 0;                      // weight-gradient CTAs the partial buffers hold
+    int nwgv[3] = {0, 0, 0};          // persistent CTAs of k_wgrad<16,32>, <32,32>, <32,16>: one wave
     int ntc = 0;                      // persistent convolution CTAs
     float* part = nullptr;            // weight-gradient partials, one set per such CTA
     float* bpart = nullptr;
@@ -795,12 +829,12 @@ int backward_all(swe_cnn* c, const __nv_bfloat16* x, const float* target) {
     k_sum<<<1, 256, 0, c->st>>>(c->lpart, nb, c->dloss);
     const dim3 grid(c->w / TX, c->h / TY, c->n), blk(32 * TY);
     const int ntiles = (int)(grid.x * grid.y * grid.z);
-    const int nblk = c->nwg;
     const __nv_bfloat16* ins[NLAYER] = {x, c->act[1], c->act[2], c->act[3]};
     int cur = 0;
     for (int l = NLAYER - 1; l >= 0; --l) {
         const __nv_bfloat16* gl = c->gbuf[cur];
         // weight gradient of layer l: inputs ins[l] (CIP), output gradient gl
+        const int nblk = c->nwgv[l == 0 ? 0 : l == 3 ? 2 : 1];
         switch (l) {
             case 0: k_wgrad<16, 32><<<nblk, blk, 0, c->st>>>(ins[0], gl, c->part, c->bpart, c->h, c->w, ntiles); break;
             case 3: k_wgrad<32, 16><<<nblk, blk, 0, c->st>>>(ins[3], gl, c->part, c->bpart, c->h, c->w, ntiles); break;
@@ -877,6 +911,17 @@ SWE_API int swe_cnn_create(int32_t n, int32_t h, int32_t w, void* stream, swe_cn
         return cfail(SWE_ERR_CUDA, "device attributes");
     }
     c->nwg = (int)std::min<size_t>((size_t)grid.x * grid.y * grid.z, (size_t)4 * nsm);
+    {
+        int occ[3] = {0, 0, 0};
+        const int nt = 32 * TY;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_wgrad<16, 32>, nt, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_wgrad<32, 32>, nt, 0) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_wgrad<32, 16>, nt, 0) != cudaSuccess) {
+            swe_cnn_destroy(c);
+            return cfail(SWE_ERR_CUDA, "weight-gradient occupancy");
+        }
+        for (int v = 0; v < 3; ++v) c->nwgv[v] = std::max(1, std::min(c->nwg, std::max(1, occ[v]) * nsm));
+    }
     c->ntc = 3 * nsm;  // three 71 KB CTAs fit an SM
     if (conv_attr<16, 32, MODE_RELU_BF16>() != cudaSuccess || conv_attr<32, 32, MODE_RELU_BF16>() != cudaSuccess ||
         conv_attr<32, 16, MODE_LINEAR_F32>() != cudaSuccess || conv_attr<16, 32, MODE_MASK_BF16>() != cudaSuccess ||
