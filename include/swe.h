@@ -387,7 +387,13 @@ SWE_API int swe_step_closed(swe_ctx* ctx, int32_t nsteps, swe_step_info* info);
  * i.e. the max_speed reported for it by swe_step or by the previous call of
  * this function (0 for still water); max_speed < 0 without dt_fixed is
  * rejected.  With info != NULL the stream is synchronised and the report
- * (new t, tau, mass, wet cells, max_speed of the output state) filled.
+ * (new t, tau, mass, wet cells, max_speed of the output state) filled, and
+ * device-side failures are returned as error codes.  With info == NULL the
+ * call only enqueues the step and reports nothing: a device error (a
+ * bounded wait that ran out, a non-finite signal speed, a non-positive
+ * step), the new t and the max_speed the next call needs are then lost,
+ * since the next call clears the control block they live in.  So pass info
+ * unless dt_fixed > 0 and the caller checks the output state another way.
  * Runs on p->cuda_stream (NULL: the legacy default stream).
  *
  * Scratch: the kernel's control block, one partial-sum record per CTA and
@@ -401,9 +407,9 @@ SWE_API int swe_step_closed(swe_ctx* ctx, int32_t nsteps, swe_step_info* info);
  * but all calls share the one array: calls whose work can overlap on the
  * GPU (other streams, other host threads) race and corrupt each other's
  * results, so serialise them.
- * Errors: SWE_ERR_ARG (sizes, alignment, layout, parameters; checked before
- * any device work), SWE_ERR_CUDA, SWE_ERR_NONFINITE, SWE_ERR_DT,
- * SWE_ERR_DEVICE_TIMEOUT.
+ * Errors: SWE_ERR_ARG (sizes, alignment, layout, a pitch above INT_MAX,
+ * parameters; checked before any device work), SWE_ERR_CUDA, and, with
+ * info != NULL only, SWE_ERR_NONFINITE, SWE_ERR_DT, SWE_ERR_DEVICE_TIMEOUT.
  * ------------------------------------------------------------------------ */
 #define SWE_PAD 10
 #define SWE_NOALLOC_MAX_ITEMS 7000

@@ -79,6 +79,8 @@ def _load(path):
     L.orc_step.argtypes = [ctypes.POINTER(_Params), _dp, _dp, ctypes.c_void_p,
                            ctypes.POINTER(_Sources), ctypes.c_double, _dp, _dp, _dp,
                            _dp, _dp, _dp, ctypes.POINTER(_Info), ctypes.POINTER(_Stages)]
+    L.orc_step_corr.restype = ctypes.c_int
+    L.orc_step_corr.argtypes = L.orc_step.argtypes + [_dp]
     L.orc_riemann.restype = None
     L.orc_riemann.argtypes = [ctypes.c_double] * 6 + [_dp]
     L.orc_state_speed.restype = ctypes.c_double
@@ -146,9 +148,11 @@ class _Bound:
         return None if self.solid is None else self.solid.ctypes.data
 
 
-def step(prob, H, Qx, Qy, t=0.0, t_end=0.0, stages=False, bound=None, L=None):
+def step(prob, H, Qx, Qy, t=0.0, t_end=0.0, stages=False, bound=None, L=None, corr=None):
     """One oracle time step.  Returns (H, Qx, Qy, info, stages-or-None).
-    ``L`` selects another loaded build (see ``lib(path)``)."""
+    ``L`` selects another loaded build (see ``lib(path)``).  ``corr``
+    ([3, ny, nx] or None): additive corrections of each cell's net face-flux
+    sums (Fh, Fv_x, Fv_y), applied in the final update (a learned closure)."""
     bd = bound or _Bound(prob)
     p = bd.params
     nx, ny = p.nx, p.ny
@@ -163,10 +167,15 @@ def step(prob, H, Qx, Qy, t=0.0, t_end=0.0, stages=False, bound=None, L=None):
         st_arrays["fy"] = np.zeros((3, ny + 1, nx))
         st = _Stages(*[_ptr(st_arrays[f]) for f in STAGE_FIELDS])
     par = _params(p, t_end)
-    rc = (L or lib()).orc_step(ctypes.byref(par), _ptr(bd.b), _ptr(bd.n), bd.solid_ptr(),
-                        ctypes.byref(bd.src), float(t), _ptr(H), _ptr(Qx), _ptr(Qy),
-                        _ptr(Hn), _ptr(Qxn), _ptr(Qyn), ctypes.byref(info),
-                        ctypes.byref(st) if st is not None else None)
+    args = (ctypes.byref(par), _ptr(bd.b), _ptr(bd.n), bd.solid_ptr(), ctypes.byref(bd.src), float(t),
+            _ptr(H), _ptr(Qx), _ptr(Qy), _ptr(Hn), _ptr(Qxn), _ptr(Qyn), ctypes.byref(info),
+            ctypes.byref(st) if st is not None else None)
+    if corr is None:
+        rc = (L or lib()).orc_step(*args)
+    else:
+        corr = _c(corr)
+        assert corr.shape == (3, ny, nx)
+        rc = (L or lib()).orc_step_corr(*args, _ptr(corr))
     if rc != 0:
         raise RuntimeError(f"oracle step failed with status {rc}")
     d = {k: getattr(info, k) for k, _ in _Info._fields_}

@@ -259,10 +259,13 @@ static double source_rate(const orc_sources* s, int m, double t)
 }
 
 /* One full time step from (H, Qx, Qy) at time t to (Hn, Qxn, Qyn).
+ * corr (may be NULL): three [ny][nx] planes added to each cell's net
+ * face-flux sums (Fh, Fv_x, Fv_y) before the final update, the additive
+ * sub-grid corrections of a learned closure of a coarse grid level.
  * Returns 0 on success, -1 on allocation failure, -5 when tau <= 0. */
-int orc_step(const orc_params* p, const double* b, const double* nm, const unsigned char* solid_in,
-             const orc_sources* src, double t, const double* H, const double* Qx, const double* Qy,
-             double* Hn, double* Qxn, double* Qyn, orc_info* info, orc_stages* st)
+int orc_step_corr(const orc_params* p, const double* b, const double* nm, const unsigned char* solid_in,
+                  const orc_sources* src, double t, const double* H, const double* Qx, const double* Qy,
+                  double* Hn, double* Qxn, double* Qyn, orc_info* info, orc_stages* st, const double* corr)
 {
     const int nx = p->nx, ny = p->ny;
     const size_t N = (size_t)nx * (size_t)ny;
@@ -327,17 +330,29 @@ int orc_step(const orc_params* p, const double* b, const double* nm, const unsig
         uty[k] = wet[k] ? (uy[k] + tau * ay2[k]) / (1.0 + tau * phi2[k]) : 0.0;
         uhx[k] = 0.5 * (ux[k] + utx[k]);
         uhy[k] = 0.5 * (uy[k] + uty[k]);
-        /* particle mass plus source; inflow carries V, a drain takes U~ */
+        /* particle mass plus source.  Inflow brings water with velocity V;
+         * a drain takes water with the cell's velocity U~, and never more
+         * than the cell holds: a drain that empties the cell (H + tau sigma
+         * <= 0) leaves it without momentum. */
         double ts = tau * sig[k];
-        ht[k] = dmax(0.0, H[k] + ts);
-        qtx[k] = H[k] * utx[k] + (sig[k] > 0.0 ? ts * vxc[k] : ts * utx[k]);
-        qty[k] = H[k] * uty[k] + (sig[k] > 0.0 ? ts * vyc[k] : ts * uty[k]);
-        /* rain, evaporation and infiltration (Eq. 1 sigma) on every non-wall cell */
+        double hp = H[k] + ts;
+        ht[k] = dmax(0.0, hp);
+        if (sig[k] > 0.0 || hp > 0.0) {
+            qtx[k] = H[k] * utx[k] + (sig[k] > 0.0 ? ts * vxc[k] : ts * utx[k]);
+            qty[k] = H[k] * uty[k] + (sig[k] > 0.0 ? ts * vyc[k] : ts * uty[k]);
+        } else {
+            qtx[k] = 0.0;
+            qty[k] = 0.0;
+        }
+        /* rain, evaporation and infiltration (Eq. 1 sigma) on every non-wall
+         * cell.  Rain adds water at rest; the losses take water with U~, at
+         * most the depth the point source left (max(0, hp)). */
         if (!solid[k] && (p->rain != 0.0 || p->evap != 0.0 || p->infil != 0.0)) {
             double loss = p->evap + p->infil;
-            ht[k] = dmax(0.0, (H[k] + ts) + tau * (p->rain - loss));
-            qtx[k] = qtx[k] - tau * loss * utx[k];
-            qty[k] = qty[k] - tau * loss * uty[k];
+            double taken = dmin(tau * loss, dmax(0.0, hp));
+            ht[k] = dmax(0.0, hp + tau * (p->rain - loss));
+            qtx[k] = qtx[k] - taken * utx[k];
+            qty[k] = qty[k] - taken * uty[k];
         }
         src_sum += ht[k] - H[k];
         wt[k] = (!solid[k] && ht[k] > eps);
@@ -406,6 +421,11 @@ int orc_step(const orc_params* p, const double* b, const double* nm, const unsig
             double fh = (fxl[fw] - fxl[fe]) + (fyl[fs] - fyl[fn]);
             double fqx = (fxl[NFX + fw] - fxl[NFX + fe]) + (fyl[NFY + fs] - fyl[NFY + fn]);
             double fqy = (fxl[2 * NFX + fw] - fxl[2 * NFX + fe]) + (fyl[2 * NFY + fs] - fyl[2 * NFY + fn]);
+            if (corr) {
+                fh = fh + corr[k];
+                fqx = fqx + corr[N + k];
+                fqy = fqy + corr[2 * N + k];
+            }
             double hn = ht[k] + dth * fh;
             if (hn < 0.0) { clip += -hn; hn = 0.0; }
             Hn[k] = hn;
@@ -437,6 +457,13 @@ int orc_step(const orc_params* p, const double* b, const double* nm, const unsig
 done:
     free(solid); free(wet); free(wt); free(w);
     return rc;
+}
+
+int orc_step(const orc_params* p, const double* b, const double* nm, const unsigned char* solid_in,
+             const orc_sources* src, double t, const double* H, const double* Qx, const double* Qy,
+             double* Hn, double* Qxn, double* Qyn, orc_info* info, orc_stages* st)
+{
+    return orc_step_corr(p, b, nm, solid_in, src, t, H, Qx, Qy, Hn, Qxn, Qyn, info, st, NULL);
 }
 
 /* Largest signal speed of a state, as used for tau (for initial checks). */

@@ -414,10 +414,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             }
         }
         const T ts = tauT * sig;
-        T ht = tmax(T(0), H + ts);
-        T qtx = H * utx + (sig > T(0) ? ts * vx : ts * utx);
-        T qty = H * uty + (sig > T(0) ? ts * vy : ts * uty);
-        if (P.dist && b < T(WALL_TEST)) distributed_sources(P, tauT, H, ts, utx, uty, ht, qtx, qty);
+        T ht, qtx, qty;
+        point_source(H, sig, ts, vx, vy, utx, uty, ht, qtx, qty);
+        if (P.dist && b < T(WALL_TEST)) distributed_sources(P, tauT, H + ts, utx, uty, ht, qtx, qty);
         const bool wt = is_wet(ht, b, eps);
         const auto C = cS(r);
         C[0][c] = ht;
@@ -957,10 +956,9 @@ __global__ void ks_correct(const StagedArgs<T> a) {
         a.uhy[k] = T(0.5) * (a.uy[k] + uty);
         const T sig = a.sig[k];
         const T ts = tauT * sig;
-        T ht = tmax(T(0), H + ts);
-        T qtx = H * utx + (sig > T(0) ? ts * a.svx[k] : ts * utx);
-        T qty = H * uty + (sig > T(0) ? ts * a.svy[k] : ts * uty);
-        if (a.P.dist && b < T(WALL_TEST)) distributed_sources(a.P, tauT, H, ts, utx, uty, ht, qtx, qty);
+        T ht, qtx, qty;
+        point_source(H, sig, ts, a.svx[k], a.svy[k], utx, uty, ht, qtx, qty);
+        if (a.P.dist && b < T(WALL_TEST)) distributed_sources(a.P, tauT, H + ts, utx, uty, ht, qtx, qty);
         const bool wt = is_wet(ht, b, a.P.eps);
         a.ht[k] = ht;
         a.qtx[k] = qtx;

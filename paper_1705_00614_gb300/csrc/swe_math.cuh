@@ -324,15 +324,32 @@ __device__ __forceinline__ void face_flux(const Phys<T>& P, const ECell<T>& L, c
     FQy = FH * (FH >= T(0) ? wl[4] : wr[4]);
 }
 
-// Rain, evaporation and infiltration (Eq. 1 sigma) on a non-wall cell after
-// the point sources: depth H~ = max(0, (H + tau sigma_pt) + tau (r - e - i));
-// rain brings water at rest, the losses take water with its velocity U~.
+// Point source of Eqs. 1-3 on the post-Lagrangian state (ts = tau sigma):
+// H~ = max(0, H + ts).  Inflow (sigma > 0) brings water with the source
+// velocity V; a drain takes water with the cell's velocity U~ and never more
+// than the cell holds, so a drain that empties the cell (H + ts <= 0) leaves
+// it without momentum.
 template <class T>
-__device__ __forceinline__ void distributed_sources(const Phys<T>& P, T tau, T H, T ts, T utx, T uty, T& ht, T& qtx,
+__device__ __forceinline__ void point_source(T H, T sig, T ts, T vx, T vy, T utx, T uty, T& ht, T& qtx, T& qty) {
+    const T hp = H + ts;
+    ht = tmax(T(0), hp);
+    const bool keep = sig > T(0) || hp > T(0);
+    qtx = keep ? H * utx + (sig > T(0) ? ts * vx : ts * utx) : T(0);
+    qty = keep ? H * uty + (sig > T(0) ? ts * vy : ts * uty) : T(0);
+}
+
+// Rain, evaporation and infiltration (Eq. 1 sigma) on a non-wall cell after
+// the point sources (hp = H + tau sigma_pt): depth
+// H~ = max(0, hp + tau (r - e - i)); rain brings water at rest, the losses
+// take water with its velocity U~, at most the depth max(0, hp) the point
+// source left.
+template <class T>
+__device__ __forceinline__ void distributed_sources(const Phys<T>& P, T tau, T hp, T utx, T uty, T& ht, T& qtx,
                                                     T& qty) {
-    ht = tmax(T(0), (H + ts) + tau * (P.rain - P.loss));
-    qtx = qtx - tau * P.loss * utx;
-    qty = qty - tau * P.loss * uty;
+    const T taken = tmin(tau * P.loss, tmax(T(0), hp));
+    ht = tmax(T(0), hp + tau * (P.rain - P.loss));
+    qtx = qtx - taken * utx;
+    qty = qty - taken * uty;
 }
 
 // Hydrograph value q(t) of one row (kind, peak, t_p, s), in FP64.

@@ -11,6 +11,7 @@
 // file-scope array below, which every GPU that loads this library holds
 // until the process exits.
 #include <algorithm>
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -84,17 +85,24 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-int encode(CUtensorMap* m, const void* base, int nx, int ny, int64_t pitch) {
+// The driver's tensor-map encoder, looked up once (under the set-up mutex).
+EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
+    std::lock_guard<std::mutex> lock(g_mu);
     if (!fn) {
         void* p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess)
-            return nfail(SWE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-        fn = reinterpret_cast<EncodeTiledFn>(p);
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
     }
+    return fn;
+}
+
+int encode(CUtensorMap* m, const void* base, int nx, int ny, int64_t pitch) {
+    const EncodeTiledFn fn = encode_fn();
+    if (!fn) return nfail(SWE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     cuuint64_t dims[2] = {(cuuint64_t)(nx + 2 * PAD), (cuuint64_t)(ny + 2 * PAD)};
     cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
     cuuint32_t box[2] = {(cuuint32_t)WIN, (cuuint32_t)RB};
@@ -128,6 +136,8 @@ extern "C" SWE_API int swe_step_f32_noalloc(const swe_params* p, const float* H,
         return nfail(SWE_ERR_ARG, "rain, evaporation and infiltration rates must lie in [0, 1) m/s");
     if (pitch < (int64_t)p->nx + 2 * PAD || (pitch % 4) != 0)
         return nfail(SWE_ERR_ARG, "pitch must be >= nx + 2*SWE_PAD and a multiple of 4 floats");
+    // the kernel indexes rows with a 32-bit pitch
+    if (pitch > (int64_t)INT_MAX) return nfail(SWE_ERR_ARG, "pitch must not exceed INT_MAX floats");
     const void* ptrs[8] = {H, Qx, Qy, b, n, H_out, Qx_out, Qy_out};
     for (const void* q : ptrs)
         if (!aligned16(q)) return nfail(SWE_ERR_ARG, "every plane must start on a 16-byte boundary");

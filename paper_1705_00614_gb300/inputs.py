@@ -326,9 +326,11 @@ def floodplain(n: int, dx: float, terrain_seed: int, manning_seed: int,
 
 
 def random_wet_dry(nx: int, ny: int, seed: int, dx: float = 10.0, wet_frac: float = 0.6,
-                   with_sources: bool = True) -> Problem:
+                   with_sources: bool = True, drain: float = -0.01) -> Problem:
     """Small random state with a wet/dry mix for stage-wise parity: fractal
-    bed, random depth where wet, random velocities, all physics terms on."""
+    bed, random depth where wet, random velocities, all physics terms on.
+    About 30% of the source cells are drains of rate ``drain`` (m/s) times a
+    weight in [0.5, 1.5]; a strong rate makes drains that empty their cell."""
     b = quantise_bed(fractal_terrain(nx, ny, seed, relief=3.0))
     u = uniform(seed, 3, np.arange(nx * ny * 4)).reshape(4, ny, nx)
     wet = u[0] < wet_frac
@@ -349,7 +351,7 @@ def random_wet_dry(nx: int, ny: int, seed: int, dx: float = 10.0, wet_frac: floa
         ix = (cells % nx).astype(np.int32)
         iy = (cells // nx).astype(np.int32)
         wts = 0.5 + uniform(seed, 6, np.arange(ns))
-        hyd = [Hydrograph(0, 0.02, 0.0, 50.0), Hydrograph(1, -0.01)]
+        hyd = [Hydrograph(0, 0.02, 0.0, 50.0), Hydrograph(1, drain)]
         hid = (uniform(seed, 7, np.arange(ns)) < 0.3).astype(np.int32)
         vx = np.where(hid == 0, 2.0 * uniform(seed, 8, np.arange(ns)) - 1.0, 0.0)
         vy = np.where(hid == 0, 2.0 * uniform(seed, 9, np.arange(ns)) - 1.0, 0.0)

@@ -1,13 +1,17 @@
 """Pins of the FP64 CNN-closure oracle (oracle/cnn_oracle.py): convolution
 against SciPy's 2-D correlation, the exact adjoint identities of the data
 and weight gradients, finite differences of the whole network's loss, Adam
-against its closed form for a constant gradient, and the 4x4 restriction's
-conservation of block sums."""
+against its closed form for a constant gradient, the 4x4 restriction's
+conservation of block sums, and the closure's corrections: they act on
+interior wet cells only, move no mass, and enter the oracle step's final
+update as (tau/h) times their value."""
 import numpy as np
 import pytest
 from scipy.signal import correlate2d
 
+import oracle
 from oracle import cnn_oracle as C
+from paper_1705_00614_gb300 import inputs as I
 
 
 def test_conv_matches_scipy_correlate():
@@ -98,3 +102,48 @@ def test_bf16_rounding_definition():
     assert C.round_bf16(1.0 + 3 * 2 ** -8) == 1.0 + 2 ** -6  # tie -> even (up)
     x = np.random.default_rng(8).normal(size=1000) * 1e3
     assert np.max(np.abs(C.round_bf16(x) - x) / np.abs(x)) <= 2 ** -8
+
+
+def test_closure_corrections_move_no_mass_and_skip_shores():
+    """Corrections act on cells >= 5 cm deep with four wet neighbours (not
+    on the shore ring, a thin cell, or a cell at the grid edge), the depth
+    part sums to zero over those cells, the momentum parts are the scaled
+    network outputs there."""
+    rng = np.random.default_rng(4)
+    ny, nx = 12, 14
+    H = np.full((ny, nx), 1.0)
+    H[3:6, 4:8] = 0.0          # a dry island
+    H[9, 9] = 0.03             # a thin cell
+    y = rng.normal(size=(1, ny, nx, 3))
+    mu, sd = np.array([0.5, -1.0, 2.0]), np.array([2.0, 3.0, 0.5])
+    c = C.closure_corrections(y, H, 1e-4, mu, sd)
+    on = C.correction_cells(H, 1e-4)
+    assert not on[0].any() and not on[-1].any() and not on[:, 0].any() and not on[:, -1].any()
+    assert not on[2:7, 3:9][H[2:7, 3:9] == 0.0].any() and not on[2, 5] and not on[6, 5] and not on[4, 3]
+    assert not on[9, 9] and on[8, 9] and on[1, 1]  # the thin cell is still wet
+    assert np.all(c[:, ~on] == 0.0)
+    assert abs(c[0][on].sum()) <= 1e-12 * np.abs(c[0][on]).sum()
+    for q in (1, 2):
+        assert np.allclose(c[q][on], (y[0, ..., q] * sd[q] + mu[q])[on], rtol=0, atol=1e-15)
+
+
+def test_oracle_step_applies_flux_corrections_in_the_final_update():
+    """On a lake at rest over a flat bed every face flux is zero, so with
+    corrections c the oracle's final update gives H = H0 + (tau/h) c_h and
+    Q = (tau/h) c_v exactly where H stays wet: +c at one cell and -c at
+    another leave the volume unchanged."""
+    n, tau, dx = 16, 0.1, 2.0
+    z = np.zeros((n, n))
+    p = I.Problem("lake", I.Params(nx=n, ny=n, dx=dx, dt_fixed=tau), z.copy(), z.copy(), np.full((n, n), 1.5),
+                  z.copy(), z.copy(), I.Sources.empty())
+    corr = np.zeros((3, n, n))
+    corr[0, 4, 5], corr[0, 10, 11] = 0.3, -0.3
+    corr[1, 4, 5], corr[2, 10, 11] = 0.7, -0.2
+    H, Qx, Qy, info, _ = oracle.step(p, p.H, p.Qx, p.Qy, 0.0, corr=corr)
+    k = tau / dx
+    assert H[4, 5] == 1.5 + k * 0.3 and H[10, 11] == 1.5 + k * -0.3
+    assert Qx[4, 5] == k * 0.7 and Qy[10, 11] == k * -0.2
+    mask = np.ones((n, n), bool)
+    mask[4, 5] = mask[10, 11] = False
+    assert np.all(H[mask] == 1.5) and np.all(Qx[mask] == 0.0) and np.all(Qy[mask] == 0.0)
+    assert abs(info["mass"] - 1.5 * n * n * dx * dx) <= 1e-12 * info["mass"]

@@ -53,9 +53,15 @@ def _setup(torch, swe, n=2, h=32, w=48, seed=0):
     return params_r, flat, xd, x64[..., :5], td, t.astype(np.float64)
 
 
-# (n, h, w): narrower than one 128-pixel tile of the convolution kernel, and
-# one full plus one partial tile per row
-SHAPES = [(2, 32, 48), (1, 16, 160)]
+# (n, h, w): narrower than one 128-pixel tile of the convolution kernel;
+# one full plus one partial tile per row; then the work splits of real sizes
+# on a 152-SM GPU (456 persistent convolution CTAs, up to 608 weight-gradient
+# CTAs): 2 x 256 x 512 gives 416 items of 5 rows (the six-slot row ring
+# wraps) and 2048 weight-gradient tiles (several per CTA); 1 x 1024 x 1024 is
+# the 1024^2 coarse grid's own split (456 items of 18 rows, 8192 tiles); and
+# 4 x 8 x 15360 makes 480 one-row-band items for 456 CTAs, so some CTAs run
+# two items in a row.
+SHAPES = [(2, 32, 48), (1, 16, 160), (2, 256, 512), (1, 1024, 1024), (4, 8, 15360)]
 
 
 @pytest.mark.parametrize("shape", SHAPES)

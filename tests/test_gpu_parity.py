@@ -111,20 +111,96 @@ def test_fused_equals_staged(swe, prec):
 
 
 def test_stoker_dam_break_f64_200_steps(swe):
-    """256^2 dam break (h 2 m / 1 m, dx 1 m, K 0.3, 200 steps): GPU FP64
-    against the oracle every 20 steps, and exact mass conservation."""
+    """256^2 dam break (h 2 m / 1 m, dx 1 m, K 0.3, 200 steps), GPU FP64:
+    every step within 1e-12 of one oracle step from the GPU's own previous
+    state; the GPU and oracle trajectories within 1e-12 for the first 20
+    steps and 1e-11 after every 20-step block (one-step differences add up);
+    exact mass conservation."""
     p = I.dam_break(256, 1.0)
     bd = oracle._Bound(p)
     H, Qx, Qy, t = p.H, p.Qx, p.Qy, 0.0
+    g = (H, Qx, Qy, t)
+    m0 = 256 * 128 * 3.0
     with swe.Solver.from_problem(p, "f64") as s:
-        for blk in range(10):
-            H, Qx, Qy, t, infos = oracle.run(p, 20, H, Qx, Qy, t)
-            gi = s.step(20)
+        for n in range(200):
+            Hs, Qxs, Qys, info, _ = oracle.step(p, g[0], g[1], g[2], g[3], bound=bd)
+            H, Qx, Qy, info_t, _ = oracle.step(p, H, Qx, Qy, t, bound=bd)
+            t = info_t["t_new"]
+            gi = s.step(1)
             g = s.get_state()
-            assert abs(g[3] - t) <= 1e-12 * t
-            assert_state_close(g[:3], (H, Qx, Qy), 1e-11, f"after {20 * (blk + 1)} steps")
-            m0 = 256 * 128 * 3.0
+            assert abs(gi["dt_last"] - info["tau"]) <= 1e-14 * info["tau"]
+            assert_state_close(g[:3], (Hs, Qxs, Qys), 1e-12, f"step {n + 1} from the GPU state")
+            if n < 20 or (n + 1) % 20 == 0:
+                assert abs(g[3] - t) <= 1e-12 * t
+                assert_state_close(g[:3], (H, Qx, Qy), 1e-12 if n < 20 else 1e-11, f"after {n + 1} steps")
             assert abs(gi["mass"] - m0) <= 1e-13 * m0
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_time_step_set_by_particle_speed(swe, prec):
+    """Thin uniform flow U = (3, 0) m/s, 1 cm deep, under a -20 m/s wind on
+    a flat frictionless bed: the wind stress gives a = -52.9 m/s^2 along x,
+    so the particle speed U_p = |U_x - sqrt(h |a_x|)| (11.5 m/s) exceeds the
+    wave speed U_s (3.3 m/s) and sets tau = K h / U_p (Fig. 2).  The first
+    tau (from the state pass) and the second (from the step's epilogue)
+    against the oracle's, and the first against the closed form."""
+    n, H0, dx = 40, 0.01, 4.0
+    z = np.zeros((n, n))
+    par = I.Params(nx=n, ny=n, dx=dx, wind_x=-20.0, wind_y=0.0, c_a=1.0, rho_air_over_rho=1.0e-3,
+                   coriolis_f=0.0, nu=0.0, cfl=0.3, dt_max=10.0)
+    p = I.Problem("wind", par, z.copy(), z.copy(), np.full((n, n), H0), np.full((n, n), 3.0 * H0),
+                  z.copy(), I.Sources.empty())
+    ax = 1.0e-3 * (-23.0) * 23.0 / H0
+    up = abs(3.0 - math.sqrt(dx * abs(ax)))
+    tol = 1e-14 if prec == "f64" else 1e-6
+    H, Qx, Qy, t = p.H, p.Qx, p.Qy, 0.0
+    with swe.Solver.from_problem(p, prec) as s:
+        for k in range(2):
+            H, Qx, Qy, info, _ = oracle.step(p, H, Qx, Qy, t)
+            t = info["t_new"]
+            gi = s.step(1)
+            assert abs(gi["dt_last"] - info["tau"]) <= tol * info["tau"], (k, gi["dt_last"], info["tau"])
+            if k == 0:
+                assert abs(gi["dt_last"] - 0.3 * dx / up) <= tol * (0.3 * dx / up)
+
+
+@pytest.mark.parametrize("prec", ["f64", "f32"])
+def test_over_draining_sources_match_oracle(swe, prec):
+    """Strong drains (rate -60 m/s x weight, against steps of ~0.01 s) that take more water than many
+    of their cells hold: those cells keep no momentum (a drain takes water
+    with the cell's velocity, never more than the cell holds).  FP64 fused
+    and staged per step within 1e-12 of the oracle; FP32 within 1e-5 after
+    one step."""
+    p = I.random_wet_dry(130, 77, seed=23, drain=-60.0)
+    if prec == "f32":
+        p = p.to_f32_values()
+    _, _, _, info, st = oracle.step(p, p.H, p.Qx, p.Qy, 0.0, stages=True)
+    s_ = p.sources
+    tau = info["tau"]
+    emptied = [(y, x) for x, y, hy, w in zip(s_.ix, s_.iy, s_.hydro, s_.weight)
+               if hy == 1 and p.H[y, x] > p.params.eps and p.H[y, x] - 60.0 * w * tau < 0.0
+               and abs(st["utx"][y, x]) + abs(st["uty"][y, x]) > 1e-3]
+    assert len(emptied) >= 3, "the case must have moving cells emptied by a drain"
+    for y, x in emptied:
+        assert st["qtx"][y, x] == 0.0 and st["qty"][y, x] == 0.0
+    bd = oracle._Bound(p)
+    if prec == "f64":
+        for mode in ("fused", "staged"):
+            H, Qx, Qy, t = p.H, p.Qx, p.Qy, 0.0
+            with swe.Solver.from_problem(p, "f64", mode) as s:
+                for n in range(4):
+                    H, Qx, Qy, info, _ = oracle.step(p, H, Qx, Qy, t, bound=bd)
+                    t = info["t_new"]
+                    gi = s.step(1)
+                    g = s.get_state()
+                    assert_state_close(g[:3], (H, Qx, Qy), 1e-12, f"{mode} step {n}")
+                    assert abs(gi["src_vol"] - info["src_vol"]) <= 1e-9 * max(1.0, abs(info["src_vol"]))
+    else:
+        Ho, Qxo, Qyo, info, _ = oracle.step(p, p.H, p.Qx, p.Qy, 0.0, bound=bd)
+        with swe.Solver.from_problem(p, "f32", "fused") as s:
+            s.step(1)
+            g = s.get_state()
+        assert_state_close(g[:3], (Ho, Qxo, Qyo), 1e-5)
 
 
 @pytest.mark.parametrize("prec", ["f64", "f32"])

@@ -76,6 +76,34 @@ def test_skip_equals_full_step_on_dry_start_floodplain(swe, prec):
     assert rb[-1]["skipped"] > 0 and rb[-1]["wet_cells"] > 0
 
 
+def test_skip_matches_oracle_each_step_on_dry_start_floodplain(swe):
+    """Skipping run against the FP64 oracle (not only against the run
+    without skipping): dry-start 384^2 floodplain with a Gaussian inflow
+    hydrograph at the west edge, FP64, skip on, 120 steps one at a time.
+    Every step's state within 1e-12 relative L-inf of the oracle's, time
+    and mass likewise, and most work items skipped throughout."""
+    import oracle
+
+    p = I.floodplain(384, 10.0, 2017, 2018, nsrc=20, hydro=I.Hydrograph(0, 5.0, 5.0, 3.0))
+    bd = oracle._Bound(p)
+    H, Qx, Qy, t = p.H, p.Qx, p.Qy, 0.0
+    skipped = []
+    with swe.Solver.from_problem(p, "f64", seg_h=32, skip_dry=True) as s:
+        for n in range(120):
+            H, Qx, Qy, info, _ = oracle.step(p, H, Qx, Qy, t, bound=bd)
+            t = info["t_new"]
+            gi = s.step(1)
+            g = s.get_state()
+            assert abs(g[3] - t) <= 1e-13 * t
+            for name, a, o in zip(("H", "Qx", "Qy"), g[:3], (H, Qx, Qy)):
+                err = np.abs(a - o).max() / max(np.abs(o).max(), 1e-6)
+                assert err <= 1e-12, f"step {n + 1} {name}: rel Linf {err:.3e}"
+            assert abs(gi["mass"] - info["mass"]) <= 1e-12 * max(info["mass"], 1e-300)
+            assert gi["wet_cells"] == info["wet"]
+            skipped.append(gi["skipped"])
+    assert info["wet"] > 0 and min(skipped[1:]) > 0
+
+
 @pytest.mark.parametrize("prec", ["f32", "f64"])
 def test_skip_with_gates_and_state_set_into_skipped_area(swe, prec):
     p = _patchy(300, 260, 51, prec, centre=(60, 70), radius=45)

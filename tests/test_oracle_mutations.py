@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as P
+from tests import test_cnn_oracle_pins as CP
 from tests import test_oracle_rain as R
 
 _SRC = os.path.join(os.path.dirname(oracle.__file__), "swe_oracle.c")
@@ -58,16 +59,45 @@ MUTANTS = [
      ["test_stoker_dam_break_256"]),
     ("source at t_n", "sig[k] = source_rate(src, m, t + th);", "sig[k] = source_rate(src, m, t);",
      ["test_source_volume_matches_hydrograph_integral"]),
-    ("drain volume unclamped", "ht[k] = dmax(0.0, H[k] + ts);", "ht[k] = H[k] + ts;",
+    ("drain volume unclamped", "ht[k] = dmax(0.0, hp);", "ht[k] = hp;",
      ["test_drain_on_dry_ground_removes_nothing"]),
-    ("evaporation adds water", "ht[k] = dmax(0.0, (H[k] + ts) + tau * (p->rain - loss));",
-     "ht[k] = dmax(0.0, (H[k] + ts) + tau * (p->rain + loss));",
+    ("evaporation adds water", "ht[k] = dmax(0.0, hp + tau * (p->rain - loss));",
+     "ht[k] = dmax(0.0, hp + tau * (p->rain + loss));",
      ["test_evaporation_and_infiltration_drain_still_water_until_dry"]),
-    ("losses leave the momentum", "qtx[k] = qtx[k] - tau * loss * utx[k];", "qtx[k] = qtx[k];",
+    ("losses leave the momentum", "qtx[k] = qtx[k] - taken * utx[k];", "qtx[k] = qtx[k];",
      ["test_losses_keep_the_velocity_and_rain_slows_the_flow"]),
     ("rain on gates", "if (!solid[k] && (p->rain != 0.0", "if ((p->rain != 0.0",
      ["test_rain_volume_budget_over_terrain_with_gates"]),
+    ("drain keeps the momentum of a negative depth", "if (sig[k] > 0.0 || hp > 0.0) {", "if (1) {",
+     ["test_drain_emptying_a_moving_cell_leaves_no_momentum"]),
+    ("losses take more than the cell holds", "double taken = dmin(tau * loss, dmax(0.0, hp));",
+     "double taken = tau * loss;",
+     ["test_losses_beyond_the_depth_take_no_more_momentum_than_the_cell_holds"]),
+    ("particle speed dropped", "double s = dmax(us, dmax(upx, upy));", "double s = us;",
+     ["test_time_step_from_particle_speed"]),
+    ("particle speed without h", "double upx = fabs(ux[k] + sgn(ax[k]) * sqrt(p->dx * fabs(ax[k])));",
+     "double upx = fabs(ux[k] + sgn(ax[k]) * sqrt(fabs(ax[k])));", ["test_time_step_from_particle_speed"]),
+    ("particle speed without sign", "double upx = fabs(ux[k] + sgn(ax[k]) * sqrt(p->dx * fabs(ax[k])));",
+     "double upx = fabs(ux[k] + sqrt(p->dx * fabs(ax[k])));", ["test_time_step_from_particle_speed"]),
+    ("particle speed y from a_x", "double upy = fabs(uy[k] + sgn(ay[k]) * sqrt(p->dx * fabs(ay[k])));",
+     "double upy = fabs(uy[k] + sgn(ax[k]) * sqrt(p->dx * fabs(ax[k])));", ["test_time_step_from_particle_speed"]),
+    ("wave speed from the sum of components", "double us = dmax(fabs(ux[k]), fabs(uy[k])) + c;",
+     "double us = fabs(ux[k]) + fabs(uy[k]) + c;", ["test_time_step_from_wave_speed_two_components"]),
+    ("closure correction of Q_x applied to Q_y", "fqy = fqy + corr[2 * N + k];", "fqy = fqy + corr[N + k];",
+     ["test_oracle_step_applies_flux_corrections_in_the_final_update"]),
+    ("closure correction subtracted", "fh = fh + corr[k];", "fh = fh - corr[k];",
+     ["test_oracle_step_applies_flux_corrections_in_the_final_update"]),
 ]
+
+
+def _cases(fn):
+    """Argument tuples of a pin: its parametrize cases, or one empty call."""
+    marks = [m for m in getattr(fn, "pytestmark", []) if m.name == "parametrize"]
+    if not marks:
+        return [()]
+    names, values = marks[0].args[0], marks[0].args[1]
+    single = "," not in names if isinstance(names, str) else len(names) == 1
+    return [(v,) if single else tuple(v) for v in values]
 
 
 @pytest.fixture(scope="module")
@@ -87,8 +117,10 @@ def test_pins_catch_mutant(name, old, new, pins, tmpdir_mod, monkeypatch):
     monkeypatch.setattr(oracle, "_lib", oracle.lib(so))
     caught = []
     for pin in pins:
+        fn = getattr(P, pin, None) or getattr(R, pin, None) or getattr(CP, pin)
         try:
-            (getattr(P, pin, None) or getattr(R, pin))(*([1] if pin == "test_thacker_bowl" else []))
+            for args in _cases(fn):
+                fn(*args)
         except (AssertionError, RuntimeError, FloatingPointError, ValueError, ZeroDivisionError):
             caught.append(pin)
             break

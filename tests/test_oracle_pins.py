@@ -264,6 +264,74 @@ def test_drain_on_dry_ground_removes_nothing():
     assert abs(infos[-1]["mass"] - m0) <= 1e-13 * m0
 
 
+
+def test_drain_emptying_a_moving_cell_leaves_no_momentum():
+    """A drain that takes more than a moving cell holds (H + tau sigma < 0)
+    empties it: no water is left to carry momentum, so the post-Lagrangian
+    momentum is zero, and the water the face fluxes then bring in (from the
+    west and from the east, both carrying the +x flow) gives the cell
+    positive x momentum, never the reversed momentum of a negative depth."""
+    n, c = 24, 12
+    p = _box(n, H=0.1, ux=1.0, dx=1.0, dt_fixed=0.05)
+    src = I.Sources(np.array([c], dtype=np.int32), np.array([c], dtype=np.int32), np.array([1.0]),
+                    np.zeros(1), np.zeros(1), np.zeros(1, dtype=np.int32), [I.Hydrograph(1, -20.0)])
+    prob = I.Problem("drain", p.params, p.b, p.n_manning, p.H, p.Qx, p.Qy, src)
+    Hn, Qxn, Qyn, info, st = oracle.step(prob, p.H, p.Qx, p.Qy, 0.0, stages=True)
+    assert st["utx"][c, c] > 0.9  # the water that was there moved at about +1 m/s
+    assert st["ht"][c, c] == 0.0 and st["qtx"][c, c] == 0.0 and st["qty"][c, c] == 0.0
+    assert Hn[c, c] > prob.params.eps  # refilled by the face fluxes
+    assert Qxn[c, c] > 0.0 and Qxn[c, c] / Hn[c, c] <= 1.0 + 1e-12
+    assert abs(Qyn[c, c]) <= 1e-15
+    # the drain removed exactly the 0.1 m the cell held
+    assert abs(info["src_vol"] - (-0.1)) <= 1e-15
+
+
+# ------------------------------------------------------------ signal speed
+
+def _wind_box(u, w, H=0.01, dx=4.0, n=12):
+    """Uniform flow U on a flat frictionless bed under wind W.  The pressure
+    and viscous terms vanish for a uniform state, Coriolis is off, so the
+    acceleration is the wind stress alone: a = C_a (rho_a/rho) (W - U)|W - U| / H."""
+    return _box(n, H=H, ux=u[0], uy=u[1], dx=dx, wind_x=w[0], wind_y=w[1], c_a=1.0,
+                rho_air_over_rho=1.0e-3, coriolis_f=0.0, nu=0.0, cfl=0.3, dt_max=10.0)
+
+
+@pytest.mark.parametrize("u,w", [((3.0, 0.0), (-20.0, 0.0)),   # a against U along x
+                                 ((0.0, 3.0), (0.0, -20.0)),   # the same along y
+                                 ((3.0, 0.0), (30.0, 0.0)),    # a along U
+                                 ((-2.0, 1.0), (15.0, -25.0))])  # both components
+def test_time_step_from_particle_speed(u, w):
+    """Where the acceleration is strong and the layer thin, the particle
+    speed U_p = max_d |U_d + sgn(a_d) sqrt(h |a_d|)| exceeds the wave speed
+    U_s = max(|U_x|, |U_y|) + sqrt(g H) and sets tau = K h / max(U_s, U_p)
+    (Sec. 2.3, Fig. 2).  Here a is known in closed form (wind stress only)."""
+    H, dx, g, K = 0.01, 4.0, 9.81, 0.3
+    p = _wind_box(u, w, H=H, dx=dx)
+    dwx, dwy = w[0] - u[0], w[1] - u[1]
+    wm = math.hypot(dwx, dwy)
+    a = (1.0e-3 * dwx * wm / H, 1.0e-3 * dwy * wm / H)
+    us = max(abs(u[0]), abs(u[1])) + math.sqrt(g * H)
+    up = max(abs(u[d] + math.copysign(math.sqrt(dx * abs(a[d])), a[d])) if a[d] != 0.0 else abs(u[d])
+             for d in range(2))
+    assert up > 1.2 * us  # the case really is set by the particle speed
+    _, _, _, info, _ = oracle.step(p, p.H, p.Qx, p.Qy, 0.0)
+    assert abs(info["smax"] - up) <= 1e-14 * up
+    assert abs(info["tau"] - K * dx / up) <= 1e-14 * (K * dx / up)
+
+
+def test_time_step_from_wave_speed_two_components():
+    """A deep uniform flow with both components nonzero and no force (no
+    wind stress since W = U, flat bed): a = 0, so U_p = max(|U_x|, |U_y|)
+    and the wave speed U_s = max(|U_x|, |U_y|) + sqrt(g H) sets
+    tau = K h / U_s (Sec. 2.3, Fig. 2)."""
+    u, H, dx, g, K = (3.0, -4.0), 2.0, 4.0, 9.81, 0.3
+    p = _wind_box(u, u, H=H, dx=dx)
+    us = max(abs(u[0]), abs(u[1])) + math.sqrt(g * H)
+    _, _, _, info, _ = oracle.step(p, p.H, p.Qx, p.Qy, 0.0)
+    assert abs(info["smax"] - us) <= 1e-14 * us
+    assert abs(info["tau"] - K * dx / us) <= 1e-14 * (K * dx / us)
+
+
 # ------------------------------------------------------------ Riemann solver
 
 def test_riemann_two_rarefactions_is_exact():

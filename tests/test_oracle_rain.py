@@ -69,3 +69,18 @@ def test_rain_volume_budget_over_terrain_with_gates():
     assert abs(oracle.mass(prob, H) - m0 - src - clip) <= 1e-9 * m0
     # gate cells got no rain
     assert np.array_equal(H[prob.solid == 1], prob.H[prob.solid == 1])
+
+
+def test_losses_beyond_the_depth_take_no_more_momentum_than_the_cell_holds():
+    """Losses of (e + i) tau deeper than a moving layer, with rain that keeps
+    the cell wet: the losses take the moving water (all of it) and its
+    momentum, never more, so what is left is rain water at rest (zero
+    momentum everywhere, not a reversed flow)."""
+    H0, u0 = 0.001, 1.0
+    prob = _basin(H0=H0, u0=u0, evap_rate=0.04, rain_rate=0.03)
+    Hn, Qxn, Qyn, info, st = oracle.step(prob, prob.H, prob.Qx, prob.Qy, 0.0, stages=True)
+    assert TAU * 0.04 > H0  # the losses exceed the layer
+    assert np.all(st["ht"] > prob.params.eps)  # the rain keeps every cell wet
+    assert np.abs(st["qtx"]).max() == 0.0 and np.abs(Qxn).max() == 0.0
+    # away from the walls the (still moving) particles carry as much in as out
+    assert np.abs(Hn[:, 3:-3] - (H0 + TAU * (0.03 - 0.04))).max() <= 1e-15

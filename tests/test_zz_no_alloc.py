@@ -76,6 +76,22 @@ def test_noalloc_step_matches_swe_step_twice(env):
         assert abs(i2["t"] - ref2[3]) <= 1e-12 * ref2[3]
     # the ring (walls) was left alone
     assert float(b[0, 0]) == float(np.float32(1.0e30)) and float(a[0][0:10].abs().max()) == 0.0
+    # the property the entry point exists for: further calls allocate no
+    # device memory (neither the driver's free bytes nor torch's pool move)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    stats0 = torch.cuda.memory_stats().get("allocation.all.allocated", 0)
+    t, ms = i2["t"], i2["max_speed"]
+    src, dst = a, out
+    with torch.cuda.stream(stream):
+        for _ in range(4):
+            i = swe.step_f32_noalloc(prob.params, *[x.data_ptr() for x in src], b.data_ptr(), n.data_ptr(),
+                                     *[x.data_ptr() for x in dst], pitch, t, ms, stream.cuda_stream)
+            t, ms = i["t"], i["max_speed"]
+            src, dst = dst, src
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] >= free0
+    assert torch.cuda.memory_stats().get("allocation.all.allocated", 0) == stats0
 
 
 def test_noalloc_rejects_grids_beyond_its_scratch(env):
@@ -86,3 +102,8 @@ def test_noalloc_rejects_grids_beyond_its_scratch(env):
     with pytest.raises(swe.SweError) as e:
         swe.step_f32_noalloc(params, *([fake] * 8), nx + 20 + 12, 0.0, 0.0)
     assert e.value.code == -1 and "scratch" in str(e.value)
+    # a row pitch the kernel's 32-bit row index cannot hold
+    params = I.Params(nx=64, ny=8, dx=1.0)
+    with pytest.raises(swe.SweError) as e:
+        swe.step_f32_noalloc(params, *([fake] * 8), (1 << 31) + 4, 0.0, 0.0)
+    assert e.value.code == -1 and "INT_MAX" in str(e.value)
