@@ -258,16 +258,22 @@ def run_cnn(args, torch, swe, stream, rank, world):
 def run_closure(args, torch, swe, stream, rank, world):
     """Learned closure of the 4x coarser grid (closure-<n>sq: fine n^2 at
     dx = 5 m, coarse (n/4)^2 at 20 m).  Trains the network on fine runs of
-    the training seeds, then runs held-out seeds fine, coarse plain and
-    coarse closed side by side and reports the relative L2 error in H of
-    both coarse runs against the restricted fine solution at several
-    horizons, and the wall-clock speed-up of the closed coarse solve over
-    the fine solve (same simulated time)."""
+    the training seeds; runs the validation seeds fine, coarse plain and
+    coarse closed with every candidate correction scale alpha side by side
+    and keeps the alpha with the smallest mean error at the longest horizon;
+    then runs the held-out test seeds the same way and reports the relative
+    L2 error in H of the plain and the closed coarse runs against the
+    restricted fine solution at several horizons (the chosen alpha's test
+    errors are the line's value), and the wall-clock speed-up of the closed
+    coarse solve over the fine solve (same simulated time).  The three seed
+    sets are disjoint; nothing is chosen on the test seeds."""
     from paper_1705_00614_gb300 import closure as CL
     n = int(args.workload.split("-")[1].replace("sq", ""))
     tau_c = 0.2
     train_seeds = list(range(20000, 20000 + args.closure_train))
     test_seeds = list(range(20064, 20064 + args.closure_test))
+    val_seeds = list(range(20100, 20100 + args.closure_val))
+    assert not (set(train_seeds) & set(test_seeds)) and not (set(val_seeds) & (set(train_seeds) | set(test_seeds)))
     horizons = [h for h in (10, 100, 1000, 5000) if h <= args.closure_steps]
 
     def scenario(seed):
@@ -276,11 +282,14 @@ def run_closure(args, torch, swe, stream, rank, world):
 
     rng = np.random.default_rng(0)
     t0 = time.perf_counter()
-    norm = CL.estimate_norm(torch, [scenario(train_seeds[0])], 10, tau_c, rng, 128, bed=args.closure_bed)
+    win = args.closure_window
+    norm = CL.estimate_norm(torch, [scenario(train_seeds[0])], 10 * win, tau_c, rng, 128, bed=args.closure_bed,
+                            horizon=win)
     X, T = [], []
     for sd in train_seeds:
-        x, t = CL.collect(torch, scenario(sd), args.closure_collect, tau_c, norm.inp(), norm.out(), 8, 128, rng,
-                          stream=stream.cuda_stream, noise=args.closure_noise, bed=args.closure_bed)
+        x, t = CL.collect(torch, scenario(sd), args.closure_collect, tau_c, norm.inp(), norm.out(),
+                          args.closure_crops, 128, rng, stream=stream.cuda_stream, noise=args.closure_noise,
+                          bed=args.closure_bed, horizon=win)
         X.append(x)
         T.append(t)
     X = torch.cat(X)
@@ -289,8 +298,8 @@ def run_closure(args, torch, swe, stream, rank, world):
     # optional rounds of pairs from the closed model's own trajectory
     for r in range(args.closure_dagger):
         for sd in train_seeds:
-            x, t = CL.collect_closed(torch, scenario(sd), args.closure_collect, tau_c, params, norm, 8, 128, rng,
-                                     stream=stream.cuda_stream, bed=args.closure_bed)
+            x, t = CL.collect_closed(torch, scenario(sd), args.closure_collect, tau_c, params, norm,
+                                     args.closure_crops, 128, rng, stream=stream.cuda_stream, bed=args.closure_bed)
             if x is not None:
                 X = torch.cat([X, x])
                 T = torch.cat([T, t])
@@ -302,75 +311,85 @@ def run_closure(args, torch, swe, stream, rank, world):
 
     alphas = [float(a) for a in args.closure_alpha.split(",")]
     names = ["plain"] + [f"closed_a{a:g}" for a in alphas]
-    errs = {k: {h: [] for h in horizons} for k in names}
     ms_fine, ms_closed = [], []
-    for sd in test_seeds:
-        fp = scenario(sd)
-        cp = CL.coarse_problem(fp, args.closure_bed)
-        fine = swe.Solver.from_problem(CL.with_dt(fp, tau_c / 4.0), "f32", stream=stream.cuda_stream)
-        plain = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
-        closed = [swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream) for _ in alphas]
-        ref = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
-        nets = [swe.CNN(1, cp.params.ny, cp.params.nx, stream.cuda_stream) for _ in alphas]
-        alive = [True] * len(alphas)
-        try:
-            plain.restrict_from(fine)
-            for c, net, a in zip(closed, nets, alphas):
-                net.set_params(params)
-                c.restrict_from(fine)
-                c.attach_closure(net, CL.shrink(norm, a).all())
-            done = 0
-            for h in horizons:
-                k = h - done
-                e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-                e[0].record(stream)
-                fine.step(4 * k, report=False)
-                e[1].record(stream)
-                if alive[0]:
-                    closed[0].step_closed(k, report=False)
-                e[2].record(stream)
-                for q in range(1, len(alphas)):
-                    if alive[q]:
-                        closed[q].step_closed(k, report=False)
-                plain.step(k, report=False)
-                torch.cuda.synchronize()
-                ms_fine.append(e[0].elapsed_time(e[1]) / k)
-                if alive[0]:
-                    ms_closed.append(e[1].elapsed_time(e[2]) / k)
-                done = h
-                ref.restrict_from(fine)
-                Hr = ref.get_state()[0]
-                den = max(np.linalg.norm(Hr), 1e-30)
-                errs["plain"][h].append(float(np.linalg.norm(plain.get_state()[0] - Hr) / den))
-                for q, (c, a) in enumerate(zip(closed, alphas)):
-                    Hc = c.get_state()[0] if alive[q] else None
-                    if Hc is None or not np.isfinite(Hc).all():
-                        alive[q] = False  # diverged: reported as NaN from here on
-                        errs[names[1 + q]][h].append(float("nan"))
-                    else:
-                        errs[names[1 + q]][h].append(float(np.linalg.norm(Hc - Hr) / den))
-        finally:
-            for c in closed:
-                c.attach_closure(None, norm.all())
-            for x in [fine, plain, ref] + closed + nets:
-                x.close()
-    mean = {k: {h: float(np.mean(v)) for h, v in d.items()} for k, d in errs.items()}
+
+    def run_seeds(seeds):
+        errs = {k: {h: [] for h in horizons} for k in names}
+        for sd in seeds:
+            fp = scenario(sd)
+            cp = CL.coarse_problem(fp, args.closure_bed)
+            fine = swe.Solver.from_problem(CL.with_dt(fp, tau_c / 4.0), "f32", stream=stream.cuda_stream)
+            plain = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
+            closed = [swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
+                      for _ in alphas]
+            ref = swe.Solver.from_problem(CL.with_dt(cp, tau_c), "f32", stream=stream.cuda_stream)
+            nets = [swe.CNN(1, cp.params.ny, cp.params.nx, stream.cuda_stream) for _ in alphas]
+            alive = [True] * len(alphas)
+            try:
+                plain.restrict_from(fine)
+                for c, net, a in zip(closed, nets, alphas):
+                    net.set_params(params)
+                    c.restrict_from(fine)
+                    c.attach_closure(net, CL.shrink(norm, a).all())
+                done = 0
+                for h in horizons:
+                    k = h - done
+                    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+                    e[0].record(stream)
+                    fine.step(4 * k, report=False)
+                    e[1].record(stream)
+                    if alive[0]:
+                        closed[0].step_closed(k, report=False)
+                    e[2].record(stream)
+                    for q in range(1, len(alphas)):
+                        if alive[q]:
+                            closed[q].step_closed(k, report=False)
+                    plain.step(k, report=False)
+                    torch.cuda.synchronize()
+                    ms_fine.append(e[0].elapsed_time(e[1]) / k)
+                    if alive[0]:
+                        ms_closed.append(e[1].elapsed_time(e[2]) / k)
+                    done = h
+                    ref.restrict_from(fine)
+                    Hr = ref.get_state()[0]
+                    den = max(np.linalg.norm(Hr), 1e-30)
+                    errs["plain"][h].append(float(np.linalg.norm(plain.get_state()[0] - Hr) / den))
+                    for q, (c, a) in enumerate(zip(closed, alphas)):
+                        Hc = c.get_state()[0] if alive[q] else None
+                        if Hc is None or not np.isfinite(Hc).all():
+                            alive[q] = False  # diverged: reported as NaN from here on
+                            errs[names[1 + q]][h].append(float("nan"))
+                        else:
+                            errs[names[1 + q]][h].append(float(np.linalg.norm(Hc - Hr) / den))
+            finally:
+                for c in closed:
+                    c.attach_closure(None, norm.all())
+                for x in [fine, plain, ref] + closed + nets:
+                    x.close()
+        return {k: {h: float(np.mean(v)) for h, v in d.items()} for k, d in errs.items()}
+
     last = horizons[-1]
-    best = min(names[1:], key=lambda k: (np.nan_to_num(mean[k][last], nan=np.inf)))
+    val = run_seeds(val_seeds)
+    chosen = min(names[1:], key=lambda k: np.nan_to_num(val[k][last], nan=np.inf))
+    test = run_seeds(test_seeds)
+    gain = [h for h in horizons if test[chosen][h] < test["plain"][h]]
     speedup = float(np.median(ms_fine)) / float(np.median(ms_closed))
     if rank == 0:
-        line = {"metric": "CNN-closure vs fine solve: relative L2 error in H", "value": mean[best][last],
+        line = {"metric": "CNN-closure vs fine solve: relative L2 error in H", "value": test[chosen][last],
                 "unit": "fraction", "n_gpus": world, "steps": last, "warmup": 0,
                 "ms_per_step": float(np.median(ms_closed)), "higher_is_better": False, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+bf16", "data": "synthetic",
                 "config": {"workload": args.workload, "fine": f"{n}^2 dx 5 m", "coarse": f"{n // 4}^2 dx 20 m",
                            "scenario": "fractal floodplain, flood release (+2 m over the first quarter) and inflow",
-                           "tau_coarse_s": tau_c, "train_seeds": len(train_seeds), "test_seeds": len(test_seeds),
-                           "collect_steps_per_seed": args.closure_collect, "train_iters": args.closure_iters,
+                           "tau_coarse_s": tau_c, "train_seeds": len(train_seeds), "val_seeds": len(val_seeds),
+                           "test_seeds": len(test_seeds), "collect_steps_per_seed": args.closure_collect,
+                           "target_window_steps": win, "crops_per_window": args.closure_crops,
+                           "train_iters": args.closure_iters,
                            "dagger_rounds": args.closure_dagger, "input_noise": args.closure_noise,
                            "coarse_bed": args.closure_bed,
                            "final_train_loss": hist[-1][1], "train_wall_s": t_train,
-                           "rel_l2": mean, "reported": best,
+                           "rel_l2_test": test, "rel_l2_val": val, "chosen_on_val": chosen,
+                           "closed_below_plain_at": gain,
                            "target": 0.01, "speedup_closed_coarse_vs_fine": speedup,
                            "ms_per_fine_step": float(np.median(ms_fine)),
                            "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -641,13 +660,19 @@ def main():
     ap.add_argument("--seg-h", type=int, default=0, help="output rows per work item (0 = automatic)")
     ap.add_argument("--mode", default="fused", choices=["fused", "staged"],
                     help="staged: one kernel per stage (the paper's K2-K8 split), for per-stage time shares")
-    ap.add_argument("--closure-train", type=int, default=8, help="closure workload: training seeds")
-    ap.add_argument("--closure-test", type=int, default=4, help="closure workload: held-out seeds")
+    ap.add_argument("--closure-train", type=int, default=64, help="closure workload: training seeds")
+    ap.add_argument("--closure-val", type=int, default=8,
+                    help="closure workload: validation seeds (choose the correction scale)")
+    ap.add_argument("--closure-test", type=int, default=16, help="closure workload: held-out test seeds")
     ap.add_argument("--closure-collect", type=int, default=100, help="closure workload: coarse steps per seed")
+    ap.add_argument("--closure-crops", type=int, default=2,
+                    help="closure workload: 128^2 training crops per target window")
+    ap.add_argument("--closure-window", type=int, default=1,
+                    help="closure workload: coarse steps per training target (average correction over the window)")
     ap.add_argument("--closure-iters", type=int, default=3000, help="closure workload: Adam steps")
     ap.add_argument("--closure-steps", type=int, default=5000, help="closure workload: longest horizon")
-    ap.add_argument("--closure-alpha", default="1",
-                    help="closure workload: comma-separated correction scales to evaluate side by side")
+    ap.add_argument("--closure-alpha", default="1,0.5,0.25,0.1,0.05",
+                    help="closure workload: comma-separated correction scales; the validation seeds pick one")
     ap.add_argument("--closure-bed", default="volume", choices=["mean", "volume"],
                     help="closure workload: coarse bed from 4x4 means, or volume-matched in partly wet cells")
     ap.add_argument("--closure-noise", type=float, default=0.0,

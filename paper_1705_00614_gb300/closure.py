@@ -127,15 +127,21 @@ def perturb(H, Qx, Qy, rel, rng):
 
 
 def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, crop, rng, stream=None, noise=0.0,
-            bed="mean"):
-    """Run the fine grid and, for every coarse step, the coarse step taken
-    from the restricted fine state; return standardised (inputs, targets)
-    crops as device tensors [S, crop, crop, 16] BF16 and [S, crop, crop, 3]
-    FP32.  With noise > 0 the coarse step starts from the restricted fine
-    state perturbed by that relative noise (perturb) while the target stays
-    the restricted fine state one step later, so the network also learns to
-    pull a state that has drifted back (input noise against the distribution
-    shift of closed runs)."""
+            bed="mean", horizon=1):
+    """Run the fine grid and, for every window of `horizon` coarse steps,
+    the plain coarse steps taken from the restricted fine state at the
+    window's start; return standardised (inputs, targets) crops as device
+    tensors [S, crop, crop, 16] BF16 and [S, crop, crop, 3] FP32.  Inputs
+    are the features of the window's first state; the target is the
+    correction of the flux sums, per coarse step, that puts the plain coarse
+    grid on the restricted fine state at the window's end (horizon = 1: the
+    next step; horizon > 1: the average correction over the window, which
+    keeps the part of the correction that persists over several steps and
+    averages out the step-to-step part).  With noise > 0 the coarse steps
+    start from the restricted fine state perturbed by that relative noise
+    (perturb) while the target stays the restricted fine state, so the
+    network also learns to pull a state that has drifted back (input noise
+    against the distribution shift of closed runs)."""
     cp = coarse_problem(fine_prob, bed)
     nyc, nxc = cp.params.ny, cp.params.nx
     fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
@@ -144,17 +150,21 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
     xs, ts = [], []
     xfull = torch.empty((nyc, nxc, 16), dtype=torch.bfloat16, device="cuda")
     tfull = torch.empty((nyc, nxc, 3), dtype=torch.float32, device="cuda")
+    # per-step corrections: (R(q_f) - q_c) h / (horizon tau) is standardised
+    # as ((R(q_f) - q_c) h / tau - horizon mu) / (horizon sd)
+    nout = np.asarray(norm_out, dtype=np.float32).copy()
+    nout *= np.float32(horizon)
     try:
-        for _ in range(steps):
+        for _ in range(max(1, steps // horizon)):
             A.restrict_from(fine)
             if noise > 0.0:
                 H, Qx, Qy, t = A.get_state()
                 A.set_state(*perturb(H, Qx, Qy, noise, rng), t)
             A.closure_features(norm_in, xfull.data_ptr())
-            A.step(1)
-            fine.step(4)
+            A.step(horizon)
+            fine.step(4 * horizon)
             B.restrict_from(fine)
-            A.closure_targets(B, norm_out, tfull.data_ptr())
+            A.closure_targets(B, nout, tfull.data_ptr())
             torch.cuda.synchronize()
             for _ in range(crops_per_step):
                 y0 = int(rng.integers(0, nyc - crop + 1))
@@ -219,12 +229,13 @@ def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step,
     return torch.stack(xs), torch.stack(ts).clamp_(-10.0, 10.0)
 
 
-def estimate_norm(torch, probs, steps, tau_c, rng, crop, bed="mean"):
+def estimate_norm(torch, probs, steps, tau_c, rng, crop, bed="mean", horizon=1):
     """Per-channel mean and standard deviation of inputs and targets from a
-    short pilot collection with identity normalisation."""
+    short pilot collection with identity normalisation (targets over windows
+    of `horizon` coarse steps, as collect makes them)."""
     X, T = [], []
     for p in probs:
-        x, t = collect(torch, p, steps, tau_c, NORM_ID_IN, NORM_ID_OUT, 4, crop, rng, bed=bed)
+        x, t = collect(torch, p, steps, tau_c, NORM_ID_IN, NORM_ID_OUT, 4, crop, rng, bed=bed, horizon=horizon)
         X.append(x.float().cpu().numpy().reshape(-1, 16)[:, :5])
         T.append(t.cpu().numpy().reshape(-1, 3))
     X = np.concatenate(X).astype(np.float64)

@@ -321,7 +321,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             T usx = T(0), usy = T(0);
             if (sizeof(T) == 4 || wet) {
                 const T den = T(1) + th * friction(P, H, rN(k)[c], ux, uy);
-                div2(ux + th * rA(0, k)[c], uy + th * rA(1, k)[c], den, usx, usy);
+                lin_div2(ux, uy, th, rA(0, k)[c], rA(1, k)[c], den, usx, usy);
             }
             const auto A = aU(k);
             A[0][c] = wet ? usx : T(0);
@@ -346,7 +346,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             T ax, ay, phi;
             forces(P, H, b, rN(r)[c], U0[0][c], U0[1][c], W, E, S, N, ax, ay, phi);
             const T den = T(1) + th * phi;
-            div2(U0[0][c] + th * ax, U0[1][c] + th * ay, den, usx, usy);
+            lin_div2(U0[0][c], U0[1][c], th, ax, ay, den, usx, usy);
         }
         const auto A = aU(r);
         A[0][c] = usx;
@@ -401,9 +401,17 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             T ax, ay, phi;
             forces(P, B0[c], b, nm, A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
             const T den = T(1) + tauT * phi;
-            div2(ux + tauT * ax, uy + tauT * ay, den, utx, uty);
+            lin_div2(ux, uy, tauT, ax, ay, den, utx, uty);
         }
-        const T uhx = T(0.5) * (ux + utx), uhy = T(0.5) * (uy + uty);
+        T uhx, uhy;
+        if constexpr (sizeof(T) == 4) {
+            const f2 uh = mul2(mk2(0.5f, 0.5f), add2(mk2(ux, uy), mk2(utx, uty)));
+            uhx = uh.x;
+            uhy = uh.y;
+        } else {
+            uhx = T(0.5) * (ux + utx);
+            uhy = T(0.5) * (uy + uty);
+        }
         T sig = T(0), vx = T(0), vy = T(0);
         while (sp < se && a.src[sp].r < r) ++sp;
         for (int q = sp; q < se && a.src[q].r == r; ++q) {
@@ -485,8 +493,16 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         if (r >= 5 && r <= nrows - 6 && (cb & 32u)) {
             const auto FX = fX(r);
             T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
-            T fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
-            T fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
+            T fqx, fqy;
+            if constexpr (sizeof(T) == 4) {
+                const f2 fq = add2(sub2(mk2(FX[1][c - 1], FX[2][c - 1]), mk2(FX[1][c], FX[2][c])),
+                                   sub2(mk2(fyPrev[1], fyPrev[2]), mk2(fyCur[1], fyCur[2])));
+                fqx = fq.x;
+                fqy = fq.y;
+            } else {
+                fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
+                fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
+            }
             if (a.corr && gx0 + c < a.g.nx + 2 * PAD) {
                 // learned sub-grid corrections of the net flux sums
                 const size_t gk = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
@@ -500,8 +516,15 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             const double clip = neg ? -(double)hn : 0.0;
             hn = neg ? T(0) : hn;
             const bool pos = hn > eps;
-            const T qxn = pos ? C[5][c] + dth * fqx : T(0);
-            const T qyn = pos ? C[6][c] + dth * fqy : T(0);
+            T qxn, qyn;
+            if constexpr (sizeof(T) == 4) {
+                const f2 qn = fma2(mk2(dth, dth), mk2(fqx, fqy), mk2(C[5][c], C[6][c]));
+                qxn = pos ? qn.x : T(0);
+                qyn = pos ? qn.y : T(0);
+            } else {
+                qxn = pos ? C[5][c] + dth * fqx : T(0);
+                qyn = pos ? C[6][c] + dth * fqy : T(0);
+            }
             const T b = C[7][c];
             const bool wetn = is_wet(hn, b, eps);
             T uxn, uyn;

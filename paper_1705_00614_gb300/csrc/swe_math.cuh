@@ -58,14 +58,62 @@ __host__ __device__ inline void phys_derive(Phys<T>& P) {
     P.ih = T(1) / P.h;
 }
 
+// Packed FP32 pairs: on sm_100 and later one add / mul / fma instruction
+// works on two FP32 lanes of a 64-bit register pair.  The FP32 instantiation
+// uses them for the x and y components of its vectors (velocities,
+// accelerations, momenta, pairs of faces), which halves the issue slots of
+// that arithmetic.  Each lane rounds like the scalar FP32 operation of the
+// fast-math build (round to nearest, denormals flushed to zero); an explicit
+// mul2 is never contracted with a following add.
+struct f2 {
+    float x, y;
+};
+__device__ __forceinline__ f2 mk2(float x, float y) { return f2{x, y}; }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+    f2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "add.rn.ftz.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+    f2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "sub.rn.ftz.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+__device__ __forceinline__ f2 mul2(f2 a, f2 b) {
+    f2 r;
+    asm("{\n\t.reg .b64 pa, pb, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mul.rn.ftz.f32x2 pr, pa, pb;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+}
+// a * b + c
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("{\n\t.reg .b64 pa, pb, pc, pr;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+        "mov.b64 pc, {%6, %7};\n\tfma.rn.ftz.f32x2 pr, pa, pb, pc;\n\tmov.b64 {%0, %1}, pr;\n\t}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return r;
+}
+__device__ __forceinline__ f2 max02(f2 a) { return f2{fmaxf(0.f, a.x), fmaxf(0.f, a.y)}; }
+__device__ __forceinline__ f2 sel2(bool c, f2 a) { return f2{c ? a.x : 0.f, c ? a.y : 0.f}; }
+
 // q = a / d and r = b / d; FP32 shares one reciprocal, FP64 divides (the
 // oracle's rounding)
 template <class T>
 __device__ __forceinline__ void div2(T a, T b, T d, T& q, T& r) {
     if constexpr (sizeof(T) == 4) {
         const T id = T(1) / d;
-        q = a * id;
-        r = b * id;
+        const f2 v = mul2(mk2(a, b), mk2(id, id));
+        q = v.x;
+        r = v.y;
     } else {
         q = a / d;
         r = b / d;
@@ -88,6 +136,18 @@ __device__ __forceinline__ void div2_if(bool cond, T a, T b, T d, T& q, T& r) {
     }
 }
 
+
+// (u + s a) / d for the two components of a vector (the implicit-friction
+// velocity updates of the predictor and the corrector)
+template <class T>
+__device__ __forceinline__ void lin_div2(T ux, T uy, T s, T ax, T ay, T d, T& qx, T& qy) {
+    if constexpr (sizeof(T) == 4) {
+        const f2 v = fma2(mk2(s, s), mk2(ax, ay), mk2(ux, uy));
+        div2(v.x, v.y, d, qx, qy);
+    } else {
+        div2(ux + s * ax, uy + s * ay, d, qx, qy);
+    }
+}
 
 // Multiplications whose products must cancel exactly (h_R^2 - h_L^2 with
 // h_R == h_L at rest) are kept out of FMA contraction.
@@ -146,6 +206,48 @@ struct Nb {
 template <class T>
 __device__ __forceinline__ void accel(const Phys<T>& P, T hs, T b, T ux, T uy, const Nb<T>& W,
                                       const Nb<T>& E, const Nb<T>& S, const Nb<T>& N, T& ax, T& ay) {
+    if constexpr (sizeof(T) == 4) {
+        // The same terms on (x, y) pairs.  Faces W and S (the cell on their
+        // right / upper side) and faces E and N (the cell on their left /
+        // lower side) are each evaluated as one pair of face_delta.
+        const f2 bsm = mk2(fmaxf(W.b, b), fmaxf(S.b, b));
+        const f2 bsp = mk2(fmaxf(b, E.b), fmaxf(b, N.b));
+        const f2 self = mk2(hs, hs), bb = mk2(b, b);
+        const f2 hlm = max02(add2(mk2(W.hs, S.hs), sub2(mk2(W.b, S.b), bsm)));
+        const f2 hrm = max02(add2(self, sub2(bb, bsm)));
+        const f2 hlp = max02(add2(self, sub2(bb, bsp)));
+        const f2 hrp = max02(add2(mk2(E.hs, N.hs), sub2(mk2(E.b, N.b), bsp)));
+        // h_R^2 - h_L^2 as (h_R - h_L)(h_R + h_L): exactly zero when
+        // h_R == h_L (still water) even where the assembler fuses the
+        // product into a following add (a difference of two rounded
+        // squares would then keep one square's rounding error)
+        f2 dm = mul2(sub2(hrm, hlm), add2(hrm, hlm));
+        f2 dp = mul2(sub2(hrp, hlp), add2(hrp, hlp));
+        dm.x = bsm.x >= T(WALL_TEST) ? T(0) : dm.x;
+        dm.y = bsm.y >= T(WALL_TEST) ? T(0) : dm.y;
+        dp.x = bsp.x >= T(WALL_TEST) ? T(0) : dp.x;
+        dp.y = bsp.y >= T(WALL_TEST) ? T(0) : dp.y;
+        const T ih = T(1) / hs;
+        const T coef = P.gq * ih;
+        const f2 u = mk2(ux, uy);
+        // viscosity: no stress from non-wet neighbours
+        f2 l = sel2(W.wet, sub2(mk2(W.ux, W.uy), u));
+        l = add2(l, sel2(E.wet, sub2(mk2(E.ux, E.uy), u)));
+        l = add2(l, sel2(S.wet, sub2(mk2(S.ux, S.uy), u)));
+        l = add2(l, sel2(N.wet, sub2(mk2(N.ux, N.uy), u)));
+        // wind stress
+        const f2 dw = sub2(mk2(P.wx, P.wy), u);
+        const T wm = sqrtf(dw.x * dw.x + dw.y * dw.y);
+        const T cw = P.cara * wm * ih;
+        // a = a^P + a^V + a^C + a^W
+        f2 a = mul2(mk2(coef, coef), add2(dm, dp));
+        a = fma2(mk2(P.cv, P.cv), l, a);
+        a = fma2(mk2(P.f, -P.f), mk2(uy, ux), a);
+        a = fma2(mk2(cw, cw), dw, a);
+        ax = a.x;
+        ay = a.y;
+        return;
+    }
     // pressure -g grad(eta) in the well-balanced face form
     T dxm = face_delta(W.hs, W.b, hs, b);
     T dxp = face_delta(hs, b, E.hs, E.b);
@@ -210,8 +312,10 @@ __device__ __forceinline__ T cell_speed(const Phys<T>& P, T H, T ux, T uy, T ax,
     T upx, upy;
     if constexpr (sizeof(T) == 4) {
         // sgn(a) sqrt(h |a|) as a sign transfer (the same value)
-        upx = fabs(ux + copysignf(sqrtf(P.h * fabsf(ax)), ax));
-        upy = fabs(uy + copysignf(sqrtf(P.h * fabsf(ay)), ay));
+        const f2 ha = mul2(mk2(P.h, P.h), mk2(fabsf(ax), fabsf(ay)));
+        const f2 up = add2(mk2(ux, uy), mk2(copysignf(sqrtf(ha.x), ax), copysignf(sqrtf(ha.y), ay)));
+        upx = fabsf(up.x);
+        upy = fabsf(up.y);
     } else {
         upx = fabs(ux + tsgn(ax) * sqrt(P.h * fabs(ax)));
         upy = fabs(uy + tsgn(ay) * sqrt(P.h * fabs(ay)));
@@ -289,6 +393,19 @@ struct ECell {
 template <class T>
 __device__ __forceinline__ void slopes(const ECell<T>& m, const ECell<T>& c, const ECell<T>& p, T s[5]) {
     bool lim = m.wt && c.wt && p.wt;
+    if constexpr (sizeof(T) == 4) {
+        // differences on pairs: (H~, b) and the velocity pairs
+        const f2 dm0 = sub2(mk2(c.w[0], c.b), mk2(m.w[0], m.b)), dp0 = sub2(mk2(p.w[0], p.b), mk2(c.w[0], c.b));
+        s[0] = lim ? minmod(dm0.x + dm0.y, dp0.x + dp0.y) : T(0);
+#pragma unroll
+        for (int q = 1; q < 5; q += 2) {
+            const f2 dm = sub2(mk2(c.w[q], c.w[q + 1]), mk2(m.w[q], m.w[q + 1]));
+            const f2 dp = sub2(mk2(p.w[q], p.w[q + 1]), mk2(c.w[q], c.w[q + 1]));
+            s[q] = lim ? minmod(dm.x, dp.x) : T(0);
+            s[q + 1] = lim ? minmod(dm.y, dp.y) : T(0);
+        }
+        return;
+    }
     s[0] = lim ? minmod((c.w[0] - m.w[0]) + (c.b - m.b), (p.w[0] - c.w[0]) + (p.b - c.b)) : T(0);
 #pragma unroll
     for (int q = 1; q < 5; ++q) s[q] = lim ? minmod(c.w[q] - m.w[q], p.w[q] - c.w[q]) : T(0);
@@ -303,10 +420,26 @@ __device__ __forceinline__ void face_flux(const Phys<T>& P, const ECell<T>& L, c
                                           const ECell<T>& R, const T sR[5], int nq, T& FH,
                                           T& FQx, T& FQy) {
     T wl[5], wr[5];
+    if constexpr (sizeof(T) == 4) {
+        const f2 hp = mk2(0.5f, 0.5f), hm = mk2(-0.5f, -0.5f);
+        const f2 d0 = fma2(mk2(0.5f, -0.5f), mk2(sL[0], sR[0]), mk2(L.w[0], R.w[0]));
+        wl[0] = d0.x;
+        wr[0] = d0.y;
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-        wl[q] = L.w[q] + T(0.5) * sL[q];
-        wr[q] = R.w[q] - T(0.5) * sR[q];
+        for (int q = 1; q < 5; q += 2) {
+            const f2 l2 = fma2(hp, mk2(sL[q], sL[q + 1]), mk2(L.w[q], L.w[q + 1]));
+            const f2 r2 = fma2(hm, mk2(sR[q], sR[q + 1]), mk2(R.w[q], R.w[q + 1]));
+            wl[q] = l2.x;
+            wl[q + 1] = l2.y;
+            wr[q] = r2.x;
+            wr[q + 1] = r2.y;
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            wl[q] = L.w[q] + T(0.5) * sL[q];
+            wr[q] = R.w[q] - T(0.5) * sR[q];
+        }
     }
     T bs = tmax(L.b, R.b);
     FH = T(0);
@@ -314,14 +447,29 @@ __device__ __forceinline__ void face_flux(const Phys<T>& P, const ECell<T>& L, c
     FQy = T(0);
     if (bs >= T(WALL_TEST)) return;
     // eta~ at the face minus b*: (H~ + half slope) + (b - b*)
-    T hl = tmax(T(0), wl[0] + (L.b - bs)), hr = tmax(T(0), wr[0] + (R.b - bs));
+    T hl, hr;
+    if constexpr (sizeof(T) == 4) {
+        const f2 h2 = max02(add2(mk2(wl[0], wr[0]), sub2(mk2(L.b, R.b), mk2(bs, bs))));
+        hl = h2.x;
+        hr = h2.y;
+    } else {
+        hl = tmax(T(0), wl[0] + (L.b - bs));
+        hr = tmax(T(0), wr[0] + (R.b - bs));
+    }
     T un_l = nq == 1 ? wl[1] : wl[2];
     T un_r = nq == 1 ? wr[1] : wr[2];
     T hs, us;
     riemann(P.g, P.ig, P.eps, hl, un_l, hr, un_r, hs, us);
     FH = hs * us;
-    FQx = FH * (FH >= T(0) ? wl[3] : wr[3]);
-    FQy = FH * (FH >= T(0) ? wl[4] : wr[4]);
+    if constexpr (sizeof(T) == 4) {
+        const bool up = FH >= T(0);
+        const f2 fq = mul2(mk2(FH, FH), mk2(up ? wl[3] : wr[3], up ? wl[4] : wr[4]));
+        FQx = fq.x;
+        FQy = fq.y;
+    } else {
+        FQx = FH * (FH >= T(0) ? wl[3] : wr[3]);
+        FQy = FH * (FH >= T(0) ? wl[4] : wr[4]);
+    }
 }
 
 // Point source of Eqs. 1-3 on the post-Lagrangian state (ts = tau sigma):
@@ -334,8 +482,15 @@ __device__ __forceinline__ void point_source(T H, T sig, T ts, T vx, T vy, T utx
     const T hp = H + ts;
     ht = tmax(T(0), hp);
     const bool keep = sig > T(0) || hp > T(0);
-    qtx = keep ? H * utx + (sig > T(0) ? ts * vx : ts * utx) : T(0);
-    qty = keep ? H * uty + (sig > T(0) ? ts * vy : ts * uty) : T(0);
+    if constexpr (sizeof(T) == 4) {
+        const bool in = sig > T(0);
+        const f2 q = fma2(mk2(ts, ts), mk2(in ? vx : utx, in ? vy : uty), mul2(mk2(H, H), mk2(utx, uty)));
+        qtx = keep ? q.x : T(0);
+        qty = keep ? q.y : T(0);
+    } else {
+        qtx = keep ? H * utx + (sig > T(0) ? ts * vx : ts * utx) : T(0);
+        qty = keep ? H * uty + (sig > T(0) ? ts * vy : ts * uty) : T(0);
+    }
 }
 
 // Rain, evaporation and infiltration (Eq. 1 sigma) on a non-wall cell after
