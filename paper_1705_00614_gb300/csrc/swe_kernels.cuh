@@ -126,6 +126,23 @@ constexpr int NBAR = 4;   // > PREF: one mbarrier per row in flight
 constexpr int PREF = 2;
 static_assert(RB == 1, "the fused kernel streams one row per TMA copy");
 
+// Vector types of the cell-major stage rings: 2 and 4 fields of one cell.
+template <class T>
+struct Vecs;
+template <>
+struct Vecs<float> {
+    using v2 = float2;
+    using v4 = float4;
+};
+struct __align__(16) dvec4 {
+    double x, y, z, w;
+};
+template <>
+struct Vecs<double> {
+    using v2 = double2;
+    using v4 = dvec4;
+};
+
 template <bool ACC>
 struct Lags {
     static constexpr int S1 = ACC ? 0 : 2, S2 = ACC ? 2 : 4, S3 = ACC ? 4 : 6, S5 = ACC ? 5 : 7, S4 = ACC ? 6 : 8,
@@ -136,28 +153,34 @@ template <class T, bool ACC>
 struct FSmem {
     // input rings (rows).  Oldest readers, ACC: H and b S3 (row r-1), Q and
     // n S3 (own row), a S0; without ACC: H and b S3 (r-1), n S3, Q S0.
-    // Later stages take b and n from the Eulerian ring cS.
+    // Later stages take b from the Eulerian ring cA.
     static constexpr int RH = ACC ? 8 : 16, RQ = ACC ? 8 : 4, RB_ = ACC ? 8 : 16, RN = ACC ? 8 : 16,
                          RA = ACC ? 4 : 1;
     static_assert(RH >= PREF + 1 + Lags<ACC>::S3 + 1 && RB_ >= PREF + 1 + Lags<ACC>::S3 + 1, "H/b ring");
     static_assert(RN >= PREF + 1 + Lags<ACC>::S3 && RQ >= PREF + 1 + (ACC ? Lags<ACC>::S3 : 0), "n/Q ring");
     static_assert(!ACC || RA >= PREF + 1, "a ring");
     // stage rings (rows); pU (U at t_n, read by S1 and S3) only without ACC:
-    // with ACC, S3 forms U from the Q ring itself
+    // with ACC, S3 forms U from the Q ring itself.  The stage rings are
+    // cell-major: a row holds WIN cells of 2 or 4 fields each, so one cell's
+    // fields move with one 8- or 16-byte shared-memory access (a warp's
+    // 16-byte accesses to 32 consecutive cells are conflict-free).
     static constexpr int DP = ACC ? 1 : 8, DA = 8, DB = 4, DC = 4, DX = 2, DF = 2, DN = 4;
+    using V2 = typename Vecs<T>::v2;
+    using V4 = typename Vecs<T>::v4;
     T inH[RH][WIN];
     T inQx[RQ][WIN];
     T inQy[RQ][WIN];
     T inB[RB_][WIN];
     T inN[RN][WIN];
     T inA[NACC][RA][WIN];  // a_x, a_y at t_n (ACC only)
-    T pU[2][DP][WIN];      // U at t_n (without ACC)
-    T aU[2][DA][WIN];      // predictor U*
+    V2 pU[DP][WIN];        // U at t_n (without ACC)
+    V2 aU[DA][WIN];        // predictor U*
     T bH[DB][WIN];         // particle depth H*
-    T cS[9][DC][WIN];      // H~, U^x, U^y, U~'x, U~'y, Q~x, Q~y, b, n
-    T sX[4][DX][WIN];      // x slopes of H~, U^x, U~'x, U~'y (an x face needs no U^y slope)
-    T fX[3][DF][WIN];      // x-face fluxes F_H, F_Qx, F_Qy
-    T nS[4][DN][WIN];      // new state H, Ux, Uy with the cell's b
+    V4 cA[DC][WIN];        // post-Lagrangian H~, U^x, U^y and the cell's b
+    V4 cB[DC][WIN];        // post-Lagrangian U~'x, U~'y, Q~x, Q~y
+    V4 sX[DX][WIN];        // x slopes of H~, U^x, U~'x, U~'y (an x face needs no U^y slope)
+    V4 fX[DF][WIN];        // x-face fluxes F_H, F_Qx, F_Qy (w unused)
+    V4 nS[DN][WIN];        // new state H, Ux, Uy with the cell's b
     unsigned long long bar[NBAR];
     double hq[MAX_HYDRO];
     double red[NT / 32];
@@ -167,14 +190,6 @@ struct FSmem {
     int abort;
 };
 
-// One row of a field-major stage ring: row[q] is field q's WIN values.  All
-// rings keep rows WIN values apart, so one slot offset per row serves every
-// field (the field offsets are constants).
-template <class T, int FS>
-struct FRow {
-    T* p;
-    __device__ __forceinline__ T* operator[](int q) const { return p + q * FS; }
-};
 
 template <class T, bool ACC>
 size_t fused_smem_bytes_v() {
@@ -212,6 +227,8 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                                            unsigned& cbase) {
     using LG = Lags<ACC>;
     using S = FSmem<T, ACC>;
+    using V2 = typename Vecs<T>::v2;
+    using V4 = typename Vecs<T>::v4;
     const int tid = threadIdx.x;
     const int c = tid & (WIN - 1);
     const bool groupL = tid < WIN;
@@ -272,13 +289,14 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     auto rB = [&](int r) -> const T* { return s.inB[r & (S::RB_ - 1)]; };
     auto rN = [&](int r) -> const T* { return s.inN[r & (S::RN - 1)]; };
     auto rA = [&](int q, int r) -> const T* { return s.inA[q][r & (S::RA - 1)]; };
-    auto pU = [&](int r) { return FRow<T, S::DP * WIN>{&s.pU[0][r & (S::DP - 1)][0]}; };
-    auto aU = [&](int r) { return FRow<T, S::DA * WIN>{&s.aU[0][r & (S::DA - 1)][0]}; };
+    auto pU = [&](int r) { return s.pU[r & (S::DP - 1)]; };
+    auto aU = [&](int r) { return s.aU[r & (S::DA - 1)]; };
     auto bH = [&](int r) { return s.bH[r & (S::DB - 1)]; };
-    auto cS = [&](int r) { return FRow<T, S::DC * WIN>{&s.cS[0][r & (S::DC - 1)][0]}; };
-    auto sX = [&](int r) { return FRow<T, S::DX * WIN>{&s.sX[0][r & (S::DX - 1)][0]}; };
-    auto fX = [&](int r) { return FRow<T, S::DF * WIN>{&s.fX[0][r & (S::DF - 1)][0]}; };
-    auto nS = [&](int r) { return FRow<T, S::DN * WIN>{&s.nS[0][r & (S::DN - 1)][0]}; };
+    auto cA = [&](int r) { return s.cA[r & (S::DC - 1)]; };
+    auto cB = [&](int r) { return s.cB[r & (S::DC - 1)]; };
+    auto sX = [&](int r) { return s.sX[r & (S::DX - 1)]; };
+    auto fX = [&](int r) { return s.fX[r & (S::DF - 1)]; };
+    auto nS = [&](int r) { return s.nS[r & (S::DN - 1)]; };
 
     // the stages' column ranges for this thread: bit i (1..5) set when
     // c is in [i, WIN-1-i], bit 6 when c is in [4, WIN-6]
@@ -308,11 +326,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         const bool wet = is_wet(H, rB(k)[c], eps);
         T ux, uy;
         div2_if(wet, rQx(k)[c], rQy(k)[c], H, ux, uy);
-        if (!ACC) {
-            const auto U = pU(k);
-            U[0][c] = ux;
-            U[1][c] = uy;
-        }
+        if (!ACC) pU(k)[c] = V2{ux, uy};
         if (ACC) {
             // FP32: every lane evaluates (a dry cell's stored accelerations
             // are 0) and keeps the value where the cell is wet; FP64 only
@@ -323,9 +337,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                 const T den = T(1) + th * friction(P, H, rN(k)[c], ux, uy);
                 lin_div2(ux, uy, th, rA(0, k)[c], rA(1, k)[c], den, usx, usy);
             }
-            const auto A = aU(k);
-            A[0][c] = wet ? usx : T(0);
-            A[1][c] = wet ? usy : T(0);
+            aU(k)[c] = V2{wet ? usx : T(0), wet ? usy : T(0)};
         }
     };
     // S1: forces at t_n and predictor velocity U* (without ACC)
@@ -333,24 +345,21 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         if (!(r >= 1 && r <= nrows - 2 && (cb & 2u))) return;
         const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
         const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
-        const auto U0 = pU(r);
-        const auto Um = pU(r - 1);
-        const auto Up = pU(r + 1);
+        const V2 *U0 = pU(r), *Um = pU(r - 1), *Up = pU(r + 1);
         const T H = H0[c], b = b0[c];
         T usx = T(0), usy = T(0);
         if (is_wet(H, b, eps)) {
-            Nb<T> W{H0[c - 1], b0[c - 1], U0[0][c - 1], U0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
-            Nb<T> E{H0[c + 1], b0[c + 1], U0[0][c + 1], U0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
-            Nb<T> S{Hm[c], bm[c], Um[0][c], Um[1][c], is_wet(Hm[c], bm[c], eps)};
-            Nb<T> N{Hp[c], bp[c], Up[0][c], Up[1][c], is_wet(Hp[c], bp[c], eps)};
+            const V2 uw = U0[c - 1], ue = U0[c + 1], us = Um[c], un = Up[c], u0 = U0[c];
+            Nb<T> W{H0[c - 1], b0[c - 1], uw.x, uw.y, is_wet(H0[c - 1], b0[c - 1], eps)};
+            Nb<T> E{H0[c + 1], b0[c + 1], ue.x, ue.y, is_wet(H0[c + 1], b0[c + 1], eps)};
+            Nb<T> S{Hm[c], bm[c], us.x, us.y, is_wet(Hm[c], bm[c], eps)};
+            Nb<T> N{Hp[c], bp[c], un.x, un.y, is_wet(Hp[c], bp[c], eps)};
             T ax, ay, phi;
-            forces(P, H, b, rN(r)[c], U0[0][c], U0[1][c], W, E, S, N, ax, ay, phi);
+            forces(P, H, b, rN(r)[c], u0.x, u0.y, W, E, S, N, ax, ay, phi);
             const T den = T(1) + th * phi;
-            lin_div2(U0[0][c], U0[1][c], th, ax, ay, den, usx, usy);
+            lin_div2(u0.x, u0.y, th, ax, ay, den, usx, usy);
         }
-        const auto A = aU(r);
-        A[0][c] = usx;
-        A[1][c] = usy;
+        aU(r)[c] = V2{usx, usy};
     };
     // S2: particle area change and H*
     auto stage2 = [&](int r) {
@@ -361,14 +370,22 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         // only where wet
         T hw = H;
         if (sizeof(T) == 4 || wet) {
-            const auto A0 = aU(r);
-            const T u = A0[0][c], uW = A0[0][c - 1], uE = A0[0][c + 1];
-            const T v = A0[1][c], vS = aU(r - 1)[1][c], vN = aU(r + 1)[1][c];
-            const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
-            const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
+            const V2* A0 = aU(r);
+            const V2 a0 = A0[c];
+            const T u = a0.x, uW = A0[c - 1].x, uE = A0[c + 1].x;
+            const T v = a0.y, vS = aU(r - 1)[c].y, vN = aU(r + 1)[c].y;
             T D;
-            if constexpr (sizeof(T) == 4) D = ((fxp - fxm) + (fyp - fym)) * P.ih;
-            else D = ((fxp - fxm) + (fyp - fym)) / P.h;
+            if constexpr (sizeof(T) == 4) {
+                // face means of the W/S and E/N faces as (x, y) pairs
+                const f2 fm = mul2(mk2(0.5f, 0.5f), add2(mk2(uW, vS), mk2(u, v)));
+                const f2 fp = mul2(mk2(0.5f, 0.5f), add2(mk2(u, v), mk2(uE, vN)));
+                const f2 d = sub2(fp, fm);
+                D = (d.x + d.y) * P.ih;
+            } else {
+                const T fxm = T(0.5) * (uW + u), fxp = T(0.5) * (u + uE);
+                const T fym = T(0.5) * (vS + v), fyp = T(0.5) * (v + vN);
+                D = ((fxp - fxm) + (fyp - fym)) / P.h;
+            }
             hw = H / tmax(T(0.5), T(1) + th * D);
         }
         bH(r)[c] = wet ? hw : H;
@@ -379,27 +396,27 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         const T *H0 = rH(r), *Hm = rH(r - 1), *Hp = rH(r + 1);
         const T *b0 = rB(r), *bm = rB(r - 1), *bp = rB(r + 1);
         const T *B0 = bH(r), *Bm = bH(r - 1), *Bp = bH(r + 1);
-        const auto A0 = aU(r);
-        const auto Am = aU(r - 1);
-        const auto Ap = aU(r + 1);
+        const V2 *A0 = aU(r), *Am = aU(r - 1), *Ap = aU(r + 1);
         const T H = H0[c], b = b0[c];
         const bool wet = is_wet(H, b, eps);
         T ux, uy;
         if (ACC) {
             div2_if(wet, rQx(r)[c], rQy(r)[c], H, ux, uy);
         } else {
-            ux = pU(r)[0][c];
-            uy = pU(r)[1][c];
+            const V2 u0 = pU(r)[c];
+            ux = u0.x;
+            uy = u0.y;
         }
         const T nm = rN(r)[c];
         T utx = T(0), uty = T(0);
         if (wet) {
-            Nb<T> W{B0[c - 1], b0[c - 1], A0[0][c - 1], A0[1][c - 1], is_wet(H0[c - 1], b0[c - 1], eps)};
-            Nb<T> E{B0[c + 1], b0[c + 1], A0[0][c + 1], A0[1][c + 1], is_wet(H0[c + 1], b0[c + 1], eps)};
-            Nb<T> S{Bm[c], bm[c], Am[0][c], Am[1][c], is_wet(Hm[c], bm[c], eps)};
-            Nb<T> N{Bp[c], bp[c], Ap[0][c], Ap[1][c], is_wet(Hp[c], bp[c], eps)};
+            const V2 aw = A0[c - 1], ae = A0[c + 1], as = Am[c], an = Ap[c], a0 = A0[c];
+            Nb<T> W{B0[c - 1], b0[c - 1], aw.x, aw.y, is_wet(H0[c - 1], b0[c - 1], eps)};
+            Nb<T> E{B0[c + 1], b0[c + 1], ae.x, ae.y, is_wet(H0[c + 1], b0[c + 1], eps)};
+            Nb<T> S{Bm[c], bm[c], as.x, as.y, is_wet(Hm[c], bm[c], eps)};
+            Nb<T> N{Bp[c], bp[c], an.x, an.y, is_wet(Hp[c], bp[c], eps)};
             T ax, ay, phi;
-            forces(P, B0[c], b, nm, A0[0][c], A0[1][c], W, E, S, N, ax, ay, phi);
+            forces(P, B0[c], b, nm, a0.x, a0.y, W, E, S, N, ax, ay, phi);
             const T den = T(1) + tauT * phi;
             lin_div2(ux, uy, tauT, ax, ay, den, utx, uty);
         }
@@ -426,31 +443,23 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         point_source(H, sig, ts, vx, vy, utx, uty, ht, qtx, qty);
         if (P.dist && b < T(WALL_TEST)) distributed_sources(P, tauT, H + ts, utx, uty, ht, qtx, qty);
         const bool wt = is_wet(ht, b, eps);
-        const auto C = cS(r);
-        C[0][c] = ht;
-        C[1][c] = uhx;
-        C[2][c] = uhy;
         T upx, upy;
         div2_if(wt, qtx, qty, ht, upx, upy);
-        C[3][c] = upx;
-        C[4][c] = upy;
-        C[5][c] = qtx;
-        C[6][c] = qty;
-        C[7][c] = b;
-        C[8][c] = nm;
+        cA(r)[c] = V4{ht, uhx, uhy, b};
+        cB(r)[c] = V4{upx, upy, qtx, qty};
         if (has_src && out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
     };
     auto ecell = [&](int rr, int col) {
         ECell<T> e;
-        const auto C = cS(rr);
-        const T bb = C[7][col];
-        e.w[0] = C[0][col];
-        e.w[1] = C[1][col];
-        e.w[2] = C[2][col];
-        e.w[3] = C[3][col];
-        e.w[4] = C[4][col];
-        e.b = bb;
-        e.wt = is_wet(e.w[0], bb, eps);
+        const V4 ca = cA(rr)[col];
+        const V2 cb2 = reinterpret_cast<const V2*>(&cB(rr)[col])[0];
+        e.w[0] = ca.x;
+        e.w[1] = ca.y;
+        e.w[2] = ca.z;
+        e.w[3] = cb2.x;
+        e.w[4] = cb2.y;
+        e.b = ca.w;
+        e.wt = is_wet(e.w[0], e.b, eps);
         return e;
     };
     // S5: MUSCL slopes along x of row r (each cell once; the face fluxes
@@ -459,11 +468,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         if (!(r >= 5 && r <= nrows - 6 && (cb & 16u))) return;
         T sx[5];
         slopes(ecell(r, c - 1), ecell(r, c), ecell(r, c + 1), sx);
-        const auto X = sX(r);
-        X[0][c] = sx[0];
-        X[1][c] = sx[1];
-        X[2][c] = sx[3];
-        X[3][c] = sx[4];
+        sX(r)[c] = V4{sx[0], sx[1], sx[3], sx[4]};
     };
     // S4: MUSCL slopes along y and face fluxes of row r (x faces, and the y
     // face below the row)
@@ -477,31 +482,28 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         for (int q = 0; q < 5; ++q) syPrev[q] = syc[q];
         if (r >= 5 && r <= nrows - 6 && (cb & 64u)) {
             const ECell<T> x1 = ecell(r, c + 1);
-            const auto X = sX(r);
-            const T sL[5] = {X[0][c], X[1][c], T(0), X[2][c], X[3][c]};
-            const T sR[5] = {X[0][c + 1], X[1][c + 1], T(0), X[2][c + 1], X[3][c + 1]};
+            const V4 xl = sX(r)[c], xr = sX(r)[c + 1];
+            const T sL[5] = {xl.x, xl.y, T(0), xl.z, xl.w};
+            const T sR[5] = {xr.x, xr.y, T(0), xr.z, xr.w};
             T FH, FQx, FQy;
             face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
-            const auto F = fX(r);
-            F[0][c] = FH;
-            F[1][c] = FQx;
-            F[2][c] = FQy;
+            fX(r)[c] = V4{FH, FQx, FQy, T(0)};
         }
     };
     // S6: final update of row r (K8)
     auto stage6 = [&](int r) {
         if (r >= 5 && r <= nrows - 6 && (cb & 32u)) {
-            const auto FX = fX(r);
-            T fh = (FX[0][c - 1] - FX[0][c]) + (fyPrev[0] - fyCur[0]);
+            const V4 fw = fX(r)[c - 1], fe = fX(r)[c];
+            T fh = (fw.x - fe.x) + (fyPrev[0] - fyCur[0]);
             T fqx, fqy;
             if constexpr (sizeof(T) == 4) {
-                const f2 fq = add2(sub2(mk2(FX[1][c - 1], FX[2][c - 1]), mk2(FX[1][c], FX[2][c])),
+                const f2 fq = add2(sub2(mk2(fw.y, fw.z), mk2(fe.y, fe.z)),
                                    sub2(mk2(fyPrev[1], fyPrev[2]), mk2(fyCur[1], fyCur[2])));
                 fqx = fq.x;
                 fqy = fq.y;
             } else {
-                fqx = (FX[1][c - 1] - FX[1][c]) + (fyPrev[1] - fyCur[1]);
-                fqy = (FX[2][c - 1] - FX[2][c]) + (fyPrev[2] - fyCur[2]);
+                fqx = (fw.y - fe.y) + (fyPrev[1] - fyCur[1]);
+                fqy = (fw.z - fe.z) + (fyPrev[2] - fyCur[2]);
             }
             if (a.corr && gx0 + c < a.g.nx + 2 * PAD) {
                 // learned sub-grid corrections of the net flux sums
@@ -510,37 +512,34 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                 fqx += a.corr[a.corr_plane + gk];
                 fqy += a.corr[2 * a.corr_plane + gk];
             }
-            const auto C = cS(r);
-            T hn = C[0][c] + dth * fh;
+            const V4 ca = cA(r)[c], cb4 = cB(r)[c];
+            T hn = ca.x + dth * fh;
             const bool neg = hn < T(0);
-            const double clip = neg ? -(double)hn : 0.0;
+            const T hneg = hn;
             hn = neg ? T(0) : hn;
             const bool pos = hn > eps;
             T qxn, qyn;
             if constexpr (sizeof(T) == 4) {
-                const f2 qn = fma2(mk2(dth, dth), mk2(fqx, fqy), mk2(C[5][c], C[6][c]));
+                const f2 qn = fma2(mk2(dth, dth), mk2(fqx, fqy), mk2(cb4.z, cb4.w));
                 qxn = pos ? qn.x : T(0);
                 qyn = pos ? qn.y : T(0);
             } else {
-                qxn = pos ? C[5][c] + dth * fqx : T(0);
-                qyn = pos ? C[6][c] + dth * fqy : T(0);
+                qxn = pos ? cb4.z + dth * fqx : T(0);
+                qyn = pos ? cb4.w + dth * fqy : T(0);
             }
-            const T b = C[7][c];
+            const T b = ca.w;
             const bool wetn = is_wet(hn, b, eps);
             T uxn, uyn;
             div2_if(wetn, qxn, qyn, hn, uxn, uyn);
-            const auto Nw = nS(r);
-            Nw[0][c] = hn;
-            Nw[1][c] = uxn;
-            Nw[2][c] = uyn;
-            Nw[3][c] = b;
+            nS(r)[c] = V4{hn, uxn, uyn, b};
             if (out_col && r >= HALO && r < HALO + sh) {
                 const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
                 outH[gi] = hn;
                 outQx[gi] = qxn;
                 outQy[gi] = qyn;
                 acc_mass += (double)hn;
-                acc_clip += clip;
+                // a clipped negative depth is rare: no FP64 work otherwise
+                if (neg) acc_clip += -(double)hneg;
                 acc_wet += wetn ? 1 : 0;
                 if (a.act) {
                     // stamp the blocks of the new state that hold a wet cell
@@ -562,17 +561,17 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
     // carries b, so no input row older than S3's is needed.
     auto stage7 = [&](int r) {
         if (!(r >= HALO && r < HALO + sh && out_col)) return;
-        const auto N0 = nS(r);
-        const auto Nm = nS(r - 1);
-        const auto Np = nS(r + 1);
-        const T H = N0[0][c], b = N0[3][c];
+        const V4* N0 = nS(r);
+        const V4 n0 = N0[c];
+        const T H = n0.x, b = n0.w;
         T ax = T(0), ay = T(0);
         if (is_wet(H, b, eps)) {
-            const T ux = N0[1][c], uy = N0[2][c];
-            Nb<T> W{N0[0][c - 1], N0[3][c - 1], N0[1][c - 1], N0[2][c - 1], is_wet(N0[0][c - 1], N0[3][c - 1], eps)};
-            Nb<T> E{N0[0][c + 1], N0[3][c + 1], N0[1][c + 1], N0[2][c + 1], is_wet(N0[0][c + 1], N0[3][c + 1], eps)};
-            Nb<T> S{Nm[0][c], Nm[3][c], Nm[1][c], Nm[2][c], is_wet(Nm[0][c], Nm[3][c], eps)};
-            Nb<T> N{Np[0][c], Np[3][c], Np[1][c], Np[2][c], is_wet(Np[0][c], Np[3][c], eps)};
+            const T ux = n0.y, uy = n0.z;
+            const V4 nw = N0[c - 1], ne = N0[c + 1], ns = nS(r - 1)[c], nn = nS(r + 1)[c];
+            Nb<T> W{nw.x, nw.w, nw.y, nw.z, is_wet(nw.x, nw.w, eps)};
+            Nb<T> E{ne.x, ne.w, ne.y, ne.z, is_wet(ne.x, ne.w, eps)};
+            Nb<T> S{ns.x, ns.w, ns.y, ns.z, is_wet(ns.x, ns.w, eps)};
+            Nb<T> N{nn.x, nn.w, nn.y, nn.z, is_wet(nn.x, nn.w, eps)};
             accel(P, H, b, ux, uy, W, E, S, N, ax, ay);
             const T v = cell_speed(P, H, ux, uy, ax, ay);
             const bool fin = v <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX);
