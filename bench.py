@@ -140,6 +140,14 @@ def run_ensemble(args, torch, swe, stream, rank, world):
     sols = [swe.Solver.from_problem(p, args.precision, stream=stream.cuda_stream) for p in probs]
     batch = swe.Batch(sols)
     seg = batch.autotune(2)
+    # gate toggles inside the timed steps: each gate flips at its seeded step
+    # of the run (steps are counted from the batch's creation; the timed
+    # region starts after the untimed pass and the warm-up steps below)
+    base = args.steps + args.warmup
+    ev = [(k, int(i), int(j), base + int(st), 1 - int(c0)) for k, g in enumerate(gates)
+          for i, j, c0, st in zip(g.ix, g.iy, g.closed0, g.toggle_step) if st < args.steps]
+    if ev:
+        batch.set_gate_events(*map(np.array, zip(*ev)))
     batch.step(args.steps, report=False)
     for _ in range(args.warmup):
         batch.step(1, report=False)
@@ -172,6 +180,7 @@ def run_ensemble(args, torch, swe, stream, rank, world):
                            "cells": int(job_cells),
                            "sizes": [min(p.params.nx for p in probs), max(p.params.nx for p in probs)],
                            "seg_h_autotuned": seg, "gates": int(sum(len(g.ix) for g in gates)),
+                           "gate_toggles_in_timed_steps": len(ev),
                            "wet_cells_end": int(sum(i["wet_cells"] for i in infos)),
                            "l2": "inputs larger than L2",
                            "parallelism": f"scenarios sharded over {world} ranks" if world > 1 else "single GPU"},
@@ -283,8 +292,9 @@ def run_closure(args, torch, swe, stream, rank, world):
     rng = np.random.default_rng(0)
     t0 = time.perf_counter()
     win = args.closure_window
-    norm = CL.estimate_norm(torch, [scenario(train_seeds[0])], 10 * win, tau_c, rng, 128, bed=args.closure_bed,
-                            horizon=win)
+    # input and target statistics from the first training seeds' runs
+    norm = CL.estimate_norm(torch, [scenario(sd) for sd in train_seeds[:4]], 40 * win, tau_c, rng, 128,
+                            bed=args.closure_bed, horizon=win)
     X, T = [], []
     for sd in train_seeds:
         x, t = CL.collect(torch, scenario(sd), args.closure_collect, tau_c, norm.inp(), norm.out(),
@@ -309,8 +319,11 @@ def run_closure(args, torch, swe, stream, rank, world):
     del X, T
     t_train = time.perf_counter() - t0
 
-    alphas = [float(a) for a in args.closure_alpha.split(",")]
-    names = ["plain"] + [f"closed_a{a:g}" for a in alphas]
+    # candidate scales: "a" scales every correction by a; "a/m" keeps only
+    # the momentum corrections (scaled by a), the depth correction off
+    specs = [(float(x.split("/")[0]), 0.0 if x.endswith("/m") else None) for x in args.closure_alpha.split(",")]
+    alphas = [a for a, _ in specs]
+    names = ["plain"] + [f"closed_a{a:g}" + ("_momentum_only" if ah == 0.0 else "") for a, ah in specs]
     ms_fine, ms_closed = [], []
 
     def run_seeds(seeds):
@@ -327,10 +340,10 @@ def run_closure(args, torch, swe, stream, rank, world):
             alive = [True] * len(alphas)
             try:
                 plain.restrict_from(fine)
-                for c, net, a in zip(closed, nets, alphas):
+                for c, net, (a, ah) in zip(closed, nets, specs):
                     net.set_params(params)
                     c.restrict_from(fine)
-                    c.attach_closure(net, CL.shrink(norm, a).all())
+                    c.attach_closure(net, CL.shrink(norm, a, ah).all())
                 done = 0
                 for h in horizons:
                     k = h - done
@@ -672,7 +685,8 @@ def main():
     ap.add_argument("--closure-iters", type=int, default=3000, help="closure workload: Adam steps")
     ap.add_argument("--closure-steps", type=int, default=5000, help="closure workload: longest horizon")
     ap.add_argument("--closure-alpha", default="1,0.5,0.25,0.1,0.05",
-                    help="closure workload: comma-separated correction scales; the validation seeds pick one")
+                    help="closure workload: comma-separated correction scales (a suffix /m keeps the momentum "
+                         "corrections only); the validation seeds pick one")
     ap.add_argument("--closure-bed", default="volume", choices=["mean", "volume"],
                     help="closure workload: coarse bed from 4x4 means, or volume-matched in partly wet cells")
     ap.add_argument("--closure-noise", type=float, default=0.0,

@@ -354,8 +354,9 @@ SWE_API int swe_closure_features(swe_ctx* ctx, const float* norm_in, void* x);
  * sd[3] (host).  Synchronises. */
 SWE_API int swe_closure_targets(swe_ctx* pred, swe_ctx* ref, const float* norm_out, float* t);
 /* Attach (cnn != NULL) or detach a trained network of batch shape
- * (1, ny, nx) to a fused context, with norm = input mu[5], sd[5], output
- * mu[3], sd[3] (host).  The context borrows the network. */
+ * (1, ny, nx) to a fused context, with norm = input mu[5], sd[5] (sd > 0),
+ * output mu[3], sd[3] (sd >= 0; a channel with mu = sd = 0 adds no
+ * correction) (host).  The context borrows the network. */
 SWE_API int swe_closure_attach(swe_ctx* ctx, swe_cnn* cnn, const float* norm);
 /* Closed coarse steps: per step, the network predicts corrections of the net
  * face-flux sums from the state at t_n, their depth part is centred over

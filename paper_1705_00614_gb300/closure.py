@@ -279,10 +279,13 @@ def train(torch, X, T, iters, batch, lr, seed, stream=None, log_every=0, init=No
         return net.get_params(), hist
 
 
-def shrink(norm: Norm, alpha: float) -> Norm:
+def shrink(norm: Norm, alpha: float, alpha_h=None) -> Norm:
     """Scale the network's corrections by alpha (0 < alpha <= 1): a shrinkage
-    that trades the one-step gain for robustness over long closed runs."""
-    return Norm(norm.mu_in, norm.sd_in, norm.mu_out * alpha, norm.sd_out * alpha)
+    that trades the one-step gain for robustness over long closed runs.
+    alpha_h, if given, scales the depth (mass-flux) correction instead of
+    alpha (0: momentum corrections only)."""
+    f = np.array([alpha if alpha_h is None else alpha_h, alpha, alpha])
+    return Norm(norm.mu_in, norm.sd_in, norm.mu_out * f, norm.sd_out * f)
 
 
 def evaluate(torch, fine_prob, params, norm, nsteps, tau_c, stream=None, bed="mean"):

@@ -1534,8 +1534,10 @@ int swe_closure_attach(swe_ctx* c, swe_cnn* cnn, const float* norm) {
     if (n != 1 || h != c->p.ny || w != c->p.nx) return fail(SWE_ERR_ARG, "the network's batch shape must be (1, ny, nx)");
     for (int k = 0; k < 5; ++k)
         if (!(norm[5 + k] > 0.f)) return fail(SWE_ERR_ARG, "normalisation");
+    // an output spread of 0 (with mean 0) switches that correction off
     for (int k = 0; k < 3; ++k)
-        if (!(norm[13 + k] > 0.f)) return fail(SWE_ERR_ARG, "normalisation");
+        if (!(norm[13 + k] >= 0.f) || !std::isfinite(norm[13 + k]) || !std::isfinite(norm[10 + k]))
+            return fail(SWE_ERR_ARG, "normalisation");
     int rc = ensure_norm(c);
     if (rc) return rc;
     if (!c->d_feat && cudaMalloc(&c->d_feat, (size_t)c->p.nx * c->p.ny * 16 * 2) != cudaSuccess)

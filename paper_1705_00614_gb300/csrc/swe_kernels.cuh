@@ -176,11 +176,13 @@ struct FSmem {
     V2 pU[DP][WIN];        // U at t_n (without ACC)
     V2 aU[DA][WIN];        // predictor U*
     T bH[DB][WIN];         // particle depth H*
-    V4 cA[DC][WIN];        // post-Lagrangian H~, U^x, U^y and the cell's b
+    // (x, y) pairs sit in the first or second half of a 4-vector, so they
+    // load into the aligned register pairs the packed FP32 arithmetic uses
+    V4 cA[DC][WIN];        // post-Lagrangian U^x, U^y, H~ and the cell's b
     V4 cB[DC][WIN];        // post-Lagrangian U~'x, U~'y, Q~x, Q~y
     V4 sX[DX][WIN];        // x slopes of H~, U^x, U~'x, U~'y (an x face needs no U^y slope)
-    V4 fX[DF][WIN];        // x-face fluxes F_H, F_Qx, F_Qy (w unused)
-    V4 nS[DN][WIN];        // new state H, Ux, Uy with the cell's b
+    V4 fX[DF][WIN];        // x-face fluxes F_Qx, F_Qy, F_H (w unused)
+    V4 nS[DN][WIN];        // new state Ux, Uy, H with the cell's b
     unsigned long long bar[NBAR];
     double hq[MAX_HYDRO];
     double red[NT / 32];
@@ -445,7 +447,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         const bool wt = is_wet(ht, b, eps);
         T upx, upy;
         div2_if(wt, qtx, qty, ht, upx, upy);
-        cA(r)[c] = V4{ht, uhx, uhy, b};
+        cA(r)[c] = V4{uhx, uhy, ht, b};
         cB(r)[c] = V4{upx, upy, qtx, qty};
         if (has_src && out_col && r >= HALO && r < HALO + sh) acc_src += (double)ht - (double)H;
     };
@@ -453,9 +455,9 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         ECell<T> e;
         const V4 ca = cA(rr)[col];
         const V2 cb2 = reinterpret_cast<const V2*>(&cB(rr)[col])[0];
-        e.w[0] = ca.x;
-        e.w[1] = ca.y;
-        e.w[2] = ca.z;
+        e.w[0] = ca.z;
+        e.w[1] = ca.x;
+        e.w[2] = ca.y;
         e.w[3] = cb2.x;
         e.w[4] = cb2.y;
         e.b = ca.w;
@@ -487,23 +489,23 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             const T sR[5] = {xr.x, xr.y, T(0), xr.z, xr.w};
             T FH, FQx, FQy;
             face_flux(P, e0, sL, x1, sR, 1, FH, FQx, FQy);
-            fX(r)[c] = V4{FH, FQx, FQy, T(0)};
+            fX(r)[c] = V4{FQx, FQy, FH, T(0)};
         }
     };
     // S6: final update of row r (K8)
     auto stage6 = [&](int r) {
         if (r >= 5 && r <= nrows - 6 && (cb & 32u)) {
             const V4 fw = fX(r)[c - 1], fe = fX(r)[c];
-            T fh = (fw.x - fe.x) + (fyPrev[0] - fyCur[0]);
+            T fh = (fw.z - fe.z) + (fyPrev[0] - fyCur[0]);
             T fqx, fqy;
             if constexpr (sizeof(T) == 4) {
-                const f2 fq = add2(sub2(mk2(fw.y, fw.z), mk2(fe.y, fe.z)),
+                const f2 fq = add2(sub2(mk2(fw.x, fw.y), mk2(fe.x, fe.y)),
                                    sub2(mk2(fyPrev[1], fyPrev[2]), mk2(fyCur[1], fyCur[2])));
                 fqx = fq.x;
                 fqy = fq.y;
             } else {
-                fqx = (fw.y - fe.y) + (fyPrev[1] - fyCur[1]);
-                fqy = (fw.z - fe.z) + (fyPrev[2] - fyCur[2]);
+                fqx = (fw.x - fe.x) + (fyPrev[1] - fyCur[1]);
+                fqy = (fw.y - fe.y) + (fyPrev[2] - fyCur[2]);
             }
             if (a.corr && gx0 + c < a.g.nx + 2 * PAD) {
                 // learned sub-grid corrections of the net flux sums
@@ -513,7 +515,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                 fqy += a.corr[2 * a.corr_plane + gk];
             }
             const V4 ca = cA(r)[c], cb4 = cB(r)[c];
-            T hn = ca.x + dth * fh;
+            T hn = ca.z + dth * fh;
             const bool neg = hn < T(0);
             const T hneg = hn;
             hn = neg ? T(0) : hn;
@@ -531,7 +533,7 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
             const bool wetn = is_wet(hn, b, eps);
             T uxn, uyn;
             div2_if(wetn, qxn, qyn, hn, uxn, uyn);
-            nS(r)[c] = V4{hn, uxn, uyn, b};
+            nS(r)[c] = V4{uxn, uyn, hn, b};
             if (out_col && r >= HALO && r < HALO + sh) {
                 const size_t gi = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
                 outH[gi] = hn;
@@ -563,15 +565,15 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
         if (!(r >= HALO && r < HALO + sh && out_col)) return;
         const V4* N0 = nS(r);
         const V4 n0 = N0[c];
-        const T H = n0.x, b = n0.w;
+        const T H = n0.z, b = n0.w;
         T ax = T(0), ay = T(0);
         if (is_wet(H, b, eps)) {
-            const T ux = n0.y, uy = n0.z;
+            const T ux = n0.x, uy = n0.y;
             const V4 nw = N0[c - 1], ne = N0[c + 1], ns = nS(r - 1)[c], nn = nS(r + 1)[c];
-            Nb<T> W{nw.x, nw.w, nw.y, nw.z, is_wet(nw.x, nw.w, eps)};
-            Nb<T> E{ne.x, ne.w, ne.y, ne.z, is_wet(ne.x, ne.w, eps)};
-            Nb<T> S{ns.x, ns.w, ns.y, ns.z, is_wet(ns.x, ns.w, eps)};
-            Nb<T> N{nn.x, nn.w, nn.y, nn.z, is_wet(nn.x, nn.w, eps)};
+            Nb<T> W{nw.z, nw.w, nw.x, nw.y, is_wet(nw.z, nw.w, eps)};
+            Nb<T> E{ne.z, ne.w, ne.x, ne.y, is_wet(ne.z, ne.w, eps)};
+            Nb<T> S{ns.z, ns.w, ns.x, ns.y, is_wet(ns.z, ns.w, eps)};
+            Nb<T> N{nn.z, nn.w, nn.x, nn.y, is_wet(nn.z, nn.w, eps)};
             accel(P, H, b, ux, uy, W, E, S, N, ax, ay);
             const T v = cell_speed(P, H, ux, uy, ax, ay);
             const bool fin = v <= T(sizeof(T) == 4 ? FLT_MAX : DBL_MAX);
@@ -625,11 +627,12 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                 fence_proxy_async();
                 issue_row<T, ACC>(s, a, buf, k + PREF, gx0, gy0, cbase);
             }
-            // every thread observes the copy of row k; a wait that gives up
-            // is reported after the iteration's barrier (the row's values
-            // are then garbage, but every index stays in bounds)
+            // the Lagrangian group's threads observe the copy of row k (the
+            // Eulerian group reads no input ring); a wait that gives up is
+            // reported after the iteration's barrier (the row's values are
+            // then garbage, but every index stays in bounds)
             const unsigned gr = cbase + (unsigned)k;
-            if (!mbar_wait_bounded(&s.bar[gr % NBAR], (gr / NBAR) & 1u)) s.abort = 1;
+            if (groupL && !mbar_wait_bounded(&s.bar[gr % NBAR], (gr / NBAR) & 1u)) s.abort = 1;
         }
         if (ACC) {
             if (groupL) {

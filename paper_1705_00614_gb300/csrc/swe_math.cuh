@@ -421,19 +421,23 @@ __device__ __forceinline__ void face_flux(const Phys<T>& P, const ECell<T>& L, c
                                           T& FQx, T& FQy) {
     T wl[5], wr[5];
     if constexpr (sizeof(T) == 4) {
-        const f2 hp = mk2(0.5f, 0.5f), hm = mk2(-0.5f, -0.5f);
-        const f2 d0 = fma2(mk2(0.5f, -0.5f), mk2(sL[0], sR[0]), mk2(L.w[0], R.w[0]));
+        // the face values this face uses, as (left, right) pairs: surface,
+        // normal velocity (nq), and the two upwind momentum velocities; the
+        // tangential mean velocity is not reconstructed (unused, so its
+        // slope is never formed either)
+        const f2 lr = mk2(0.5f, -0.5f);
+        const f2 d0 = fma2(lr, mk2(sL[0], sR[0]), mk2(L.w[0], R.w[0]));
+        const f2 dn = fma2(lr, mk2(sL[nq], sR[nq]), mk2(L.w[nq], R.w[nq]));
+        const f2 l2 = fma2(mk2(0.5f, 0.5f), mk2(sL[3], sL[4]), mk2(L.w[3], L.w[4]));
+        const f2 r2 = fma2(mk2(-0.5f, -0.5f), mk2(sR[3], sR[4]), mk2(R.w[3], R.w[4]));
         wl[0] = d0.x;
         wr[0] = d0.y;
-#pragma unroll
-        for (int q = 1; q < 5; q += 2) {
-            const f2 l2 = fma2(hp, mk2(sL[q], sL[q + 1]), mk2(L.w[q], L.w[q + 1]));
-            const f2 r2 = fma2(hm, mk2(sR[q], sR[q + 1]), mk2(R.w[q], R.w[q + 1]));
-            wl[q] = l2.x;
-            wl[q + 1] = l2.y;
-            wr[q] = r2.x;
-            wr[q + 1] = r2.y;
-        }
+        wl[1] = wl[2] = dn.x;
+        wr[1] = wr[2] = dn.y;
+        wl[3] = l2.x;
+        wl[4] = l2.y;
+        wr[3] = r2.x;
+        wr[4] = r2.y;
     } else {
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
