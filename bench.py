@@ -294,12 +294,12 @@ def run_closure(args, torch, swe, stream, rank, world):
     win = args.closure_window
     # input and target statistics from the first training seeds' runs
     norm = CL.estimate_norm(torch, [scenario(sd) for sd in train_seeds[:4]], 40 * win, tau_c, rng, 128,
-                            bed=args.closure_bed, horizon=win)
+                            bed=args.closure_bed, horizon=win, stride=args.closure_stride)
     X, T = [], []
     for sd in train_seeds:
         x, t = CL.collect(torch, scenario(sd), args.closure_collect, tau_c, norm.inp(), norm.out(),
                           args.closure_crops, 128, rng, stream=stream.cuda_stream, noise=args.closure_noise,
-                          bed=args.closure_bed, horizon=win)
+                          bed=args.closure_bed, horizon=win, stride=args.closure_stride)
         X.append(x)
         T.append(t)
     X = torch.cat(X)
@@ -309,7 +309,8 @@ def run_closure(args, torch, swe, stream, rank, world):
     for r in range(args.closure_dagger):
         for sd in train_seeds:
             x, t = CL.collect_closed(torch, scenario(sd), args.closure_collect, tau_c, params, norm,
-                                     args.closure_crops, 128, rng, stream=stream.cuda_stream, bed=args.closure_bed)
+                                     args.closure_crops, 128, rng, stream=stream.cuda_stream, bed=args.closure_bed,
+                                     stride=args.closure_stride)
             if x is not None:
                 X = torch.cat([X, x])
                 T = torch.cat([T, t])
@@ -396,7 +397,8 @@ def run_closure(args, torch, swe, stream, rank, world):
                            "scenario": "fractal floodplain, flood release (+2 m over the first quarter) and inflow",
                            "tau_coarse_s": tau_c, "train_seeds": len(train_seeds), "val_seeds": len(val_seeds),
                            "test_seeds": len(test_seeds), "collect_steps_per_seed": args.closure_collect,
-                           "target_window_steps": win, "crops_per_window": args.closure_crops,
+                           "target_window_steps": win, "window_stride_steps": args.closure_stride,
+                           "crops_per_window": args.closure_crops,
                            "train_iters": args.closure_iters,
                            "dagger_rounds": args.closure_dagger, "input_noise": args.closure_noise,
                            "coarse_bed": args.closure_bed,
@@ -680,6 +682,8 @@ def main():
     ap.add_argument("--closure-collect", type=int, default=100, help="closure workload: coarse steps per seed")
     ap.add_argument("--closure-crops", type=int, default=2,
                     help="closure workload: 128^2 training crops per target window")
+    ap.add_argument("--closure-stride", type=int, default=1,
+                    help="closure workload: coarse steps between training windows (spreads the pairs over the run)")
     ap.add_argument("--closure-window", type=int, default=1,
                     help="closure workload: coarse steps per training target (average correction over the window)")
     ap.add_argument("--closure-iters", type=int, default=3000, help="closure workload: Adam steps")

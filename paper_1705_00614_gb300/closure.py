@@ -127,7 +127,7 @@ def perturb(H, Qx, Qy, rel, rng):
 
 
 def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, crop, rng, stream=None, noise=0.0,
-            bed="mean", horizon=1):
+            bed="mean", horizon=1, stride=None):
     """Run the fine grid and, for every window of `horizon` coarse steps,
     the plain coarse steps taken from the restricted fine state at the
     window's start; return standardised (inputs, targets) crops as device
@@ -141,7 +141,10 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
     start from the restricted fine state perturbed by that relative noise
     (perturb) while the target stays the restricted fine state, so the
     network also learns to pull a state that has drifted back (input noise
-    against the distribution shift of closed runs)."""
+    against the distribution shift of closed runs).  stride (coarse steps,
+    >= horizon; default horizon): windows start every `stride` coarse steps,
+    so `steps` // horizon windows cover steps // horizon * stride coarse
+    steps of the run (pairs from late states of a long run as well)."""
     cp = coarse_problem(fine_prob, bed)
     nyc, nxc = cp.params.ny, cp.params.nx
     fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
@@ -165,6 +168,8 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
             fine.step(4 * horizon)
             B.restrict_from(fine)
             A.closure_targets(B, nout, tfull.data_ptr())
+            if stride is not None and stride > horizon:
+                fine.step(4 * (stride - horizon), report=False)
             torch.cuda.synchronize()
             for _ in range(crops_per_step):
                 y0 = int(rng.integers(0, nyc - crop + 1))
@@ -178,13 +183,15 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
     return torch.stack(xs), torch.stack(ts)
 
 
-def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step, crop, rng, stream=None, bed="mean"):
+def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step, crop, rng, stream=None, bed="mean",
+                   stride=None):
     """Training pairs along the closed model's own coarse trajectory: the
     closed grid runs beside the fine grid; at every coarse step the plain
     coarse step is taken from the closed grid's state and the target is the
     correction that would have put it on the restricted fine state.  A
     network trained on them also learns to undo its own drift (pairs from
-    the states it visits, not only from restricted fine states)."""
+    the states it visits, not only from restricted fine states).  stride:
+    coarse steps between pairs (both runs advance that far), as in collect."""
     cp = coarse_problem(fine_prob, bed)
     nyc, nxc = cp.params.ny, cp.params.nx
     fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
@@ -211,6 +218,9 @@ def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step,
                 B.restrict_from(fine)
                 A.closure_targets(B, norm.out(), tfull.data_ptr())
                 C.step_closed(1, report=False)
+                if stride is not None and stride > 1:
+                    C.step_closed(stride - 1, report=False)
+                    fine.step(4 * (stride - 1), report=False)
                 torch.cuda.synchronize()
             except S.SweError:
                 break  # the closed state no longer gives a finite step
@@ -229,13 +239,14 @@ def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step,
     return torch.stack(xs), torch.stack(ts).clamp_(-10.0, 10.0)
 
 
-def estimate_norm(torch, probs, steps, tau_c, rng, crop, bed="mean", horizon=1):
+def estimate_norm(torch, probs, steps, tau_c, rng, crop, bed="mean", horizon=1, stride=None):
     """Per-channel mean and standard deviation of inputs and targets from a
     short pilot collection with identity normalisation (targets over windows
     of `horizon` coarse steps, as collect makes them)."""
     X, T = [], []
     for p in probs:
-        x, t = collect(torch, p, steps, tau_c, NORM_ID_IN, NORM_ID_OUT, 4, crop, rng, bed=bed, horizon=horizon)
+        x, t = collect(torch, p, steps, tau_c, NORM_ID_IN, NORM_ID_OUT, 4, crop, rng, bed=bed, horizon=horizon,
+                       stride=stride)
         X.append(x.float().cpu().numpy().reshape(-1, 16)[:, :5])
         T.append(t.cpu().numpy().reshape(-1, 3))
     X = np.concatenate(X).astype(np.float64)
