@@ -384,7 +384,14 @@ def run_closure(args, torch, swe, stream, rank, world):
 
     last = horizons[-1]
     val = run_seeds(val_seeds)
-    chosen = min(names[1:], key=lambda k: np.nan_to_num(val[k][last], nan=np.inf))
+    # the validation seeds pick the largest correction scale whose error at
+    # the longest horizon stays within the 1% bar (the most the network may
+    # act while meeting it); if none does, the one with the smallest error
+    ok = [k for k, (a, _) in zip(names[1:], specs) if np.nan_to_num(val[k][last], nan=np.inf) <= 0.01]
+    if ok:
+        chosen = max(ok, key=lambda k: specs[names.index(k) - 1][0])
+    else:
+        chosen = min(names[1:], key=lambda k: np.nan_to_num(val[k][last], nan=np.inf))
     test = run_seeds(test_seeds)
     gain = [h for h in horizons if test[chosen][h] < test["plain"][h]]
     speedup = float(np.median(ms_fine)) / float(np.median(ms_closed))
@@ -680,13 +687,13 @@ def main():
                     help="closure workload: validation seeds (choose the correction scale)")
     ap.add_argument("--closure-test", type=int, default=16, help="closure workload: held-out test seeds")
     ap.add_argument("--closure-collect", type=int, default=100, help="closure workload: coarse steps per seed")
-    ap.add_argument("--closure-crops", type=int, default=2,
+    ap.add_argument("--closure-crops", type=int, default=4,
                     help="closure workload: 128^2 training crops per target window")
-    ap.add_argument("--closure-stride", type=int, default=1,
+    ap.add_argument("--closure-stride", type=int, default=50,
                     help="closure workload: coarse steps between training windows (spreads the pairs over the run)")
     ap.add_argument("--closure-window", type=int, default=1,
                     help="closure workload: coarse steps per training target (average correction over the window)")
-    ap.add_argument("--closure-iters", type=int, default=3000, help="closure workload: Adam steps")
+    ap.add_argument("--closure-iters", type=int, default=6000, help="closure workload: Adam steps")
     ap.add_argument("--closure-steps", type=int, default=5000, help="closure workload: longest horizon")
     ap.add_argument("--closure-alpha", default="1,0.5,0.25,0.1,0.05",
                     help="closure workload: comma-separated correction scales (a suffix /m keeps the momentum "
