@@ -310,7 +310,7 @@ def run_closure(args, torch, swe, stream, rank, world):
         for sd in train_seeds:
             x, t = CL.collect_closed(torch, scenario(sd), args.closure_collect, tau_c, params, norm,
                                      args.closure_crops, 128, rng, stream=stream.cuda_stream, bed=args.closure_bed,
-                                     stride=args.closure_stride)
+                                     stride=args.closure_stride, bound=args.closure_bound)
             if x is not None:
                 X = torch.cat([X, x])
                 T = torch.cat([T, t])
@@ -345,6 +345,7 @@ def run_closure(args, torch, swe, stream, rank, world):
                     net.set_params(params)
                     c.restrict_from(fine)
                     c.attach_closure(net, CL.shrink(norm, a, ah).all())
+                    c.closure_bound(args.closure_bound)
                 done = 0
                 for h in horizons:
                     k = h - done
@@ -408,7 +409,7 @@ def run_closure(args, torch, swe, stream, rank, world):
                            "crops_per_window": args.closure_crops,
                            "train_iters": args.closure_iters,
                            "dagger_rounds": args.closure_dagger, "input_noise": args.closure_noise,
-                           "coarse_bed": args.closure_bed,
+                           "coarse_bed": args.closure_bed, "correction_bound": args.closure_bound,
                            "final_train_loss": hist[-1][1], "train_wall_s": t_train,
                            "rel_l2_test": test, "rel_l2_val": val, "chosen_on_val": chosen,
                            "closed_below_plain_at": gain,
@@ -694,6 +695,8 @@ def main():
     ap.add_argument("--closure-window", type=int, default=1,
                     help="closure workload: coarse steps per training target (average correction over the window)")
     ap.add_argument("--closure-iters", type=int, default=6000, help="closure workload: Adam steps")
+    ap.add_argument("--closure-bound", type=float, default=0.5,
+                    help="closure workload: corrections bounded by this fraction of the plain flux sums (0: unbounded)")
     ap.add_argument("--closure-steps", type=int, default=5000, help="closure workload: longest horizon")
     ap.add_argument("--closure-alpha", default="1,0.5,0.25,0.1,0.05",
                     help="closure workload: comma-separated correction scales (a suffix /m keeps the momentum "

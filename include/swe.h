@@ -358,6 +358,14 @@ SWE_API int swe_closure_targets(swe_ctx* pred, swe_ctx* ref, const float* norm_o
  * output mu[3], sd[3] (sd >= 0; a channel with mu = sd = 0 adds no
  * correction) (host).  The context borrows the network. */
 SWE_API int swe_closure_attach(swe_ctx* ctx, swe_cnn* cnn, const float* norm);
+/* Bound the attached network's corrections (no counterpart in the paper, a
+ * reading of how a learned closure may act): with beta > 0 each correction
+ * c of a cell's net flux sum f (Fh, Fv_x or Fv_y of the plain step) is
+ * applied as min(max(c, -beta |f|), beta |f|), so it never exceeds that
+ * fraction of the flux it corrects and adds nothing where the plain step
+ * moves nothing; beta = 0 (the default) applies the corrections unbounded.
+ * SWE_ERR_ARG for a negative or non-finite beta.  Synchronises. */
+SWE_API int swe_closure_bound(swe_ctx* ctx, double beta);
 /* Closed coarse steps: per step, the network predicts corrections of the net
  * face-flux sums from the state at t_n, their depth part is centred over
  * wet cells (the corrections add no mass), and the fused step adds them in

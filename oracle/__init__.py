@@ -80,7 +80,7 @@ def _load(path):
                            ctypes.POINTER(_Sources), ctypes.c_double, _dp, _dp, _dp,
                            _dp, _dp, _dp, ctypes.POINTER(_Info), ctypes.POINTER(_Stages)]
     L.orc_step_corr.restype = ctypes.c_int
-    L.orc_step_corr.argtypes = L.orc_step.argtypes + [_dp]
+    L.orc_step_corr.argtypes = L.orc_step.argtypes + [_dp, ctypes.c_double]
     L.orc_riemann.restype = None
     L.orc_riemann.argtypes = [ctypes.c_double] * 6 + [_dp]
     L.orc_state_speed.restype = ctypes.c_double
@@ -148,11 +148,13 @@ class _Bound:
         return None if self.solid is None else self.solid.ctypes.data
 
 
-def step(prob, H, Qx, Qy, t=0.0, t_end=0.0, stages=False, bound=None, L=None, corr=None):
+def step(prob, H, Qx, Qy, t=0.0, t_end=0.0, stages=False, bound=None, L=None, corr=None, corr_bound=0.0):
     """One oracle time step.  Returns (H, Qx, Qy, info, stages-or-None).
     ``L`` selects another loaded build (see ``lib(path)``).  ``corr``
     ([3, ny, nx] or None): additive corrections of each cell's net face-flux
-    sums (Fh, Fv_x, Fv_y), applied in the final update (a learned closure)."""
+    sums (Fh, Fv_x, Fv_y), applied in the final update (a learned closure),
+    each bounded by ``corr_bound`` times the magnitude of its flux sum when
+    ``corr_bound`` > 0."""
     bd = bound or _Bound(prob)
     p = bd.params
     nx, ny = p.nx, p.ny
@@ -175,7 +177,7 @@ def step(prob, H, Qx, Qy, t=0.0, t_end=0.0, stages=False, bound=None, L=None, co
     else:
         corr = _c(corr)
         assert corr.shape == (3, ny, nx)
-        rc = (L or lib()).orc_step_corr(*args, _ptr(corr))
+        rc = (L or lib()).orc_step_corr(*args, _ptr(corr), float(corr_bound))
     if rc != 0:
         raise RuntimeError(f"oracle step failed with status {rc}")
     d = {k: getattr(info, k) for k, _ in _Info._fields_}

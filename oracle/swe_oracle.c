@@ -258,14 +258,26 @@ static double source_rate(const orc_sources* s, int m, double t)
     return s->weight[m] * q;
 }
 
+/* A correction c of a net flux sum f, bounded by beta |f| when beta > 0:
+ * min(max(c, -beta |f|), beta |f|) (beta <= 0: c unchanged). */
+static double bounded(double c, double f, double beta)
+{
+    if (!(beta > 0.0)) return c;
+    double lim = beta * fabs(f);
+    return dmin(dmax(c, -lim), lim);
+}
+
 /* One full time step from (H, Qx, Qy) at time t to (Hn, Qxn, Qyn).
  * corr (may be NULL): three [ny][nx] planes added to each cell's net
  * face-flux sums (Fh, Fv_x, Fv_y) before the final update, the additive
- * sub-grid corrections of a learned closure of a coarse grid level.
+ * sub-grid corrections of a learned closure of a coarse grid level; with
+ * corr_bound > 0 each correction is first bounded by corr_bound times the
+ * magnitude of the flux sum it corrects.
  * Returns 0 on success, -1 on allocation failure, -5 when tau <= 0. */
 int orc_step_corr(const orc_params* p, const double* b, const double* nm, const unsigned char* solid_in,
                   const orc_sources* src, double t, const double* H, const double* Qx, const double* Qy,
-                  double* Hn, double* Qxn, double* Qyn, orc_info* info, orc_stages* st, const double* corr)
+                  double* Hn, double* Qxn, double* Qyn, orc_info* info, orc_stages* st, const double* corr,
+                  double corr_bound)
 {
     const int nx = p->nx, ny = p->ny;
     const size_t N = (size_t)nx * (size_t)ny;
@@ -422,9 +434,9 @@ int orc_step_corr(const orc_params* p, const double* b, const double* nm, const 
             double fqx = (fxl[NFX + fw] - fxl[NFX + fe]) + (fyl[NFY + fs] - fyl[NFY + fn]);
             double fqy = (fxl[2 * NFX + fw] - fxl[2 * NFX + fe]) + (fyl[2 * NFY + fs] - fyl[2 * NFY + fn]);
             if (corr) {
-                fh = fh + corr[k];
-                fqx = fqx + corr[N + k];
-                fqy = fqy + corr[2 * N + k];
+                fh = fh + bounded(corr[k], fh, corr_bound);
+                fqx = fqx + bounded(corr[N + k], fqx, corr_bound);
+                fqy = fqy + bounded(corr[2 * N + k], fqy, corr_bound);
             }
             double hn = ht[k] + dth * fh;
             if (hn < 0.0) { clip += -hn; hn = 0.0; }
@@ -463,7 +475,7 @@ int orc_step(const orc_params* p, const double* b, const double* nm, const unsig
              const orc_sources* src, double t, const double* H, const double* Qx, const double* Qy,
              double* Hn, double* Qxn, double* Qyn, orc_info* info, orc_stages* st)
 {
-    return orc_step_corr(p, b, nm, solid_in, src, t, H, Qx, Qy, Hn, Qxn, Qyn, info, st, NULL);
+    return orc_step_corr(p, b, nm, solid_in, src, t, H, Qx, Qy, Hn, Qxn, Qyn, info, st, NULL, 0.0);
 }
 
 /* Largest signal speed of a state, as used for tau (for initial checks). */

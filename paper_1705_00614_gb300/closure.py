@@ -184,7 +184,7 @@ def collect(torch, fine_prob, steps, tau_c, norm_in, norm_out, crops_per_step, c
 
 
 def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step, crop, rng, stream=None, bed="mean",
-                   stride=None):
+                   stride=None, bound=0.0):
     """Training pairs along the closed model's own coarse trajectory: the
     closed grid runs beside the fine grid; at every coarse step the plain
     coarse step is taken from the closed grid's state and the target is the
@@ -206,6 +206,7 @@ def collect_closed(torch, fine_prob, steps, tau_c, params, norm, crops_per_step,
         net.set_params(params)
         C.restrict_from(fine)
         C.attach_closure(net, norm.all())
+        C.closure_bound(bound)
         for _ in range(steps):
             H, Qx, Qy, t = C.get_state()
             if not (np.isfinite(H).all() and np.isfinite(Qx).all() and np.isfinite(Qy).all()):
@@ -299,9 +300,10 @@ def shrink(norm: Norm, alpha: float, alpha_h=None) -> Norm:
     return Norm(norm.mu_in, norm.sd_in, norm.mu_out * f, norm.sd_out * f)
 
 
-def evaluate(torch, fine_prob, params, norm, nsteps, tau_c, stream=None, bed="mean"):
+def evaluate(torch, fine_prob, params, norm, nsteps, tau_c, stream=None, bed="mean", bound=0.0):
     """Relative L2 error in H after nsteps coarse steps against the
-    restricted fine solution, with and without the closure."""
+    restricted fine solution, with and without the closure (corrections
+    bounded by `bound` times the plain flux sums when bound > 0)."""
     cp = coarse_problem(fine_prob, bed)
     fine = S.Solver.from_problem(with_dt(fine_prob, tau_c / 4.0), "f32", stream=stream)
     plain = S.Solver.from_problem(with_dt(cp, tau_c), "f32", stream=stream)
@@ -313,6 +315,7 @@ def evaluate(torch, fine_prob, params, norm, nsteps, tau_c, stream=None, bed="me
         plain.restrict_from(fine)
         closed.restrict_from(fine)
         closed.attach_closure(net, norm.all())
+        closed.closure_bound(bound)
         fine.step(4 * nsteps)
         plain.step(nsteps)
         closed.step_closed(nsteps)

@@ -116,6 +116,7 @@ struct swe_ctx {
     void* d_feat = nullptr;    // BF16 [ny][nx][16]
     void* d_corr = nullptr;    // 3 padded planes
     double* d_acc = nullptr;
+    double corr_bound = 0.0;   // > 0: corrections bounded by this fraction of the plain flux sums
     cudaGraphExec_t cexec = nullptr;
     int csteps = 0;
     // wet-block stamps (skip_dry)
@@ -228,6 +229,7 @@ FusedArgs<T> fused_args(const swe_ctx* c, bool closed = false) {
     a.seg_h = c->seg_h;
     a.nitems = c->nitems;
     a.corr = closed ? (const T*)c->d_corr : nullptr;
+    a.corr_bound = (T)c->corr_bound;
     a.act = c->d_act;
     a.act_nbx = c->act_nbx;
     // closed steps stamp but never skip; rain wets dry tiles and the losses
@@ -1512,6 +1514,20 @@ int swe_closure_targets(swe_ctx* pred, swe_ctx* ref, const float* norm_out, floa
     cudaFree(d);
     CK(e);
     CK(e2);
+    return SWE_OK;
+}
+
+int swe_closure_bound(swe_ctx* c, double beta) {
+    if (!c) return fail(SWE_ERR_ARG, "null context");
+    if (!(beta >= 0.0) || !std::isfinite(beta)) return fail(SWE_ERR_ARG, "bound must be finite and >= 0");
+    CK(cudaSetDevice(c->dev));
+    CK(cudaStreamSynchronize(c->st));
+    if (c->cexec) {  // the bound is a launch argument of the captured steps
+        cudaGraphExecDestroy(c->cexec);
+        c->cexec = nullptr;
+        c->csteps = 0;
+    }
+    c->corr_bound = beta;
     return SWE_OK;
 }
 

@@ -508,11 +508,20 @@ __device__ __forceinline__ bool fused_item(FSmem<T, ACC>& s, const FusedArgs<T>&
                 fqy = (fw.y - fe.y) + (fyPrev[2] - fyCur[2]);
             }
             if (a.corr && gx0 + c < a.g.nx + 2 * PAD) {
-                // learned sub-grid corrections of the net flux sums
+                // learned sub-grid corrections of the net flux sums, bounded
+                // by a fraction of the plain sums when a bound is set
                 const size_t gk = (size_t)(gy0 + r) * (size_t)a.g.pitch + (size_t)(gx0 + c);
-                fh += a.corr[gk];
-                fqx += a.corr[a.corr_plane + gk];
-                fqy += a.corr[2 * a.corr_plane + gk];
+                const T c0 = a.corr[gk], c1 = a.corr[a.corr_plane + gk], c2 = a.corr[2 * a.corr_plane + gk];
+                if (a.corr_bound > T(0)) {
+                    const T l0 = a.corr_bound * fabs(fh), l1 = a.corr_bound * fabs(fqx), l2 = a.corr_bound * fabs(fqy);
+                    fh = fh + tmin(tmax(c0, -l0), l0);
+                    fqx = fqx + tmin(tmax(c1, -l1), l1);
+                    fqy = fqy + tmin(tmax(c2, -l2), l2);
+                } else {
+                    fh += c0;
+                    fqx += c1;
+                    fqy += c2;
+                }
             }
             const V4 ca = cA(r)[c], cb4 = cB(r)[c];
             T hn = ca.z + dth * fh;

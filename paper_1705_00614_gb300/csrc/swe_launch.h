@@ -107,6 +107,9 @@ struct FusedArgs {
     // planes F_H, F_Qx, F_Qy), or null
     const T* corr;
     size_t corr_plane;
+    // > 0: each correction is bounded by corr_bound times the magnitude of
+    // the cell's plain flux sum it corrects
+    T corr_bound;
 };
 
 // Control block of a batched launch: the next work-list entry to hand out and

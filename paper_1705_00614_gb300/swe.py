@@ -26,7 +26,7 @@ API = ["swe_params_default", "swe_create", "swe_set_terrain", "swe_set_state", "
        "swe_batch_create", "swe_batch_set_gate_events", "swe_batch_step", "swe_batch_autotune",
        "swe_batch_destroy", "swe_cnn_create", "swe_cnn_num_params", "swe_cnn_set_params", "swe_cnn_get_params",
        "swe_cnn_forward", "swe_cnn_gradients", "swe_cnn_train_step", "swe_cnn_destroy", "swe_restrict_state",
-       "swe_closure_features", "swe_closure_targets", "swe_closure_attach", "swe_step_closed",
+       "swe_closure_features", "swe_closure_targets", "swe_closure_attach", "swe_closure_bound", "swe_step_closed",
        "swe_set_terrain_ext", "swe_nest_create", "swe_nest_step", "swe_nest_destroy", "swe_set_state_native",
        "swe_get_state_native", "swe_check_bounded_wait"]
 CNN_CHANNELS = (5, 32, 32, 32, 3)
@@ -148,6 +148,7 @@ def load(path=None):
                        ("swe_closure_features", [ctypes.c_void_p, _fp, ctypes.c_void_p]),
                        ("swe_closure_targets", [ctypes.c_void_p, ctypes.c_void_p, _fp, ctypes.c_void_p]),
                        ("swe_closure_attach", [ctypes.c_void_p, ctypes.c_void_p, _fp]),
+                       ("swe_closure_bound", [ctypes.c_void_p, ctypes.c_double]),
                        ("swe_step_closed", [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(StepInfo)]),
                        ("swe_set_terrain_ext", [ctypes.c_void_p, _dp, _dp]),
                        ("swe_nest_create", [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
@@ -372,6 +373,9 @@ class Solver:
         a = np.ascontiguousarray(norm, dtype=np.float32)
         _check(self.L, self.L.swe_closure_attach(self.h, cnn.h if cnn is not None else None,
                                                  a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def closure_bound(self, beta):
+        _check(self.L, self.L.swe_closure_bound(self.h, float(beta)))
 
     def step_closed(self, nsteps=1, report=True):
         info = StepInfo()

@@ -147,3 +147,36 @@ def test_oracle_step_applies_flux_corrections_in_the_final_update():
     mask[4, 5] = mask[10, 11] = False
     assert np.all(H[mask] == 1.5) and np.all(Qx[mask] == 0.0) and np.all(Qy[mask] == 0.0)
     assert abs(info["mass"] - 1.5 * n * n * dx * dx) <= 1e-12 * info["mass"]
+
+
+def test_bounded_corrections_are_clamped_to_a_fraction_of_the_flux_sums():
+    """With a bound beta > 0 each correction c of a net flux sum f is applied
+    as min(max(c, -beta |f|), beta |f|): on a lake at rest (every flux sum
+    zero) no correction moves the water at all; on a dam break the change
+    each bounded correction makes to H and Q is (tau/h) times the clamped
+    value, with f read off the plain step (f = (new - post-Lagrangian) h/tau)."""
+    rng = np.random.default_rng(11)
+    beta = 0.5
+    # lake at rest: all flux sums vanish, so every correction is clamped to 0
+    n = 16
+    z = np.zeros((n, n))
+    lake = I.Problem("lake", I.Params(nx=n, ny=n, dx=2.0, dt_fixed=0.1), z.copy(), z.copy(), np.full((n, n), 1.5),
+                     z.copy(), z.copy(), I.Sources.empty())
+    corr = rng.normal(0.0, 5.0, size=(3, n, n))
+    H, Qx, Qy, _, _ = oracle.step(lake, lake.H, lake.Qx, lake.Qy, 0.0, corr=corr, corr_bound=beta)
+    assert np.all(H == 1.5) and np.all(Qx == 0.0) and np.all(Qy == 0.0)
+    # dam break: compare with the plain step's flux sums
+    p = I.dam_break(40, 1.0, 2.0, 1.0, ny=6)
+    p.params.dt_fixed = 0.05
+    Hp, Qxp, Qyp, info, st = oracle.step(p, p.H, p.Qx, p.Qy, 0.0, stages=True)
+    k = info["tau"] / p.params.dx
+    corr = rng.normal(0.0, 1.0, size=(3, 6, 40))
+    Hb, Qxb, Qyb, _, _ = oracle.step(p, p.H, p.Qx, p.Qy, 0.0, corr=corr, corr_bound=beta)
+    fh = (Hp - st["ht"]) / k
+    fqx = (Qxp - st["qtx"]) / k
+    for got, plain, f, c in ((Hb, Hp, fh, corr[0]), (Qxb, Qxp, fqx, corr[1])):
+        lim = beta * np.abs(f)
+        want = np.minimum(np.maximum(c, -lim), lim) * k
+        assert np.abs((got - plain) - want).max() <= 1e-12
+    clamped = np.abs(corr[0]) > beta * np.abs(fh)
+    assert clamped.any() and (~clamped & (np.abs(fh) > 0)).any()

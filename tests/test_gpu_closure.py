@@ -161,7 +161,8 @@ def test_coarse_lake_on_gpu_matches_oracle(env, bed):
     assert (moved <= 1e-12) == (bed == "volume"), (bed, moved)
 
 
-def test_closed_step_with_a_network_matches_oracle(env):
+@pytest.mark.parametrize("bound", [0.0, 0.5])
+def test_closed_step_with_a_network_matches_oracle(env, bound):
     """Closed coarse steps with a non-zero network (seeded He weights and
     biases) on a flooded 96 x 80 coarse floodplain in FP64, against the
     oracle's closed step: the FP64 oracle network on the same BF16 features
@@ -170,7 +171,9 @@ def test_closed_step_with_a_network_matches_oracle(env):
     wet cells' flux sums, added in the oracle step's final update.  The
     network runs in BF16 on the GPU, so the closed states agree to the
     network's tolerance: the GPU-oracle difference is within 2e-2 of what
-    the corrections change (relative L2, each field), over three steps."""
+    the corrections change (relative L2, each field), over three steps;
+    unbounded, and with the corrections bounded by half the plain flux sums
+    (swe_closure_bound, the oracle's corr_bound)."""
     import oracle
     from oracle import cnn_oracle as C
     torch, swe, closure = env
@@ -199,13 +202,14 @@ def test_closed_step_with_a_network_matches_oracle(env):
     with swe.Solver.from_problem(cp, "f64") as s, swe.CNN(1, ny, nx) as net:
         net.set_params(flat)
         s.attach_closure(net, norm.all())
+        s.closure_bound(bound)
         for k in range(3):
             x = C.closure_features(H, Qx, Qy, cp.b, cp.n_manning, cp.params.eps, mu_in, sd_in)
             y = C.forward(params_r, x, store=C.round_bf16)[-1]
             corr = C.closure_corrections(y, H, cp.params.eps, mu_out, sd_out)
             assert np.abs(corr).max() > 1e-3
             Hp, Qxp, Qyp, _, _ = oracle.step(cp, H, Qx, Qy, t)
-            H, Qx, Qy, info, _ = oracle.step(cp, H, Qx, Qy, t, corr=corr)
+            H, Qx, Qy, info, _ = oracle.step(cp, H, Qx, Qy, t, corr=corr, corr_bound=bound)
             t = info["t_new"]
             s.step_closed(1)
             g = s.get_state()

@@ -83,10 +83,17 @@ MUTANTS = [
      "double upy = fabs(uy[k] + sgn(ax[k]) * sqrt(p->dx * fabs(ax[k])));", ["test_time_step_from_particle_speed"]),
     ("wave speed from the sum of components", "double us = dmax(fabs(ux[k]), fabs(uy[k])) + c;",
      "double us = fabs(ux[k]) + fabs(uy[k]) + c;", ["test_time_step_from_wave_speed_two_components"]),
-    ("closure correction of Q_x applied to Q_y", "fqy = fqy + corr[2 * N + k];", "fqy = fqy + corr[N + k];",
+    ("closure correction of Q_x applied to Q_y", "fqy = fqy + bounded(corr[2 * N + k], fqy, corr_bound);",
+     "fqy = fqy + bounded(corr[N + k], fqy, corr_bound);",
      ["test_oracle_step_applies_flux_corrections_in_the_final_update"]),
-    ("closure correction subtracted", "fh = fh + corr[k];", "fh = fh - corr[k];",
+    ("closure correction subtracted", "fh = fh + bounded(corr[k], fh, corr_bound);",
+     "fh = fh - bounded(corr[k], fh, corr_bound);",
      ["test_oracle_step_applies_flux_corrections_in_the_final_update"]),
+    ("bound without the magnitude", "double lim = beta * fabs(f);", "double lim = beta * f;",
+     ["test_bounded_corrections_are_clamped_to_a_fraction_of_the_flux_sums"]),
+    ("momentum correction bounded by the mass flux", "fqx = fqx + bounded(corr[N + k], fqx, corr_bound);",
+     "fqx = fqx + bounded(corr[N + k], fh, corr_bound);",
+     ["test_bounded_corrections_are_clamped_to_a_fraction_of_the_flux_sums"]),
 ]
 
 
