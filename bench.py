@@ -256,7 +256,7 @@ def run_cnn(args, torch, swe, stream, rank, world):
                            "parallelism": "replicas" if world > 1 else "single GPU"},
                 "roofline": {"bound": "tensor", "achieved": tflops, "peak": peak, "unit": "TFLOP/s",
                              "frac": tflops / peak, "peak_source": src, "traffic": None,
-                             "kernel": "k_conv (tcgen05) + k_wgrad (mma.sync), BF16"},
+                             "kernel": "k_conv + k_wgrad_tc (tcgen05), BF16"},
                 "forward_roofline": {"bound": "hbm", "achieved": fwd_gbs, "peak": hbm_peak, "unit": "GB/s",
                                      "frac": fwd_gbs / hbm_peak, "bytes_per_pixel": CNN_FWD_BYTES,
                                      "kernel": "k_conv x 4 (forward)"},

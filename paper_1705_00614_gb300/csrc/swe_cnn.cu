@@ -7,9 +7,9 @@
 // Tensor-core kernels: BF16 operands, FP32 accumulation, NHWC activations.
 // Forward and data-gradient convolutions are implicit GEMMs over (pixel) x
 // (tap, input channel) on the fifth-generation tensor cores (tcgen05.mma,
-// accumulator in tensor memory); the weight gradient is an implicit GEMM
-// over (input channel) x (pixel) per tap (mma.sync m16n8k16), reduced over
-// CTAs in a fixed order.  Channel counts are padded: inputs to multiples of
+// accumulator in tensor memory); the weight gradient is, per tap, a GEMM
+// of (output channel) x (input channel) over pixels on the same tensor
+// cores, reduced over CTAs in a fixed order.  Channel counts are padded: inputs to multiples of
 // 16 (the MMA K step), outputs to 16 or 32 (the MMA N).
 #include <cuda_bf16.h>
 
@@ -40,31 +40,14 @@ int cfail(int code, const std::string& m) {
             return cfail(SWE_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_));  \
     } while (0)
 
-constexpr int TY = 8, TX = 16;   // pixels per CTA tile (one warp per row)
+constexpr int TY = 8, TX = 16;   // the image height and width are multiples of these
 constexpr int NLAYER = 4;
 constexpr int CH[NLAYER + 1] = {5, 32, 32, 32, 3};
 constexpr int CIP[NLAYER] = {16, 32, 32, 32};  // padded input channels
 constexpr int COP[NLAYER] = {32, 32, 32, 16};  // padded output channels
 
-// Four 8 x 8 BF16 matrices from shared memory, transposed (lanes 8q .. 8q+7
-// give the 16-byte rows of matrix q).
-__device__ __forceinline__ void ldsm_x4_t(uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3, const void* p) {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(smem_u32(p)));
-}
-
 __device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
-}
-
-__device__ __forceinline__ void mma_bf16(float d[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
 }
 
 // Output handling of the convolution kernel.
@@ -266,128 +249,245 @@ __global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMa
     }
 }
 
-// Weight gradient partials of one persistent CTA: the CTA takes the tiles
-// blockIdx.x, blockIdx.x + gridDim.x, ... (a fixed set, in a fixed order) and
-// accumulates, in registers, P[cta][tap][c][o] = sum over their pixels p of
-// x[p + off(tap)][c] * g[p][o]; per tap a GEMM with M = c (16-row blocks),
-// N = o (8-column blocks), K = pixels.  Each warp owns up to UPW (tap,
-// c-block) units for the whole launch.
+// Weight gradient on the fifth-generation tensor cores.  For a layer with
+// weights W[dy][dx][c][o] the gradient is
+//   P[dy][dx][c][o] = sum over pixels p of x[p + (dy - 1, dx - 1)][c] g[p][o],
+// for each column shift dx one GEMM of M = (dy, c) (the three input rows of a
+// 128-pixel row tile stacked, with a row of ones after each row's channels:
+// 3 (CI + 8) rows, padded to 128) by N = o over K = pixels, 16 per
+// instruction.  The ones rows give the bias gradient sum_p g[p][o].  Both
+// operands are read in the MN-major layout straight from NHWC rows staged by
+// TMA ([chunk of 8 channels][pixel][8], 16 bytes per pixel and chunk): the
+// shift dx moves the start address by 16 bytes, the K groups of 8 pixels are
+// 128 bytes apart (LBO) and the channel chunks one chunk apart (SBO).
+// Stacking dy on M needs the three rows of a tile in consecutive row
+// positions, so the input rows stream through a ring of WT_RS positions
+// followed by two shadow positions that take second copies of the rows in
+// positions 0 and 1, and spare positions that the padding rows of M read
+// (finite data in accumulator rows that are never stored).
+//
+// A persistent CTA walks items of rows of one 128-pixel column band, keeps
+// its accumulators in tensor memory and writes its partial sums once at the
+// end (reduced over CTAs in a fixed order by k_wgrad_reduce).  One thread
+// issues the copies, one the MMAs; a row slot is released to the copies by
+// tcgen05.commit after the last tile that reads it.  Waits are bounded; on a
+// timeout *err is set, both threads wait (bounded) for what they issued, the
+// CTA frees its tensor memory and writes no partials.
+constexpr int WT_RS = 10;  // input row positions of the ring
+constexpr int WT_GS = 8;   // output-gradient row slots
+
 template <int CI, int CO>
-__global__ void __launch_bounds__(32 * TY) k_wgrad(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ g,
-                                                   float* __restrict__ part, float* __restrict__ bpart, int H, int W,
-                                                   int ntiles) {
-    constexpr int PS = CI + 8, GS = CO + 8;
-    constexpr int UNITS = 9 * (CI / 16);
-    constexpr int UPW = (UNITS + TY - 1) / TY;
-    constexpr int NT = 32 * TY;
-    // 16-byte elements of a tile's inputs (with halo) and output gradients,
-    // and how many of each one thread moves
-    constexpr int NXE = (TY + 2) * (TX + 2) * (CI / 8), NGE = TY * TX * (CO / 8);
-    constexpr int XPT = (NXE + NT - 1) / NT, GPT = (NGE + NT - 1) / NT;
-    constexpr int BG = NT / CO;  // threads summing one output's bias gradient
-    __shared__ __align__(16) __nv_bfloat16 sx[(TY + 2) * (TX + 2) * PS];
-    __shared__ __align__(16) __nv_bfloat16 sg[TY * TX * GS];
-    __shared__ float sb[NT];
-    static_assert(CO % 16 == 0, "B fragments are loaded in pairs");
-    static_assert(NT % CO == 0, "bias groups");
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int bo = tid % CO, bg = tid / CO;
-    const int gx = W / TX, gy = H / TY;
-    const int r0 = lane >> 2, kc = (lane & 3) * 2;
-    const int lq = lane >> 3, lr = lane & 7;  // ldmatrix: matrix and row this lane addresses
-    float acc[UPW][CO / 8][4];
+struct WgTc {
+    static constexpr int NCX = CI / 8, NCG = CO / 8;  // channel chunks of x and g
+    static constexpr int PCH = NCX + 1;               // chunks per row position (channels, ones)
+    static constexpr int MROWS = 3 * 8 * PCH;         // real rows of M
+    static constexpr int NPOS = WT_RS + 2 + (16 - 3 * PCH + PCH - 1) / PCH;
+    static constexpr int TMC = 3 * CO <= 64 ? 64 : 128;  // accumulator columns (three shifts)
+    static constexpr uint32_t CS = TC_APAD * 16;      // chunk stride
+    static constexpr uint32_t POS = PCH * CS;         // row-position stride
+    static constexpr uint32_t XBYTES = (uint32_t)NPOS * POS;
+    static constexpr uint32_t GBYTES = (uint32_t)(WT_GS * NCG) * CS;
+    static constexpr size_t SMEM = (size_t)XBYTES + GBYTES + 128;
+    static_assert(MROWS <= 128, "M");
+    static_assert(CO == 16 || CO == 32, "MMA N");
+};
+
+template <int CI, int CO>
+__global__ void __launch_bounds__(128, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap gmap,
+               float* __restrict__ part, float* __restrict__ bpart, int H, int W, int rc, int nitems,
+               unsigned* __restrict__ err) {
+    using L = WgTc<CI, CO>;
+    extern __shared__ __align__(128) unsigned char wsm[];
+    unsigned char* const sX = wsm + ((128u - (smem_u32(wsm) & 127u)) & 127u);
+    unsigned char* const sG = sX + L::XBYTES;
+    __shared__ __align__(8) unsigned long long xfull[WT_RS], xempty[WT_RS];
+    __shared__ __align__(8) unsigned long long gfull[WT_GS], gempty[WT_GS];
+    __shared__ __align__(8) unsigned long long tdone;
+    __shared__ uint32_t s_taddr;
+    __shared__ int s_abort;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // zero both rings, then ones in the last chunk of every row position
+    for (uint32_t e = tid; e < (L::XBYTES + L::GBYTES) / 16; e += 128)
+        *reinterpret_cast<uint4*>(sX + 16 * e) = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const uint32_t one2 = 0x3F803F80u;  // two BF16 ones
+    for (uint32_t e = tid; e < (uint32_t)L::NPOS * TC_APAD; e += 128) {
+        const uint32_t pos = e / TC_APAD, px = e % TC_APAD;
+        *reinterpret_cast<uint4*>(sX + pos * L::POS + L::NCX * L::CS + 16 * px) = make_uint4(one2, one2, one2, one2);
+    }
+    if (warp == 0) {
+        tmem_alloc(&s_taddr, L::TMC);
+        tmem_relinquish();
+    }
+    if (tid == 0) {
+        for (int q = 0; q < WT_RS; ++q) {
+            mbar_init(&xfull[q], 1);
+            mbar_init(&xempty[q], 1);
+        }
+        for (int q = 0; q < WT_GS; ++q) {
+            mbar_init(&gfull[q], 1);
+            mbar_init(&gempty[q], 1);
+        }
+        mbar_init(&tdone, 1);
+        fence_mbar_init();
+        s_abort = 0;
+    }
+    fence_proxy_async();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = s_taddr;
+    const int tpr = (W + TCM - 1) / TCM, rcn = (H + rc - 1) / rc;
+
+    if (tid == 32) {
+        // copies: per item the input rows r0 - 1 and r0, then per output row
+        // k the input row r0 + k + 1 and the gradient row r0 + k (the order
+        // the MMAs consume them); a slot is refilled once it is released
+        uint32_t xR = 0, gR = 0, xlap = 0, glap = 0;
+        int xs = 0, gs = 0;
+        auto load_x = [&](int n, int row, int j0) {
+            if (xlap > 0 && !mbar_wait_bounded(&xempty[xs], (xlap - 1) & 1u)) return false;
+            constexpr unsigned bytes = (unsigned)(L::NCX * (TCM + 2) * 16);
+            mbar_expect_tx(&xfull[xs], xs < 2 ? 2u * bytes : bytes);
 #pragma unroll
-    for (int q = 0; q < UPW; ++q)
-#pragma unroll
-        for (int f = 0; f < CO / 8; ++f) acc[q][f][0] = acc[q][f][1] = acc[q][f][2] = acc[q][f][3] = 0.f;
-    float bsum = 0.f;
-    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int n = t / (gx * gy), i0 = ((t / gx) % gy) * TY, j0 = (t % gx) * TX;
-        // all of this thread's loads are issued before the barrier that
-        // retires the previous tile, so their latencies overlap
-        uint4 vx[XPT], vg[GPT];
-#pragma unroll
-        for (int k = 0; k < XPT; ++k) {
-            const int e = tid + k * NT;
-            vx[k] = make_uint4(0, 0, 0, 0);
-            if (e < NXE) {
-                const int p = e / (CI / 8), c8 = e % (CI / 8);
-                const int gi = i0 + p / (TX + 2) - 1, gj = j0 + p % (TX + 2) - 1;
-                if (gi >= 0 && gi < H && gj >= 0 && gj < W)
-                    vx[k] = *reinterpret_cast<const uint4*>(&x[(((size_t)n * H + gi) * W + gj) * CI + 8 * c8]);
+            for (int kc = 0; kc < L::NCX; ++kc) {
+                tma_load_4d(sX + xs * L::POS + kc * L::CS, &xmap, 8 * kc, j0 - 1, row, n, &xfull[xs]);
+                if (xs < 2)
+                    tma_load_4d(sX + (xs + WT_RS) * L::POS + kc * L::CS, &xmap, 8 * kc, j0 - 1, row, n, &xfull[xs]);
             }
-        }
-#pragma unroll
-        for (int k = 0; k < GPT; ++k) {
-            const int e = tid + k * NT;
-            if (e < NGE) {
-                const int p = e / (CO / 8), c8 = e % (CO / 8);
-                vg[k] = *reinterpret_cast<const uint4*>(
-                    &g[(((size_t)n * H + i0 + p / TX) * W + j0 + p % TX) * CO + 8 * c8]);
+            ++xR;
+            if (++xs == WT_RS) {
+                xs = 0;
+                ++xlap;
             }
+            return true;
+        };
+        auto load_g = [&](int n, int row, int j0) {
+            if (glap > 0 && !mbar_wait_bounded(&gempty[gs], (glap - 1) & 1u)) return false;
+            mbar_expect_tx(&gfull[gs], (unsigned)(L::NCG * TCM * 16));
+#pragma unroll
+            for (int kc = 0; kc < L::NCG; ++kc)
+                tma_load_4d(sG + (gs * L::NCG + kc) * L::CS, &gmap, 8 * kc, j0, row, n, &gfull[gs]);
+            ++gR;
+            if (++gs == WT_GS) {
+                gs = 0;
+                ++glap;
+            }
+            return true;
+        };
+        bool ok = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int jt = item % tpr, ri = (item / tpr) % rcn, n = item / (tpr * rcn);
+            const int r0 = ri * rc, nt = min(rc, H - r0), j0 = jt * TCM;
+            ok = load_x(n, r0 - 1, j0) && load_x(n, r0, j0);
+            for (int k = 0; k < nt && ok; ++k) ok = load_x(n, r0 + k + 1, j0) && load_g(n, r0 + k, j0);
         }
-        __syncthreads();  // the previous tile's shared data is no longer read
-#pragma unroll
-        for (int k = 0; k < XPT; ++k) {
-            const int e = tid + k * NT;
-            if (e < NXE) *reinterpret_cast<uint4*>(&sx[(e / (CI / 8)) * PS + 8 * (e % (CI / 8))]) = vx[k];
+        if (!ok) {
+            atomicOr(err, 1u);
+            atomicOr(&s_abort, 1);
         }
+        // copies in flight (the newest row of each slot) land before the CTA exits
+        for (uint32_t R = xR > WT_RS ? xR - WT_RS : 0; R < xR; ++R)
+            mbar_wait_bounded(&xfull[R % WT_RS], (R / WT_RS) & 1u);
+        for (uint32_t R = gR > WT_GS ? gR - WT_GS : 0; R < gR; ++R)
+            mbar_wait_bounded(&gfull[R % WT_GS], (R / WT_GS) & 1u);
+    } else if (tid == 0) {
+        // MMAs: per tile three (one per dx) for each 16-pixel K step
+        const uint64_t ad0 = smem_desc(smem_u32(sX), 128u, L::CS);
+        const uint64_t bd0 = smem_desc(smem_u32(sG), 128u, L::CS);
+        constexpr uint32_t IDESC = idesc_bf16_f32(128, CO) | (1u << 15) | (1u << 16);  // both MN-major
+        uint32_t x_seen = 0, cx = 0, glap = 0;
+        int gs = 0;
+        bool ok = true, first = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int ri = (item / tpr) % rcn, nt = min(rc, H - ri * rc);
+            for (int k = 0; k < nt; ++k) {
+                while (x_seen <= cx + k + 2) {
+                    if (!mbar_wait_bounded(&xfull[x_seen % WT_RS], (x_seen / WT_RS) & 1u)) {
+                        ok = false;
+                        break;
+                    }
+                    ++x_seen;
+                }
+                if (!ok || !mbar_wait_bounded(&gfull[gs], glap & 1u)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t xsl = (cx + k) % WT_RS;
+                const uint64_t ad = ad0 + ((xsl * L::POS) >> 4);
+                const uint64_t bd = bd0 + (((uint32_t)gs * L::NCG * L::CS) >> 4);
 #pragma unroll
-        for (int k = 0; k < GPT; ++k) {
-            const int e = tid + k * NT;
-            if (e < NGE) *reinterpret_cast<uint4*>(&sg[(e / (CO / 8)) * GS + 8 * (e % (CO / 8))]) = vg[k];
-        }
-        __syncthreads();
+                for (int s = 0; s < TCM / 16; ++s) {
+                    const uint32_t acc = (first && s == 0) ? 0u : 1u;
 #pragma unroll
-        for (int q = 0; q < UPW; ++q) {
-            const int u = warp + q * TY;
-            if (u >= UNITS) continue;
-            const int tap = u / (CI / 16), cb = (u % (CI / 16)) * 16;
-            const int ky = tap / 3, kx = tap % 3;
-            // K = 128 pixels of the tile, 16 per MMA (one tile row)
-            for (int ti = 0; ti < TY; ++ti) {
-                const __nv_bfloat16* xr = &sx[((ti + ky) * (TX + 2) + kx) * PS];
-                const __nv_bfloat16* gr = &sg[(ti * TX) * GS];
-                // A[m = c][k = p] = x[p][c]: the transposes of the 8 x 8 blocks
-                // (pixels 0-7 | 8-15) x (channels cb + 0-7 | 8-15)
-                uint32_t a0, a1, a2, a3;
-                ldsm_x4_t(a0, a1, a2, a3, xr + ((lq & 2) ? 8 : 0) * PS + lr * PS + cb + ((lq & 1) ? 8 : 0));
-#pragma unroll
-                for (int f = 0; f < CO / 8; f += 2) {
-                    // B[k = p][n = o] = g[p][o]: transposed blocks (pixels 0-7 |
-                    // 8-15) x (outputs 8f + 0-7 | 8f + 8-15)
-                    uint32_t b0, b1, b2, b3;
-                    ldsm_x4_t(b0, b1, b2, b3, gr + ((lq & 1) ? 8 : 0) * GS + lr * GS + 8 * f + ((lq & 2) ? 8 : 0));
-                    mma_bf16(acc[q][f], a0, a1, a2, a3, b0, b1);
-                    mma_bf16(acc[q][f + 1], a0, a1, a2, a3, b2, b3);
+                    for (int dx = 0; dx < 3; ++dx)
+                        tc_mma_bf16(taddr + (uint32_t)(dx * CO), ad + (uint64_t)(dx + 16 * s), bd + (uint64_t)(16 * s),
+                                    IDESC, acc);
+                }
+                first = false;
+                // this tile is the last reader of gradient row k and input row k
+                // (and, at the item's end, of input rows k + 1 and k + 2)
+                tc_commit(&gempty[gs]);
+                tc_commit(&xempty[xsl]);
+                if (k == nt - 1) {
+                    tc_commit(&xempty[(xsl + 1) % WT_RS]);
+                    tc_commit(&xempty[(xsl + 2) % WT_RS]);
+                }
+                if (++gs == WT_GS) {
+                    gs = 0;
+                    ++glap;
                 }
             }
+            cx += (uint32_t)(nt + 2);
         }
-        // bias gradient: thread (bg, bo) sums output bo over the pixels
-        // bg, bg + BG, ... of each of its tiles, in order
-        for (int p = bg; p < TY * TX; p += BG) bsum += __bfloat162float(sg[p * GS + bo]);
-    }
-#pragma unroll
-    for (int q = 0; q < UPW; ++q) {
-        const int u = warp + q * TY;
-        if (u >= UNITS) continue;
-        const int tap = u / (CI / 16), cb = (u % (CI / 16)) * 16;
-        float* P = part + (size_t)blockIdx.x * 9 * CI * CO + (size_t)tap * CI * CO;
-#pragma unroll
-        for (int f = 0; f < CO / 8; ++f) {
-            const int o = 8 * f + kc;
-            P[(cb + r0) * CO + o] = acc[q][f][0];
-            P[(cb + r0) * CO + o + 1] = acc[q][f][1];
-            P[(cb + r0 + 8) * CO + o] = acc[q][f][2];
-            P[(cb + r0 + 8) * CO + o + 1] = acc[q][f][3];
+        tc_commit(&tdone);
+        if (!mbar_wait_bounded(&tdone, 0u)) ok = false;
+        if (!ok) {
+            atomicOr(err, 1u);
+            atomicOr(&s_abort, 1);
         }
+        if (first) atomicOr(&s_abort, 2);  // no tile: the partials are zero
     }
-    sb[tid] = bsum;
+    tc_fence_before();
     __syncthreads();
-    if (tid < CO) {
-        float b = 0.f;
-        for (int k = 0; k < BG; ++k) b += sb[k * CO + tid];
-        bpart[(size_t)blockIdx.x * CO + tid] = b;
+    __syncwarp();
+    tc_fence_after();
+    const int ab = s_abort;
+    if (!(ab & 1)) {
+        // accumulator row m sits in lane m: chunk m / 8 of the stacked rows
+        const int m = 32 * warp + lane, j = m >> 3, dy = j / L::PCH, kc = j % L::PCH;
+        const int c = 8 * kc + (m & 7);
+        const bool wrow = dy < 3 && kc < L::NCX;
+        const bool brow = m == 8 * L::NCX;  // first ones row (dy = 0)
+        float* P = part + (size_t)blockIdx.x * 9 * CI * CO;
+        float v[16];
+#pragma unroll
+        for (int col = 0; col < 3 * CO; col += 16) {
+            tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)col, v);
+            tmem_ld_wait();
+            if (ab & 2) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.f;
+            }
+            const int dx = col / CO, o0 = col % CO;
+            if (wrow) {
+                float4* dst = reinterpret_cast<float4*>(P + ((size_t)(3 * dy + dx) * CI + c) * CO + o0);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+            }
+            if (brow && dx == 0) {
+#pragma unroll
+                for (int i = 0; i < 16; ++i) bpart[(size_t)blockIdx.x * CO + o0 + i] = v[i];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(taddr, L::TMC);
     }
 }
 
@@ -689,7 +789,6 @@ struct swe_cnn {
     float* yout = nullptr;            // last layer output FP32 [n][h][w][3]
     __nv_bfloat16* gbuf[2] = {};      // gradient ping-pong, BF16 [n][h][w][32]
     int nwg = 0;                      // weight-gradient CTAs the partial buffers hold
-    int nwgv[3] = {0, 0, 0};          // persistent CTAs of k_wgrad<16,32>, <32,32>, <32,16>: one wave
     int ntc = 0;                      // persistent convolution CTAs
     float* part = nullptr;            // weight-gradient partials, one set per such CTA
     float* bpart = nullptr;
@@ -734,12 +833,12 @@ EncodeTiledFn encode_fn() {
 
 // TMA map of a BF16 NHWC image batch [n][h][w][ci]: boxes of 8 channels x
 // (TCM + 2) pixels of one row; reads outside the image return zeros.
-int x_map(CUtensorMap* m, const void* x, int n, int h, int w, int ci) {
+int x_map(CUtensorMap* m, const void* x, int n, int h, int w, int ci, int box_w = TCM + 2) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return cfail(SWE_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const cuuint64_t dims[4] = {(cuuint64_t)ci, (cuuint64_t)w, (cuuint64_t)h, (cuuint64_t)n};
     const cuuint64_t strides[3] = {(cuuint64_t)ci * 2, (cuuint64_t)w * ci * 2, (cuuint64_t)h * w * ci * 2};
-    const cuuint32_t box[4] = {8, (cuuint32_t)(TCM + 2), 1, 1};
+    const cuuint32_t box[4] = {8, (cuuint32_t)box_w, 1, 1};
     const cuuint32_t estr[4] = {1, 1, 1, 1};
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box, estr,
                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -787,6 +886,36 @@ cudaError_t conv_attr() {
                                 (int)conv_smem_bytes<CI, CO>());
 }
 
+// Weight gradient of one layer on the tensor cores: one persistent CTA per
+// SM, items of rows of one 128-pixel column band as for the convolution.
+// Returns the number of CTAs (partial-sum sets) in *nblk.
+template <int CI, int CO>
+int wgrad_tc(swe_cnn* c, const void* x, const void* g, int* nblk) {
+    CUtensorMap xm, gm;
+    int rc = x_map(&xm, x, c->n, c->h, c->w, CI);
+    if (!rc) rc = x_map(&gm, g, c->n, c->h, c->w, CO, TCM);
+    if (rc) return rc;
+    const int slots = c->nwg;
+    const int tpr = (c->w + TCM - 1) / TCM;
+    const long long tiles = (long long)c->n * c->h * tpr;
+    int rows = (int)std::max<long long>(4, (tiles + slots - 1) / slots);
+    rows = std::min(rows, c->h);
+    while (rows < c->h && (long long)c->n * tpr * ((c->h + rows - 1) / rows) > slots) ++rows;
+    const int nitems = c->n * tpr * ((c->h + rows - 1) / rows);
+    const int grid = std::min(nitems, slots);
+    k_wgrad_tc<CI, CO><<<grid, 128, WgTc<CI, CO>::SMEM, c->st>>>(xm, gm, c->part, c->bpart, c->h, c->w, rows, nitems,
+                                                                 c->derr);
+    CKC(cudaGetLastError());
+    *nblk = grid;
+    return SWE_OK;
+}
+
+template <int CI, int CO>
+cudaError_t wgrad_tc_attr() {
+    return cudaFuncSetAttribute(k_wgrad_tc<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)WgTc<CI, CO>::SMEM);
+}
+
 int layer_fwd(swe_cnn* c, int l, const __nv_bfloat16* x, void* out) {
     const float* bias = c->p + c->off_b[l];
     switch (l) {
@@ -827,19 +956,18 @@ int backward_all(swe_cnn* c, const __nv_bfloat16* x, const float* target) {
     // gbuf[0] holds the 16-channel gradient of the last layer's output
     k_mse<<<nb, 256, 0, c->st>>>(c->yout, target, c->gbuf[0], c->lpart, npix, 3, 1.0f / (float)(npix * 3));
     k_sum<<<1, 256, 0, c->st>>>(c->lpart, nb, c->dloss);
-    const dim3 grid(c->w / TX, c->h / TY, c->n), blk(32 * TY);
-    const int ntiles = (int)(grid.x * grid.y * grid.z);
     const __nv_bfloat16* ins[NLAYER] = {x, c->act[1], c->act[2], c->act[3]};
     int cur = 0;
     for (int l = NLAYER - 1; l >= 0; --l) {
         const __nv_bfloat16* gl = c->gbuf[cur];
         // weight gradient of layer l: inputs ins[l] (CIP), output gradient gl
-        const int nblk = c->nwgv[l == 0 ? 0 : l == 3 ? 2 : 1];
+        int nblk = 0, rcw = 0;
         switch (l) {
-            case 0: k_wgrad<16, 32><<<nblk, blk, 0, c->st>>>(ins[0], gl, c->part, c->bpart, c->h, c->w, ntiles); break;
-            case 3: k_wgrad<32, 16><<<nblk, blk, 0, c->st>>>(ins[3], gl, c->part, c->bpart, c->h, c->w, ntiles); break;
-            default: k_wgrad<32, 32><<<nblk, blk, 0, c->st>>>(ins[l], gl, c->part, c->bpart, c->h, c->w, ntiles); break;
+            case 0: rcw = wgrad_tc<16, 32>(c, ins[0], gl, &nblk); break;
+            case 3: rcw = wgrad_tc<32, 16>(c, ins[3], gl, &nblk); break;
+            default: rcw = wgrad_tc<32, 32>(c, ins[l], gl, &nblk); break;
         }
+        if (rcw) return rcw;
         const int nw = 9 * CH[l] * CH[l + 1] + CH[l + 1];
         k_wgrad_reduce<<<(nw + 31) / 32, 256, 0, c->st>>>(c->part, c->bpart, nblk, CIP[l], cog(l), CH[l], CH[l + 1],
                                                            c->g + c->off_w[l], c->g + c->off_b[l]);
@@ -903,29 +1031,18 @@ SWE_API int swe_cnn_create(int32_t n, int32_t h, int32_t w, void* stream, swe_cn
     }
     c->nparam = np;
     const size_t npix = (size_t)n * h * w;
-    const dim3 grid(w / TX, h / TY, n);
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         swe_cnn_destroy(c);
         return cfail(SWE_ERR_CUDA, "device attributes");
     }
-    c->nwg = (int)std::min<size_t>((size_t)grid.x * grid.y * grid.z, (size_t)4 * nsm);
-    {
-        int occ[3] = {0, 0, 0};
-        const int nt = 32 * TY;
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], k_wgrad<16, 32>, nt, 0) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], k_wgrad<32, 32>, nt, 0) != cudaSuccess ||
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], k_wgrad<32, 16>, nt, 0) != cudaSuccess) {
-            swe_cnn_destroy(c);
-            return cfail(SWE_ERR_CUDA, "weight-gradient occupancy");
-        }
-        for (int v = 0; v < 3; ++v) c->nwgv[v] = std::max(1, std::min(c->nwg, std::max(1, occ[v]) * nsm));
-    }
+    c->nwg = nsm;  // weight-gradient CTAs: one per SM
     c->ntc = 3 * nsm;  // three 71 KB CTAs fit an SM
     if (conv_attr<16, 32, MODE_RELU_BF16>() != cudaSuccess || conv_attr<32, 32, MODE_RELU_BF16>() != cudaSuccess ||
         conv_attr<32, 16, MODE_LINEAR_F32>() != cudaSuccess || conv_attr<16, 32, MODE_MASK_BF16>() != cudaSuccess ||
-        conv_attr<32, 32, MODE_MASK_BF16>() != cudaSuccess) {
+        conv_attr<32, 32, MODE_MASK_BF16>() != cudaSuccess || wgrad_tc_attr<16, 32>() != cudaSuccess ||
+        wgrad_tc_attr<32, 32>() != cudaSuccess || wgrad_tc_attr<32, 16>() != cudaSuccess) {
         swe_cnn_destroy(c);
         return cfail(SWE_ERR_CUDA, "convolution kernel shared-memory size");
     }
