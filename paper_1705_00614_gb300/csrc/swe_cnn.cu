@@ -251,30 +251,35 @@ __global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMa
 
 // Weight gradient on the fifth-generation tensor cores.  For a layer with
 // weights W[dy][dx][c][o] the gradient is
-//   P[dy][dx][c][o] = sum over pixels p of x[p + (dy - 1, dx - 1)][c] g[p][o],
-// for each column shift dx one GEMM of M = (dy, c) (the three input rows of a
-// 128-pixel row tile stacked, with a row of ones after each row's channels:
-// 3 (CI + 8) rows, padded to 128) by N = o over K = pixels, 16 per
-// instruction.  The ones rows give the bias gradient sum_p g[p][o].  Both
-// operands are read in the MN-major layout straight from NHWC rows staged by
-// TMA ([chunk of 8 channels][pixel][8], 16 bytes per pixel and chunk): the
-// shift dx moves the start address by 16 bytes, the K groups of 8 pixels are
-// 128 bytes apart (LBO) and the channel chunks one chunk apart (SBO).
-// Stacking dy on M needs the three rows of a tile in consecutive row
-// positions, so the input rows stream through a ring of WT_RS positions
-// followed by two shadow positions that take second copies of the rows in
-// positions 0 and 1, and spare positions that the padding rows of M read
-// (finite data in accumulator rows that are never stored).
+//   P[dy][dx][c][o] = sum over pixels p of x[p + (dy - 1, dx - 1)][c] g[p][o]
+//                   = sum over pixels q of x[q + (dy - 1, 0)][c] g[q - (0, dx - 1)][o],
+// one GEMM per 16-pixel K step of M = (dy, c) -- the three input rows of a
+// 128-pixel row tile stacked, each row's channels followed by a chunk of
+// ones (3 (CI + 8) rows, padded to 128) -- by N = (dx, o), the tile's
+// output-gradient row in three copies shifted by 1 - dx pixels.  The ones
+// rows give the bias gradient sum_p g[p][o].  Both operands are in the
+// MN-major layout without swizzling ([chunk of 8 channels][pixel][8], 16
+// bytes per pixel and chunk; K groups of 8 pixels 128 bytes apart (LBO),
+// channel chunks one chunk apart (SBO)).  Input rows come straight from TMA:
+// stacking dy on M needs a tile's three rows in consecutive row positions,
+// so they stream through a ring of WT_RS positions followed by two shadow
+// positions (second copies of the rows in positions 0 and 1) and spare
+// positions that the padding rows of M read (finite data in accumulator
+// rows that are never stored).  Output-gradient rows land by TMA in a raw
+// ring (130 pixels from one left of the tile); warps 2 and 3 write the three
+// shifted copies into the operand ring with plain shared-memory copies.
 //
 // A persistent CTA walks items of rows of one 128-pixel column band, keeps
 // its accumulators in tensor memory and writes its partial sums once at the
-// end (reduced over CTAs in a fixed order by k_wgrad_reduce).  One thread
-// issues the copies, one the MMAs; a row slot is released to the copies by
-// tcgen05.commit after the last tile that reads it.  Waits are bounded; on a
-// timeout *err is set, both threads wait (bounded) for what they issued, the
-// CTA frees its tensor memory and writes no partials.
-constexpr int WT_RS = 10;  // input row positions of the ring
-constexpr int WT_GS = 8;   // output-gradient row slots
+// end (reduced over CTAs in a fixed order by k_wgrad_reduce).  Thread 32
+// issues the copies, warps 2-3 build the shifted operands, thread 0 issues
+// the MMAs; full/empty mbarriers join them (tcgen05.commit releases what
+// the MMAs read).  Waits are bounded; on a timeout *err is set, every role
+// waits (bounded) for what it issued, the CTA frees its tensor memory and
+// writes no partials.
+constexpr int WT_RS = 8;  // input row positions of the ring
+constexpr int WT_GR = 4;  // raw output-gradient row slots
+constexpr int WT_GS = 2;  // shifted output-gradient operand slots
 
 template <int CI, int CO>
 struct WgTc {
@@ -282,14 +287,21 @@ struct WgTc {
     static constexpr int PCH = NCX + 1;               // chunks per row position (channels, ones)
     static constexpr int MROWS = 3 * 8 * PCH;         // real rows of M
     static constexpr int NPOS = WT_RS + 2 + (16 - 3 * PCH + PCH - 1) / PCH;
-    static constexpr int TMC = 3 * CO <= 64 ? 64 : 128;  // accumulator columns (three shifts)
-    static constexpr uint32_t CS = TC_APAD * 16;      // chunk stride
+    static constexpr int N = 3 * CO;                  // MMA N: (dx, o)
+    static constexpr int TMC = N <= 64 ? 64 : 128;    // accumulator columns
+    static constexpr uint32_t CS = TC_APAD * 16;      // chunk stride of the TMA rings (136 pixels)
+    static constexpr uint32_t CSB = TCM * 16;         // chunk stride of the shifted operand (128 pixels)
     static constexpr uint32_t POS = PCH * CS;         // row-position stride
     static constexpr uint32_t XBYTES = (uint32_t)NPOS * POS;
-    static constexpr uint32_t GBYTES = (uint32_t)(WT_GS * NCG) * CS;
-    static constexpr size_t SMEM = (size_t)XBYTES + GBYTES + 128;
+    static constexpr uint32_t RSLOT = (uint32_t)NCG * CS;
+    static constexpr uint32_t SSLOT = (uint32_t)(3 * NCG) * CSB;
+    static constexpr uint32_t RBYTES = WT_GR * RSLOT;
+    static constexpr uint32_t SBYTES = WT_GS * SSLOT;
+    static constexpr size_t SMEM = (size_t)XBYTES + RBYTES + SBYTES + 128;
+    static constexpr int CPY = 3 * NCG * TCM / 64;    // 16-byte copies per copy thread and row
     static_assert(MROWS <= 128, "M");
     static_assert(CO == 16 || CO == 32, "MMA N");
+    static_assert((3 * NCG * TCM) % 64 == 0, "copy split");
 };
 
 template <int CI, int CO>
@@ -300,15 +312,17 @@ __global__ void __launch_bounds__(128, 1)
     using L = WgTc<CI, CO>;
     extern __shared__ __align__(128) unsigned char wsm[];
     unsigned char* const sX = wsm + ((128u - (smem_u32(wsm) & 127u)) & 127u);
-    unsigned char* const sG = sX + L::XBYTES;
+    unsigned char* const sR = sX + L::XBYTES;
+    unsigned char* const sS = sR + L::RBYTES;
     __shared__ __align__(8) unsigned long long xfull[WT_RS], xempty[WT_RS];
-    __shared__ __align__(8) unsigned long long gfull[WT_GS], gempty[WT_GS];
+    __shared__ __align__(8) unsigned long long rfull[WT_GR], rempty[WT_GR];
+    __shared__ __align__(8) unsigned long long sfull[WT_GS], sempty[WT_GS];
     __shared__ __align__(8) unsigned long long tdone;
     __shared__ uint32_t s_taddr;
     __shared__ int s_abort;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    // zero both rings, then ones in the last chunk of every row position
-    for (uint32_t e = tid; e < (L::XBYTES + L::GBYTES) / 16; e += 128)
+    // zero the input ring, then ones in the last chunk of every row position
+    for (uint32_t e = tid; e < L::XBYTES / 16; e += 128)
         *reinterpret_cast<uint4*>(sX + 16 * e) = make_uint4(0, 0, 0, 0);
     __syncthreads();
     const uint32_t one2 = 0x3F803F80u;  // two BF16 ones
@@ -325,9 +339,13 @@ __global__ void __launch_bounds__(128, 1)
             mbar_init(&xfull[q], 1);
             mbar_init(&xempty[q], 1);
         }
+        for (int q = 0; q < WT_GR; ++q) {
+            mbar_init(&rfull[q], 1);
+            mbar_init(&rempty[q], 64);
+        }
         for (int q = 0; q < WT_GS; ++q) {
-            mbar_init(&gfull[q], 1);
-            mbar_init(&gempty[q], 1);
+            mbar_init(&sfull[q], 64);
+            mbar_init(&sempty[q], 1);
         }
         mbar_init(&tdone, 1);
         fence_mbar_init();
@@ -343,7 +361,7 @@ __global__ void __launch_bounds__(128, 1)
     if (tid == 32) {
         // copies: per item the input rows r0 - 1 and r0, then per output row
         // k the input row r0 + k + 1 and the gradient row r0 + k (the order
-        // the MMAs consume them); a slot is refilled once it is released
+        // they are consumed in); a slot is refilled once it is released
         uint32_t xR = 0, gR = 0, xlap = 0, glap = 0;
         int xs = 0, gs = 0;
         auto load_x = [&](int n, int row, int j0) {
@@ -364,13 +382,13 @@ __global__ void __launch_bounds__(128, 1)
             return true;
         };
         auto load_g = [&](int n, int row, int j0) {
-            if (glap > 0 && !mbar_wait_bounded(&gempty[gs], (glap - 1) & 1u)) return false;
-            mbar_expect_tx(&gfull[gs], (unsigned)(L::NCG * TCM * 16));
+            if (glap > 0 && !mbar_wait_bounded(&rempty[gs], (glap - 1) & 1u)) return false;
+            mbar_expect_tx(&rfull[gs], (unsigned)(L::NCG * (TCM + 2) * 16));
 #pragma unroll
             for (int kc = 0; kc < L::NCG; ++kc)
-                tma_load_4d(sG + (gs * L::NCG + kc) * L::CS, &gmap, 8 * kc, j0, row, n, &gfull[gs]);
+                tma_load_4d(sR + gs * L::RSLOT + kc * L::CS, &gmap, 8 * kc, j0 - 1, row, n, &rfull[gs]);
             ++gR;
-            if (++gs == WT_GS) {
+            if (++gs == WT_GR) {
                 gs = 0;
                 ++glap;
             }
@@ -390,19 +408,53 @@ __global__ void __launch_bounds__(128, 1)
         // copies in flight (the newest row of each slot) land before the CTA exits
         for (uint32_t R = xR > WT_RS ? xR - WT_RS : 0; R < xR; ++R)
             mbar_wait_bounded(&xfull[R % WT_RS], (R / WT_RS) & 1u);
-        for (uint32_t R = gR > WT_GS ? gR - WT_GS : 0; R < gR; ++R)
-            mbar_wait_bounded(&gfull[R % WT_GS], (R / WT_GS) & 1u);
+        for (uint32_t R = gR > WT_GR ? gR - WT_GR : 0; R < gR; ++R)
+            mbar_wait_bounded(&rfull[R % WT_GR], (R / WT_GR) & 1u);
+    } else if (warp >= 2) {
+        // shifted operands: copy dx of gradient row R holds raw pixels
+        // 2 - dx .. 129 - dx (the raw row starts one pixel left of the tile)
+        const int ct = tid - 64;
+        uint32_t R = 0;
+        bool ok = true;
+        for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
+            const int ri = (item / tpr) % rcn, nt = min(rc, H - ri * rc);
+            for (int k = 0; k < nt; ++k, ++R) {
+                const uint32_t rs = R % WT_GR, ss = R % WT_GS;
+                if (!mbar_wait_bounded(&rfull[rs], (R / WT_GR) & 1u) ||
+                    (R >= WT_GS && !mbar_wait_bounded(&sempty[ss], ((R / WT_GS) - 1) & 1u))) {
+                    ok = false;
+                    break;
+                }
+                const unsigned char* src = sR + rs * L::RSLOT;
+                unsigned char* dst = sS + ss * L::SSLOT;
+#pragma unroll
+                for (int i = 0; i < L::CPY; ++i) {
+                    const int e = ct + 64 * i;
+                    const int dx = e / (L::NCG * TCM), oc = (e / TCM) % L::NCG, p = e % TCM;
+                    *reinterpret_cast<uint4*>(dst + (uint32_t)(dx * L::NCG + oc) * L::CSB + 16u * p) =
+                        *reinterpret_cast<const uint4*>(src + (uint32_t)oc * L::CS + 16u * (uint32_t)(p + 2 - dx));
+                }
+                fence_proxy_async();  // the stores precede the MMAs' reads
+                mbar_arrive(&rempty[rs]);
+                mbar_arrive(&sfull[ss]);
+            }
+        }
+        if (!ok) {
+            atomicOr(err, 1u);
+            atomicOr(&s_abort, 1);
+        }
     } else if (tid == 0) {
-        // MMAs: per tile three (one per dx) for each 16-pixel K step
-        const uint64_t ad0 = smem_desc(smem_u32(sX), 128u, L::CS);
-        const uint64_t bd0 = smem_desc(smem_u32(sG), 128u, L::CS);
-        constexpr uint32_t IDESC = idesc_bf16_f32(128, CO) | (1u << 15) | (1u << 16);  // both MN-major
-        uint32_t x_seen = 0, cx = 0, glap = 0;
-        int gs = 0;
+        // MMAs: one per 16-pixel K step, M = the stacked input rows (read
+        // from pixel 1 of the row positions: the tile's own pixels), N = the
+        // three shifted gradient copies
+        const uint64_t ad0 = smem_desc(smem_u32(sX) + 16u, 128u, L::CS);
+        const uint64_t bd0 = smem_desc(smem_u32(sS), 128u, L::CSB);
+        constexpr uint32_t IDESC = idesc_bf16_f32(128, L::N) | (1u << 15) | (1u << 16);  // both MN-major
+        uint32_t x_seen = 0, cx = 0, R = 0;
         bool ok = true, first = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
             const int ri = (item / tpr) % rcn, nt = min(rc, H - ri * rc);
-            for (int k = 0; k < nt; ++k) {
+            for (int k = 0; k < nt; ++k, ++R) {
                 while (x_seen <= cx + k + 2) {
                     if (!mbar_wait_bounded(&xfull[x_seen % WT_RS], (x_seen / WT_RS) & 1u)) {
                         ok = false;
@@ -410,34 +462,27 @@ __global__ void __launch_bounds__(128, 1)
                     }
                     ++x_seen;
                 }
-                if (!ok || !mbar_wait_bounded(&gfull[gs], glap & 1u)) {
+                const uint32_t ss = R % WT_GS;
+                if (!ok || !mbar_wait_bounded(&sfull[ss], (R / WT_GS) & 1u)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
                 const uint32_t xsl = (cx + k) % WT_RS;
                 const uint64_t ad = ad0 + ((xsl * L::POS) >> 4);
-                const uint64_t bd = bd0 + (((uint32_t)gs * L::NCG * L::CS) >> 4);
+                const uint64_t bd = bd0 + ((ss * L::SSLOT) >> 4);
 #pragma unroll
-                for (int s = 0; s < TCM / 16; ++s) {
-                    const uint32_t acc = (first && s == 0) ? 0u : 1u;
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx)
-                        tc_mma_bf16(taddr + (uint32_t)(dx * CO), ad + (uint64_t)(dx + 16 * s), bd + (uint64_t)(16 * s),
-                                    IDESC, acc);
-                }
+                for (int s = 0; s < TCM / 16; ++s)
+                    tc_mma_bf16(taddr, ad + (uint64_t)(16 * s), bd + (uint64_t)(16 * s), IDESC,
+                                (first && s == 0) ? 0u : 1u);
                 first = false;
-                // this tile is the last reader of gradient row k and input row k
-                // (and, at the item's end, of input rows k + 1 and k + 2)
-                tc_commit(&gempty[gs]);
+                // this tile is the last reader of its gradient copies and of
+                // input row k (and, at the item's end, of input rows k + 1, k + 2)
+                tc_commit(&sempty[ss]);
                 tc_commit(&xempty[xsl]);
                 if (k == nt - 1) {
                     tc_commit(&xempty[(xsl + 1) % WT_RS]);
                     tc_commit(&xempty[(xsl + 2) % WT_RS]);
-                }
-                if (++gs == WT_GS) {
-                    gs = 0;
-                    ++glap;
                 }
             }
             cx += (uint32_t)(nt + 2);
@@ -456,7 +501,8 @@ __global__ void __launch_bounds__(128, 1)
     tc_fence_after();
     const int ab = s_abort;
     if (!(ab & 1)) {
-        // accumulator row m sits in lane m: chunk m / 8 of the stacked rows
+        // accumulator row m sits in lane m: chunk m / 8 of the stacked rows;
+        // column dx * CO + o
         const int m = 32 * warp + lane, j = m >> 3, dy = j / L::PCH, kc = j % L::PCH;
         const int c = 8 * kc + (m & 7);
         const bool wrow = dy < 3 && kc < L::NCX;
@@ -464,7 +510,7 @@ __global__ void __launch_bounds__(128, 1)
         float* P = part + (size_t)blockIdx.x * 9 * CI * CO;
         float v[16];
 #pragma unroll
-        for (int col = 0; col < 3 * CO; col += 16) {
+        for (int col = 0; col < L::N; col += 16) {
             tmem_ld16(taddr + ((uint32_t)(32 * warp) << 16) + (uint32_t)col, v);
             tmem_ld_wait();
             if (ab & 2) {
@@ -477,7 +523,7 @@ __global__ void __launch_bounds__(128, 1)
 #pragma unroll
                 for (int i = 0; i < 4; ++i) dst[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
             }
-            if (brow && dx == 0) {
+            if (brow && dx == 1) {
 #pragma unroll
                 for (int i = 0; i < 16; ++i) bpart[(size_t)blockIdx.x * CO + o0 + i] = v[i];
             }
@@ -893,7 +939,7 @@ template <int CI, int CO>
 int wgrad_tc(swe_cnn* c, const void* x, const void* g, int* nblk) {
     CUtensorMap xm, gm;
     int rc = x_map(&xm, x, c->n, c->h, c->w, CI);
-    if (!rc) rc = x_map(&gm, g, c->n, c->h, c->w, CO, TCM);
+    if (!rc) rc = x_map(&gm, g, c->n, c->h, c->w, CO);
     if (rc) return rc;
     const int slots = c->nwg;
     const int tpr = (c->w + TCM - 1) / TCM;
