@@ -277,33 +277,6 @@ __global__ void __launch_bounds__(128) k_conv(const __grid_constant__ CUtensorMa
 // the MMAs read).  Waits are bounded; on a timeout *err is set, every role
 // waits (bounded) for what it issued, the CTA frees its tensor memory and
 // writes no partials.
-constexpr int WT_RS = 8;  // input row positions of the ring
-constexpr int WT_GR = 4;  // raw output-gradient row slots
-constexpr int WT_GS = 2;  // shifted output-gradient operand slots
-
-template <int CI, int CO>
-struct WgTc {
-    static constexpr int NCX = CI / 8, NCG = CO / 8;  // channel chunks of x and g
-    static constexpr int PCH = NCX + 1;               // chunks per row position (channels, ones)
-    static constexpr int MROWS = 3 * 8 * PCH;         // real rows of M
-    static constexpr int NPOS = WT_RS + 2 + (16 - 3 * PCH + PCH - 1) / PCH;
-    static constexpr int N = 3 * CO;                  // MMA N: (dx, o)
-    static constexpr int TMC = N <= 64 ? 64 : 128;    // accumulator columns
-    static constexpr uint32_t CS = TC_APAD * 16;      // chunk stride of the TMA rings (136 pixels)
-    static constexpr uint32_t CSB = TCM * 16;         // chunk stride of the shifted operand (128 pixels)
-    static constexpr uint32_t POS = PCH * CS;         // row-position stride
-    static constexpr uint32_t XBYTES = (uint32_t)NPOS * POS;
-    static constexpr uint32_t RSLOT = (uint32_t)NCG * CS;
-    static constexpr uint32_t SSLOT = (uint32_t)(3 * NCG) * CSB;
-    static constexpr uint32_t RBYTES = WT_GR * RSLOT;
-    static constexpr uint32_t SBYTES = WT_GS * SSLOT;
-    static constexpr size_t SMEM = (size_t)XBYTES + RBYTES + SBYTES + 128;
-    static constexpr int CPY = 3 * NCG * TCM / 64;    // 16-byte copies per copy thread and row
-    static_assert(MROWS <= 128, "M");
-    static_assert(CO == 16 || CO == 32, "MMA N");
-    static_assert((3 * NCG * TCM) % 64 == 0, "copy split");
-};
-
 template <int CI, int CO>
 __global__ void __launch_bounds__(128, 1)
     k_wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap gmap,
@@ -328,7 +301,7 @@ __global__ void __launch_bounds__(128, 1)
     const uint32_t one2 = 0x3F803F80u;  // two BF16 ones
     for (uint32_t e = tid; e < (uint32_t)L::NPOS * TC_APAD; e += 128) {
         const uint32_t pos = e / TC_APAD, px = e % TC_APAD;
-        *reinterpret_cast<uint4*>(sX + pos * L::POS + L::NCX * L::CS + 16 * px) = make_uint4(one2, one2, one2, one2);
+        *reinterpret_cast<uint4*>(sX + wt_x_stage<CI, CO>((int)pos, L::NCX, (int)px)) = make_uint4(one2, one2, one2, one2);
     }
     if (warp == 0) {
         tmem_alloc(&s_taddr, L::TMC);
@@ -370,9 +343,9 @@ __global__ void __launch_bounds__(128, 1)
             mbar_expect_tx(&xfull[xs], xs < 2 ? 2u * bytes : bytes);
 #pragma unroll
             for (int kc = 0; kc < L::NCX; ++kc) {
-                tma_load_4d(sX + xs * L::POS + kc * L::CS, &xmap, 8 * kc, j0 - 1, row, n, &xfull[xs]);
+                tma_load_4d(sX + wt_x_stage<CI, CO>(xs, kc, 0), &xmap, 8 * kc, j0 - 1, row, n, &xfull[xs]);
                 if (xs < 2)
-                    tma_load_4d(sX + (xs + WT_RS) * L::POS + kc * L::CS, &xmap, 8 * kc, j0 - 1, row, n, &xfull[xs]);
+                    tma_load_4d(sX + wt_x_stage<CI, CO>(xs + WT_RS, kc, 0), &xmap, 8 * kc, j0 - 1, row, n, &xfull[xs]);
             }
             ++xR;
             if (++xs == WT_RS) {
@@ -386,7 +359,7 @@ __global__ void __launch_bounds__(128, 1)
             mbar_expect_tx(&rfull[gs], (unsigned)(L::NCG * (TCM + 2) * 16));
 #pragma unroll
             for (int kc = 0; kc < L::NCG; ++kc)
-                tma_load_4d(sR + gs * L::RSLOT + kc * L::CS, &gmap, 8 * kc, j0 - 1, row, n, &rfull[gs]);
+                tma_load_4d(sR + wt_raw_stage<CI, CO>(gs, kc, 0), &gmap, 8 * kc, j0 - 1, row, n, &rfull[gs]);
             ++gR;
             if (++gs == WT_GR) {
                 gs = 0;
@@ -413,7 +386,7 @@ __global__ void __launch_bounds__(128, 1)
     } else if (warp >= 2) {
         // shifted operands: copy dx of gradient row R holds raw pixels
         // 2 - dx .. 129 - dx (the raw row starts one pixel left of the tile)
-        const int ct = tid - 64;
+        const int ct = tid - 64;  // WT_COPY_THREADS copy threads
         uint32_t R = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -425,14 +398,12 @@ __global__ void __launch_bounds__(128, 1)
                     ok = false;
                     break;
                 }
-                const unsigned char* src = sR + rs * L::RSLOT;
-                unsigned char* dst = sS + ss * L::SSLOT;
 #pragma unroll
                 for (int i = 0; i < L::CPY; ++i) {
-                    const int e = ct + 64 * i;
-                    const int dx = e / (L::NCG * TCM), oc = (e / TCM) % L::NCG, p = e % TCM;
-                    *reinterpret_cast<uint4*>(dst + (uint32_t)(dx * L::NCG + oc) * L::CSB + 16u * p) =
-                        *reinterpret_cast<const uint4*>(src + (uint32_t)oc * L::CS + 16u * (uint32_t)(p + 2 - dx));
+                    int dx, oc, p;
+                    wt_copy_index<CI, CO>(ct + WT_COPY_THREADS * i, dx, oc, p);
+                    *reinterpret_cast<uint4*>(sS + wt_s_stage<CI, CO>((int)ss, dx, oc, p)) =
+                        *reinterpret_cast<const uint4*>(sR + wt_raw_stage<CI, CO>((int)rs, oc, wt_copy_src(dx, p)));
                 }
                 fence_proxy_async();  // the stores precede the MMAs' reads
                 mbar_arrive(&rempty[rs]);
@@ -447,9 +418,8 @@ __global__ void __launch_bounds__(128, 1)
         // MMAs: one per 16-pixel K step, M = the stacked input rows (read
         // from pixel 1 of the row positions: the tile's own pixels), N = the
         // three shifted gradient copies
-        const uint64_t ad0 = smem_desc(smem_u32(sX) + 16u, 128u, L::CS);
-        const uint64_t bd0 = smem_desc(smem_u32(sS), 128u, L::CSB);
-        constexpr uint32_t IDESC = idesc_bf16_f32(128, L::N) | (1u << 15) | (1u << 16);  // both MN-major
+        const uint32_t xbase = smem_u32(sX), sbase = smem_u32(sS);
+        constexpr uint32_t IDESC = wt_idesc<CO>();
         uint32_t x_seen = 0, cx = 0, R = 0;
         bool ok = true, first = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
@@ -469,12 +439,11 @@ __global__ void __launch_bounds__(128, 1)
                 }
                 tc_fence_after();
                 const uint32_t xsl = (cx + k) % WT_RS;
-                const uint64_t ad = ad0 + ((xsl * L::POS) >> 4);
-                const uint64_t bd = bd0 + ((ss * L::SSLOT) >> 4);
+                const uint64_t ad = wt_a_desc<CI, CO>(xbase, (int)xsl);
+                const uint64_t bd = wt_b_desc<CI, CO>(sbase, (int)ss);
 #pragma unroll
                 for (int s = 0; s < TCM / 16; ++s)
-                    tc_mma_bf16(taddr, ad + (uint64_t)(16 * s), bd + (uint64_t)(16 * s), IDESC,
-                                (first && s == 0) ? 0u : 1u);
+                    tc_mma_bf16(taddr, ad + wt_kstep(s), bd + wt_kstep(s), IDESC, (first && s == 0) ? 0u : 1u);
                 first = false;
                 // this tile is the last reader of its gradient copies and of
                 // input row k (and, at the item's end, of input rows k + 1, k + 2)
@@ -503,7 +472,9 @@ __global__ void __launch_bounds__(128, 1)
     if (!(ab & 1)) {
         // accumulator row m sits in lane m: chunk m / 8 of the stacked rows;
         // column dx * CO + o
-        const int m = 32 * warp + lane, j = m >> 3, dy = j / L::PCH, kc = j % L::PCH;
+        const int m = 32 * warp + lane;
+        int dy, kc;
+        wt_row<CI, CO>(m, dy, kc);
         const int c = 8 * kc + (m & 7);
         const bool wrow = dy < 3 && kc < L::NCX;
         const bool brow = m == 8 * L::NCX;  // first ones row (dy = 0)

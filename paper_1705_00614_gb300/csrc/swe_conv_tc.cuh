@@ -77,4 +77,97 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// ---- Weight gradient (k_wgrad_tc) ----
+// Per 16-pixel K step one MMA: M = (dy, c), the three input rows of a tile
+// stacked, each row's NCX channel chunks followed by a chunk of ones
+// (3 (CI + 8) rows, padded to 128); N = (dx, o), three copies of the tile's
+// output-gradient row shifted by 1 - dx pixels.  Both operands MN-major
+// without swizzling: element (mn, k) at start + (mn / 8) * SBO + (k / 8) *
+// LBO + (k % 8) * 16 + (mn % 8) * 2, LBO = 128 (8 pixels), SBO = the chunk
+// stride.  Input rows: a ring of WT_RS row positions, two shadow positions
+// (positions WT_RS and WT_RS + 1 hold second copies of the rows in 0 and 1)
+// and spare positions for the padding rows of M; per position NCX chunks
+// of TC_APAD pixels (pixel 0 is one left of the tile) and the ones chunk.
+// Output-gradient rows: a raw ring of WT_GR slots (NCG chunks of TC_APAD
+// pixels, pixel 0 one left of the tile) and WT_GS slots of shifted copies
+// (3 NCG chunks of TCM pixels).
+constexpr int WT_RS = 8;  // input row positions of the ring
+constexpr int WT_GR = 4;  // raw output-gradient row slots
+constexpr int WT_GS = 2;  // shifted output-gradient operand slots
+constexpr int WT_COPY_THREADS = 64;  // threads that write the shifted copies
+
+template <int CI, int CO>
+struct WgTc {
+    static constexpr int NCX = CI / 8, NCG = CO / 8;  // channel chunks of x and g
+    static constexpr int PCH = NCX + 1;               // chunks per row position (channels, ones)
+    static constexpr int MROWS = 3 * 8 * PCH;         // real rows of M
+    static constexpr int NPOS = WT_RS + 2 + (16 - 3 * PCH + PCH - 1) / PCH;
+    static constexpr int N = 3 * CO;                  // MMA N: (dx, o)
+    static constexpr int TMC = N <= 64 ? 64 : 128;    // accumulator columns
+    static constexpr uint32_t CS = TC_APAD * 16;      // chunk stride of the TMA rings
+    static constexpr uint32_t CSB = TCM * 16;         // chunk stride of the shifted copies
+    static constexpr uint32_t POS = PCH * CS;         // row-position stride
+    static constexpr uint32_t XBYTES = (uint32_t)NPOS * POS;
+    static constexpr uint32_t RSLOT = (uint32_t)NCG * CS;
+    static constexpr uint32_t SSLOT = (uint32_t)(3 * NCG) * CSB;
+    static constexpr uint32_t RBYTES = WT_GR * RSLOT;
+    static constexpr uint32_t SBYTES = WT_GS * SSLOT;
+    static constexpr uint32_t SMEM = XBYTES + RBYTES + SBYTES + 128;
+    static constexpr int CPY = 3 * NCG * TCM / WT_COPY_THREADS;  // 16-byte copies per copy thread and row
+    static_assert(MROWS <= 128, "M");
+    static_assert(CO == 16 || CO == 32, "MMA N");
+    static_assert((3 * NCG * TCM) % WT_COPY_THREADS == 0, "copy split");
+};
+
+// Byte offsets: 8 channels of input pixel p in row position pos, chunk kc
+// (kc = NCX: the ones chunk); of raw gradient pixel u in slot rs, chunk oc;
+// of shifted copy dx, tile pixel p in slot ss, chunk oc.
+template <int CI, int CO>
+__host__ __device__ constexpr uint32_t wt_x_stage(int pos, int kc, int p) {
+    return (uint32_t)pos * WgTc<CI, CO>::POS + (uint32_t)kc * WgTc<CI, CO>::CS + 16u * (uint32_t)p;
+}
+template <int CI, int CO>
+__host__ __device__ constexpr uint32_t wt_raw_stage(int rs, int oc, int u) {
+    return (uint32_t)rs * WgTc<CI, CO>::RSLOT + (uint32_t)oc * WgTc<CI, CO>::CS + 16u * (uint32_t)u;
+}
+template <int CI, int CO>
+__host__ __device__ constexpr uint32_t wt_s_stage(int ss, int dx, int oc, int p) {
+    return (uint32_t)ss * WgTc<CI, CO>::SSLOT + (uint32_t)(dx * WgTc<CI, CO>::NCG + oc) * WgTc<CI, CO>::CSB +
+           16u * (uint32_t)p;
+}
+// Copy e (0 .. 3 NCG TCM - 1) of a gradient row: shift dx, chunk oc, tile
+// pixel p; it takes raw pixel p + 2 - dx (gradient pixel j0 + p + 1 - dx).
+template <int CI, int CO>
+__host__ __device__ constexpr void wt_copy_index(int e, int& dx, int& oc, int& p) {
+    dx = e / (WgTc<CI, CO>::NCG * TCM);
+    oc = (e / TCM) % WgTc<CI, CO>::NCG;
+    p = e % TCM;
+}
+__host__ __device__ constexpr int wt_copy_src(int dx, int p) { return p + 2 - dx; }
+// Descriptors of K step 0 for the tile whose first input row sits in ring
+// slot `slot` (the tile's own pixels start at pixel 1), and for shifted
+// slot ss; K step s adds wt_kstep(s) (256 bytes = 16 pixels).
+template <int CI, int CO>
+__host__ __device__ constexpr uint64_t wt_a_desc(uint32_t xbase, int slot) {
+    return smem_desc(xbase + wt_x_stage<CI, CO>(slot, 0, 1), 128u, WgTc<CI, CO>::CS);
+}
+template <int CI, int CO>
+__host__ __device__ constexpr uint64_t wt_b_desc(uint32_t sbase, int ss) {
+    return smem_desc(sbase + wt_s_stage<CI, CO>(ss, 0, 0, 0), 128u, WgTc<CI, CO>::CSB);
+}
+__host__ __device__ constexpr uint64_t wt_kstep(int s) { return (uint64_t)(16 * s); }
+// Instruction descriptor: M = 128, N = 3 CO, both operands MN-major
+// (transpose bits 15 and 16).
+template <int CO>
+__host__ __device__ constexpr uint32_t wt_idesc() {
+    return idesc_bf16_f32(128, 3 * CO) | (1u << 15) | (1u << 16);
+}
+// Accumulator row m: input-row offset dy and chunk kc of the stacked rows
+// (kc = NCX: a ones row; dy >= 3: padding).
+template <int CI, int CO>
+__host__ __device__ constexpr void wt_row(int m, int& dy, int& kc) {
+    dy = (m >> 3) / WgTc<CI, CO>::PCH;
+    kc = (m >> 3) % WgTc<CI, CO>::PCH;
+}
+
 }  // namespace swe
