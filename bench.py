@@ -28,6 +28,13 @@ Prints one JSON line:
                clock sampled during the timed region
   cpu_baseline the FP64 CPU oracle on a bounded crop of the same workload,
                one process per host core
+  secondary    (one GPU, default workload, unless --no-secondary) short runs
+               of the other measured paths, after the timed region above and
+               each in its own: the batched ensemble (64 scenarios of
+               512^2-2048^2, 500 steps with gate toggles; the HBM roofline of
+               k_fused_batch) and the closure network's training step on a
+               2048^2 grid (the BF16 tensor roofline); a path that fails
+               reports its error instead of a value
 ``--impl reference`` times the oracle alone on the host cores (the same way).
 """
 import argparse
@@ -129,7 +136,7 @@ def flooded_ensemble(n, rank=0, world=1):
     return out, gates
 
 
-def run_ensemble(args, torch, swe, stream, rank, world):
+def run_ensemble(args, torch, swe, stream, rank, world, emit=True):
     """Batched ensemble: all of this rank's scenarios advance in one
     persistent launch per step (CUDA graph of K steps); ranks run disjoint
     scenarios (n each), value counts every rank's cells over the slowest
@@ -188,7 +195,10 @@ def run_ensemble(args, torch, swe, stream, rank, world):
                              "frac": achieved / peak, "traffic": None, "kernel": "k_fused_batch<float>",
                              "algorithmic_bytes_per_cell": BYTES_PER_CELL[args.precision]},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": args.steps, "clocks": clk.summary()}
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
+        return line
+    return None
 
 
 # algorithmic FLOPs per pixel of the closure network (3x3 convolutions
@@ -205,7 +215,7 @@ CNN_TRAIN_FLOP = 3 * CNN_FWD_FLOP - 2 * 9 * _CNN_CH[0] * _CNN_CH[1]
 CNN_FWD_BYTES = 32 + 3 * 64 + 3 * 64 + 12
 
 
-def run_cnn(args, torch, swe, stream, rank, world):
+def run_cnn(args, torch, swe, stream, rank, world, emit=True):
     """Closure network on one coarse grid (cnn-<n>sq: n x n pixels): K
     training steps (forward, backward, Adam) timed with CUDA events."""
     from paper_1705_00614_gb300 import closure
@@ -261,7 +271,44 @@ def run_cnn(args, torch, swe, stream, rank, world):
                                      "frac": fwd_gbs / hbm_peak, "bytes_per_pixel": CNN_FWD_BYTES,
                                      "kernel": "k_conv x 4 (forward)"},
                 "cpu_baseline": None, "e2e": None, "gpu_launches": None, "clocks": clk.summary()}
-        print(json.dumps(line), flush=True)
+        if emit:
+            print(json.dumps(line), flush=True)
+        return line
+    return None
+
+
+# Short runs of the other measured paths that the default (one-GPU) run
+# adds to its line: (workload, timed steps, warm-up steps, runner name)
+SECONDARY = (("ensemble-64", 500, 3, "run_ensemble"), ("cnn-2048sq", 20, 5, "run_cnn"))
+_SECONDARY_CONFIG = ("scenarios", "cells", "sizes", "gates", "gate_toggles_in_timed_steps", "pixels",
+                     "forward_ms", "forward_tflops")
+
+
+def secondary_entry(line):
+    """The part of a secondary workload's line that the default line keeps."""
+    out = {k: line[k] for k in ("metric", "value", "unit", "steps", "warmup", "ms_per_step", "dtype",
+                                "roofline", "forward_roofline", "gpu_launches", "clocks") if k in line}
+    out["workload"] = line["config"]["workload"]
+    out["config"] = {k: line["config"][k] for k in _SECONDARY_CONFIG if k in line["config"]}
+    return out
+
+
+def run_secondary(args, torch, swe):
+    """Each secondary workload on a stream of its own; an exception becomes
+    an entry with the error instead of a value."""
+    out = []
+    for wl, steps, warmup, fn in SECONDARY:
+        a2 = argparse.Namespace(**vars(args))
+        a2.workload, a2.steps, a2.warmup = wl, steps, warmup
+        try:
+            stream = torch.cuda.Stream()
+            torch.cuda.set_stream(stream)
+            line = globals()[fn](a2, torch, swe, stream, 0, 1, emit=False)
+            torch.cuda.synchronize()
+            out.append(secondary_entry(line))
+        except Exception as e:  # report, do not lose the headline line
+            out.append({"workload": wl, "error": f"{type(e).__name__}: {e}"[:300]})
+    return out
 
 
 def run_closure(args, torch, swe, stream, rank, world):
@@ -681,6 +728,8 @@ def main():
     ap.add_argument("--skip-dry", action="store_true",
                     help="skip dry work items (the paper's K1 wet-block test); off for the headline")
     ap.add_argument("--seg-h", type=int, default=0, help="output rows per work item (0 = automatic)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="default workload: leave out the short ensemble and closure-network runs")
     ap.add_argument("--mode", default="fused", choices=["fused", "staged"],
                     help="staged: one kernel per stage (the paper's K2-K8 split), for per-stage time shares")
     ap.add_argument("--closure-train", type=int, default=64, help="closure workload: training seeds")
@@ -887,6 +936,9 @@ def main():
                                                                    "d2h_bytes_per_step": io64_bytes}},
                 "gpu_launches": args.steps * (1 if args.mode == "fused" else 12 + (1 if len(prob.sources) else 0)),
                 "clocks": clk.summary()}
+        if world == 1 and not args.no_secondary and args.workload == ap.get_default("workload") \
+                and args.precision == "f32" and args.mode == "fused" and not args.skip_dry:
+            line["secondary"] = run_secondary(args, torch, swe)
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
