@@ -314,10 +314,10 @@ __global__ void __launch_bounds__(128, 1)
         }
         for (int q = 0; q < WT_GR; ++q) {
             mbar_init(&rfull[q], 1);
-            mbar_init(&rempty[q], 64);
+            mbar_init(&rempty[q], WT_COPY_THREADS);
         }
         for (int q = 0; q < WT_GS; ++q) {
-            mbar_init(&sfull[q], 64);
+            mbar_init(&sfull[q], WT_COPY_THREADS);
             mbar_init(&sempty[q], 1);
         }
         mbar_init(&tdone, 1);
@@ -384,9 +384,11 @@ __global__ void __launch_bounds__(128, 1)
         for (uint32_t R = gR > WT_GR ? gR - WT_GR : 0; R < gR; ++R)
             mbar_wait_bounded(&rfull[R % WT_GR], (R / WT_GR) & 1u);
     } else if (warp >= 2) {
-        // shifted operands: copy dx of gradient row R holds raw pixels
-        // 2 - dx .. 129 - dx (the raw row starts one pixel left of the tile)
-        const int ct = tid - 64;  // WT_COPY_THREADS copy threads
+        // shifted operands (warps 2 and 3): copy dx of gradient row R holds
+        // raw pixels 2 - dx .. 129 - dx (the raw row starts one pixel left of
+        // the tile)
+        static_assert(WT_COPY_THREADS == 64, "warps 0 and 1 issue the MMAs and the copies");
+        const int ct = tid - (128 - WT_COPY_THREADS);
         uint32_t R = 0;
         bool ok = true;
         for (int item = blockIdx.x; item < nitems && ok; item += gridDim.x) {
