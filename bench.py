@@ -293,6 +293,14 @@ def secondary_entry(line):
     return out
 
 
+def wants_secondary(args, world, default_workload):
+    """The secondary runs belong to the default line only: one GPU, the
+    default workload in FP32, the fused step without skipping, and not
+    turned off with --no-secondary."""
+    return (world == 1 and not args.no_secondary and args.workload == default_workload and args.precision == "f32"
+            and args.mode == "fused" and not args.skip_dry)
+
+
 def run_secondary(args, torch, swe):
     """Each secondary workload on a stream of its own; an exception becomes
     an entry with the error instead of a value."""
@@ -936,8 +944,7 @@ def main():
                                                                    "d2h_bytes_per_step": io64_bytes}},
                 "gpu_launches": args.steps * (1 if args.mode == "fused" else 12 + (1 if len(prob.sources) else 0)),
                 "clocks": clk.summary()}
-        if world == 1 and not args.no_secondary and args.workload == ap.get_default("workload") \
-                and args.precision == "f32" and args.mode == "fused" and not args.skip_dry:
+        if wants_secondary(args, world, ap.get_default("workload")):
             line["secondary"] = run_secondary(args, torch, swe)
         print(json.dumps(line), flush=True)
     if dist is not None:

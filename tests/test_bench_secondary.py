@@ -69,3 +69,20 @@ def test_default_secondary_workloads_exist():
         assert callable(getattr(bench, fn))
         assert steps > 0 and warmup >= 3
         assert wl.split("-")[0] in ("ensemble", "cnn")
+
+
+def test_only_the_default_one_gpu_line_gets_secondary_runs():
+    base = dict(workload="floodplain-16384sq-dx2m-flooded", precision="f32", mode="fused", skip_dry=False,
+                no_secondary=False)
+    default = base["workload"]
+
+    def wants(world=1, **kw):
+        return bench.wants_secondary(argparse.Namespace(**{**base, **kw}), world, default)
+
+    assert wants()
+    assert not wants(world=2)
+    assert not wants(no_secondary=True)
+    assert not wants(workload="floodplain-4096sq-dx5m-flooded")
+    assert not wants(precision="f64")
+    assert not wants(mode="staged")
+    assert not wants(skip_dry=True)
