@@ -315,8 +315,12 @@ SWE_API void swe_nest_destroy(swe_nest* n);
  * gives no closure model.  This library adds one: a 4-layer network of 3x3
  * convolutions, channels 5 -> 32 -> 32 -> 32 -> 3 with ReLU between layers,
  * that maps standardised coarse inputs (H, Ux, Uy, b, n_M) to corrections of
- * the coarse cells' net face-flux sums (the Fh, Fv of K8).  Convolutions run
- * on tensor cores with BF16 weights and activations and FP32 accumulation.
+ * the coarse cells' net face-flux sums (the Fh, Fv of K8).  Convolutions and
+ * weight gradients run on the tensor cores with BF16 weights and activations
+ * and FP32 accumulation.  Their device waits are bounded: a wait that gives
+ * up sets a device error word, which every later call that synchronises
+ * (set/get_params, gradients, train_step with loss != NULL) reports as
+ * SWE_ERR_DEVICE_TIMEOUT; the word stays set for the object's lifetime.
  *
  * A swe_cnn holds FP32 master parameters (flat: for each layer l, weights
  * [3][3][c_l][c_{l+1}] then biases [c_{l+1}]), Adam moments and the
