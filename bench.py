@@ -319,6 +319,19 @@ def run_secondary(args, torch, swe):
     return out
 
 
+def choose_on_validation(names, alphas, err_last, bar=0.01):
+    """The closed variant the validation seeds pick: the largest correction
+    scale whose mean relative error at the longest horizon stays within the
+    bar (the most the network may act while meeting it); if none does, the
+    one with the smallest error.  A diverged run (NaN) never passes; among
+    equal scales the first listed wins."""
+    err = {k: float(np.nan_to_num(err_last[k], nan=np.inf)) for k in names}
+    ok = [(a, -i, k) for i, (k, a) in enumerate(zip(names, alphas)) if err[k] <= bar]
+    if ok:
+        return max(ok)[2]
+    return min(names, key=lambda k: err[k])
+
+
 def run_closure(args, torch, swe, stream, rank, world):
     """Learned closure of the 4x coarser grid (closure-<n>sq: fine n^2 at
     dx = 5 m, coarse (n/4)^2 at 20 m).  Trains the network on fine runs of
@@ -440,14 +453,7 @@ def run_closure(args, torch, swe, stream, rank, world):
 
     last = horizons[-1]
     val = run_seeds(val_seeds)
-    # the validation seeds pick the largest correction scale whose error at
-    # the longest horizon stays within the 1% bar (the most the network may
-    # act while meeting it); if none does, the one with the smallest error
-    ok = [k for k, (a, _) in zip(names[1:], specs) if np.nan_to_num(val[k][last], nan=np.inf) <= 0.01]
-    if ok:
-        chosen = max(ok, key=lambda k: specs[names.index(k) - 1][0])
-    else:
-        chosen = min(names[1:], key=lambda k: np.nan_to_num(val[k][last], nan=np.inf))
+    chosen = choose_on_validation(names[1:], alphas, {k: val[k][last] for k in names[1:]})
     test = run_seeds(test_seeds)
     gain = [h for h in horizons if test[chosen][h] < test["plain"][h]]
     speedup = float(np.median(ms_fine)) / float(np.median(ms_closed))
