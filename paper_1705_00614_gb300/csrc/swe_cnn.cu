@@ -866,33 +866,15 @@ int x_map(CUtensorMap* m, const void* x, int n, int h, int w, int ci, int box_w 
     return SWE_OK;
 }
 
-// Work split of the convolution kernel: items of rc rows of one 128-pixel
-// column band, about one item per persistent CTA.
-struct ConvPlan {
-    int grid, rc, nitems;
-};
-ConvPlan conv_plan(const swe_cnn* c) {
-    const int tpr = (c->w + TCM - 1) / TCM;
-    const long long tiles = (long long)c->n * c->h * tpr;
-    int rc = (int)std::max<long long>(4, (tiles + c->ntc - 1) / c->ntc);
-    rc = std::min(rc, c->h);
-    // taller items until they fit one pass of the CTAs: a few items left
-    // over for a second pass would double the makespan
-    while (rc < c->h && (long long)c->n * tpr * ((c->h + rc - 1) / rc) > c->ntc) ++rc;
-    ConvPlan p;
-    p.rc = rc;
-    p.nitems = c->n * tpr * ((c->h + rc - 1) / rc);
-    p.grid = std::min(p.nitems, c->ntc);
-    return p;
-}
-
+// Convolution launch: items from row_plan (rc rows of one 128-pixel column
+// band, about one item per persistent CTA).
 template <int CI, int CO, int MODE>
 int conv(swe_cnn* c, const void* x, const __nv_bfloat16* w, const float* bias, void* out, const __nv_bfloat16* mask,
          int co_store) {
     CUtensorMap m;
     int rc = x_map(&m, x, c->n, c->h, c->w, CI);
     if (rc) return rc;
-    const ConvPlan p = conv_plan(c);
+    const RowPlan p = row_plan(c->n, c->h, c->w, c->ntc);
     k_conv<CI, CO, MODE><<<p.grid, 128, conv_smem_bytes<CI, CO>(), c->st>>>(m, w, bias, out, mask, c->n, c->h, c->w,
                                                                            co_store, p.rc, p.nitems, c->derr);
     CKC(cudaGetLastError());
@@ -914,18 +896,11 @@ int wgrad_tc(swe_cnn* c, const void* x, const void* g, int* nblk) {
     int rc = x_map(&xm, x, c->n, c->h, c->w, CI);
     if (!rc) rc = x_map(&gm, g, c->n, c->h, c->w, CO);
     if (rc) return rc;
-    const int slots = c->nwg;
-    const int tpr = (c->w + TCM - 1) / TCM;
-    const long long tiles = (long long)c->n * c->h * tpr;
-    int rows = (int)std::max<long long>(4, (tiles + slots - 1) / slots);
-    rows = std::min(rows, c->h);
-    while (rows < c->h && (long long)c->n * tpr * ((c->h + rows - 1) / rows) > slots) ++rows;
-    const int nitems = c->n * tpr * ((c->h + rows - 1) / rows);
-    const int grid = std::min(nitems, slots);
-    k_wgrad_tc<CI, CO><<<grid, 128, WgTc<CI, CO>::SMEM, c->st>>>(xm, gm, c->part, c->bpart, c->h, c->w, rows, nitems,
-                                                                 c->derr);
+    const RowPlan p = row_plan(c->n, c->h, c->w, c->nwg);
+    k_wgrad_tc<CI, CO><<<p.grid, 128, WgTc<CI, CO>::SMEM, c->st>>>(xm, gm, c->part, c->bpart, c->h, c->w, p.rc,
+                                                                   p.nitems, c->derr);
     CKC(cudaGetLastError());
-    *nblk = grid;
+    *nblk = p.grid;
     return SWE_OK;
 }
 

@@ -77,6 +77,30 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int m, int n) {
     return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+// Work plan of the persistent row-streaming kernels (the convolution and the
+// weight gradient): an item is rc consecutive rows (the last item of an
+// image may be shorter) of one 128-pixel column band of one image; items are
+// numbered band-fastest, then row block, then image, and CTA b takes items
+// b, b + grid, ...  rc starts at max(4, tiles / slots) and grows until the
+// items fit one pass of `slots` CTAs (a few items left for a second pass
+// would double the makespan) or rc reaches h.
+struct RowPlan {
+    int rc, nitems, grid;
+};
+__host__ __device__ inline RowPlan row_plan(int n, int h, int w, int slots) {
+    const int tpr = (w + TCM - 1) / TCM;
+    const long long tiles = (long long)n * h * tpr;
+    long long rc = (tiles + slots - 1) / slots;
+    rc = rc < 4 ? 4 : rc;
+    rc = rc > h ? h : rc;
+    while (rc < h && (long long)n * tpr * ((h + rc - 1) / rc) > slots) ++rc;
+    RowPlan p;
+    p.rc = (int)rc;
+    p.nitems = (int)((long long)n * tpr * ((h + rc - 1) / rc));
+    p.grid = p.nitems < slots ? p.nitems : slots;
+    return p;
+}
+
 // ---- Weight gradient (k_wgrad_tc) ----
 // Per 16-pixel K step one MMA: M = (dy, c), the three input rows of a tile
 // stacked, each row's NCX channel chunks followed by a chunk of ones
